@@ -1,0 +1,238 @@
+/*
+ * Oracle: FMM evaluation stages and the direct sum.  TEST INFRASTRUCTURE ONLY
+ * (see fmm_oracle.h).
+ *
+ * The evaluation runs the stages in the paper's order (Sec. III.A stage
+ * list): sort charges into tree order, leaf multipoles (P2M), upward M2M,
+ * M2L over the whole interaction list, downward L2L, local evaluation (L2P)
+ * and the direct near field (P2P), then the inverse sort.  The potential is
+ * u_i = -1/(4 pi) sum_{j != i} q_j / |r_i - r_j| (Eq. 1-3); pairs at zero
+ * distance contribute nothing (the self term, and coincident points).  The
+ * field is -grad u.
+ */
+#include "fmm_oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* accessors defined in tree.c */
+const int32_t* orc__perm(const orc_tree* t);
+const double* orc__pos_tree(const orc_tree* t);
+const int64_t* orc__box_start(const orc_tree* t);
+const int64_t* orc__box_count(const orc_tree* t);
+const double* orc__center(const orc_tree* t);
+int orc__levels(const orc_tree* t);
+int orc__splits(const orc_tree* t);
+int64_t orc__n(const orc_tree* t);
+int64_t orc__n_boxes(const orc_tree* t);
+int64_t orc__n_m2l(const orc_tree* t);
+const int32_t* orc__m2l_trg(const orc_tree* t);
+const int32_t* orc__m2l_src(const orc_tree* t);
+int64_t orc__n_p2p(const orc_tree* t);
+const int32_t* orc__p2p_trg(const orc_tree* t);
+const int32_t* orc__p2p_src(const orc_tree* t);
+
+static const double FOUR_PI = 12.566370614359172953850573533118;
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+static int64_t level_off(int l, int s) {
+  int64_t off = 0;
+  for (int i = 0; i < l; i++) off += (int64_t)1 << (s * i);
+  return off;
+}
+
+static int64_t first_ge(const int32_t* a, int64_t n, int32_t v) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targets,
+                  int64_t n_targets, double* u, double* field) {
+  const int64_t n = orc__n(t);
+  const int L = orc__levels(t), s = orc__splits(t);
+  const int64_t nch = (int64_t)1 << s;
+  const int64_t nbox = orc__n_boxes(t);
+  const int P = (p + 1) * (p + 1);
+  const int32_t* perm = orc__perm(t);
+  const double* X = orc__pos_tree(t);
+  const int64_t* bs = orc__box_start(t);
+  const int64_t* bc = orc__box_count(t);
+  const double* cen = orc__center(t);
+  const int64_t leaf_off = level_off(L, s);
+  const int64_t n_leaves = (int64_t)1 << (s * L);
+
+  /* sort: charges into tree order */
+  double* qt = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int64_t i = 0; i < n; i++) qt[i] = q[perm[i]];
+
+  /* which tree positions are evaluated, and which boxes feed them */
+  int64_t* inv = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t i = 0; i < n; i++) inv[perm[i]] = i;
+  int64_t n_eval = targets ? n_targets : n;
+  int64_t* tpos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_eval + 1));
+  for (int64_t k = 0; k < n_eval; k++) tpos[k] = targets ? inv[targets[k]] : inv[k];
+  char* need = (char*)calloc((size_t)nbox, 1);
+  for (int64_t k = 0; k < n_eval; k++) {
+    /* leaf holding tree position tpos[k] */
+    int64_t lo = 0, hi = n_leaves - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) / 2;
+      if (bs[leaf_off + mid] <= tpos[k]) lo = mid;
+      else hi = mid - 1;
+    }
+    int64_t b = lo;
+    for (int l = L; l >= 0; l--) {
+      need[level_off(l, s) + b] = 1;
+      b /= nch;
+    }
+  }
+
+  double* C = (double*)calloc((size_t)nbox * P, sizeof(double));
+  double* D = (double*)calloc((size_t)nbox * P, sizeof(double));
+
+  /* mpls: P2M on every leaf */
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t b = 0; b < n_leaves; b++) {
+    int64_t g = leaf_off + b;
+    double* pts = (double*)malloc(sizeof(double) * 3 * (size_t)bc[g]);
+    memcpy(pts, X + 3 * bs[g], sizeof(double) * 3 * (size_t)bc[g]);
+    orc_p2m(p, pts, qt + bs[g], bc[g], cen + 3 * g, C + (size_t)g * P);
+    free(pts);
+  }
+  /* M2M: levels L-1 .. 0 */
+  for (int l = L - 1; l >= 0; l--) {
+    int64_t off = level_off(l, s), offc = level_off(l + 1, s);
+    int64_t nb = (int64_t)1 << (s * l);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t b = 0; b < nb; b++) {
+      int64_t g = off + b;
+      for (int64_t c = 0; c < nch; c++) {
+        int64_t gc = offc + nch * b + c;
+        orc_m2m(p, C + (size_t)gc * P, cen + 3 * gc, cen + 3 * g, C + (size_t)g * P);
+      }
+    }
+  }
+  /* M2L over the whole list, grouped by target */
+  const int64_t nm = orc__n_m2l(t);
+  const int32_t* mt = orc__m2l_trg(t);
+  const int32_t* ms = orc__m2l_src(t);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t g = 0; g < nbox; g++) {
+    if (!need[g]) continue;
+    for (int64_t k = first_ge(mt, nm, (int32_t)g); k < nm && mt[k] == g; k++)
+      orc_m2l(p, C + (size_t)ms[k] * P, cen + 3 * (int64_t)ms[k], cen + 3 * g, D + (size_t)g * P);
+  }
+  /* L2L: levels 1 .. L */
+  for (int l = 1; l <= L; l++) {
+    int64_t off = level_off(l, s), offp = level_off(l - 1, s);
+    int64_t nb = (int64_t)1 << (s * l);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < nb; b++) {
+      int64_t g = off + b;
+      if (!need[g]) continue;
+      int64_t gp = offp + b / nch;
+      orc_l2l(p, D + (size_t)gp * P, cen + 3 * gp, cen + 3 * g, D + (size_t)g * P);
+    }
+  }
+  /* evloc (L2P) and evdir (P2P) for every evaluated point */
+  const int64_t np = orc__n_p2p(t);
+  const int32_t* pt = orc__p2p_trg(t);
+  const int32_t* ps = orc__p2p_src(t);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t k = 0; k < n_eval; k++) {
+    int64_t i = tpos[k];
+    int64_t lo = 0, hi = n_leaves - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) / 2;
+      if (bs[leaf_off + mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    int64_t leaf = lo, g = leaf_off + leaf;
+    double grad[3];
+    double uf = orc_l2p(p, D + (size_t)g * P, cen + 3 * g, X + 3 * i, grad);
+    double un = 0.0, gn[3] = {0.0, 0.0, 0.0};
+    for (int64_t e = first_ge(pt, np, (int32_t)leaf); e < np && pt[e] == leaf; e++) {
+      int64_t gs = leaf_off + ps[e];
+      for (int64_t j = bs[gs]; j < bs[gs] + bc[gs]; j++) {
+        double dx = X[3 * i] - X[3 * j], dy = X[3 * i + 1] - X[3 * j + 1], dz = X[3 * i + 2] - X[3 * j + 2];
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 == 0.0) continue;
+        double r = sqrt(r2);
+        un += qt[j] / r;
+        double w = qt[j] / (r2 * r);
+        gn[0] -= w * dx;
+        gn[1] -= w * dy;
+        gn[2] -= w * dz;
+      }
+    }
+    /* u = -1/(4 pi) (far + near); field = -grad u = +1/(4 pi) grad(far + near) */
+    u[k] = -(uf + un) / FOUR_PI;
+    if (field)
+      for (int a = 0; a < 3; a++) field[3 * k + a] = (grad[a] + gn[a]) / FOUR_PI;
+  }
+  free(qt);
+  free(inv);
+  free(tpos);
+  free(need);
+  free(C);
+  free(D);
+}
+
+/* Eq. 1-3 summed directly. */
+void orc_direct(const double* pos, const double* q, int64_t n, const int64_t* targets,
+                int64_t n_targets, double* u, double* field) {
+  int64_t n_eval = targets ? n_targets : n;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n_eval; k++) {
+    int64_t i = targets ? targets[k] : k;
+    double acc = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+      double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1], dz = pos[3 * i + 2] - pos[3 * j + 2];
+      double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 == 0.0) continue;
+      double r = sqrt(r2);
+      acc += q[j] / r;
+      double w = q[j] / (r2 * r);
+      g0 += w * dx;
+      g1 += w * dy;
+      g2 += w * dz;
+    }
+    u[k] = -acc / FOUR_PI;
+    /* grad(1/r) = -(r_i - r_j)/r^3, so field = -grad u = -(1/4pi) sum q (r_i - r_j)/r^3 */
+    if (field) {
+      field[3 * k] = -g0 / FOUR_PI;
+      field[3 * k + 1] = -g1 / FOUR_PI;
+      field[3 * k + 2] = -g2 / FOUR_PI;
+    }
+  }
+}
+
+void orc_direct_vjp(const double* pos, const double* q, const double* g, int64_t n,
+                    double* dq, double* dpos) {
+  double* fu = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  double* fv = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  double* uq = (double*)malloc(sizeof(double) * (size_t)n);
+  orc_direct(pos, q, n, NULL, 0, uq, fu);
+  orc_direct(pos, g, n, NULL, 0, dq, fv);
+  /* grad u = -field */
+  for (int64_t k = 0; k < n; k++)
+    for (int a = 0; a < 3; a++) dpos[3 * k + a] = -(g[k] * fu[3 * k + a] + q[k] * fv[3 * k + a]);
+  free(fu);
+  free(fv);
+  free(uq);
+}
