@@ -1,0 +1,173 @@
+/*
+ * fmm.h - C ABI of the GB300 (sm_103a) evaluator for the adaptive
+ * point-charge Laplace Fast Multipole Method of Kraft, Bruckner, Suess and
+ * Abert, "jaxFMM: An Adaptive, GPU-Parallel Implementation of the Fast
+ * Multipole Method in JAX" (arXiv 2511.15269).
+ *
+ * What is computed (Sec. II, Eq. 1-3): for N point charges q_i at r_i,
+ *     u_i = -1/(4 pi) * sum_{j != i} q_j / |r_i - r_j|          (potential)
+ *     E_i = -grad u (r_i)                                       (field)
+ * approximated by an FMM of expansion order p over a median-split 2^s-tree
+ * (Sec. II.A) with level-marching cross-level interaction lists built from
+ * the well-separation criterion R + theta r <= theta d (Eq. 4, Sec. II.B).
+ * Pairs at zero distance (the self term and coincident points) contribute
+ * nothing.
+ *
+ * Conventions shared by every entry point:
+ *  - Data pointers are DEVICE pointers (cudaMalloc'd or equivalent) owned by
+ *    the caller, contiguous, unless a function says "host".  Positions are
+ *    N x 3 row-major doubles (x, y, z per point); charges, potentials and
+ *    gradients with respect to charges are N doubles; fields and gradients
+ *    with respect to positions are N x 3 doubles.  Outputs come back in the
+ *    caller's point order.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Evaluation calls only enqueue work on it and return; errors
+ *    that kernels detect (a bounded wait that gave up) are latched in the
+ *    tree and returned by fmm_tree_status().
+ *  - Every call returns an fmm_status; on failure fmm_last_error() gives a
+ *    thread-local message.  Nothing throws or aborts.
+ *  - A tree owns the device workspace its evaluations use (allocated once
+ *    by fmm_build_tree).  Evaluations of one tree must be ordered on one
+ *    stream; two evaluations of the same tree in flight at once race.
+ *    Distinct trees are independent.
+ */
+#ifndef GB300_FMM_H
+#define GB300_FMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FMM_OK = 0,
+  FMM_ERR_INVALID_ARG = 1, /* bad size, parameter, null pointer, NaN/Inf position */
+  FMM_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
+  FMM_ERR_OOM = 3,         /* device allocation failed */
+  FMM_ERR_CAPACITY = 4,    /* a fixed-capacity buffer overflowed (batched calls) */
+  FMM_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+} fmm_status;
+
+enum {
+  FMM_FP64 = 0,  /* every stage in FP64                                        */
+  FMM_FP32C = 1  /* P2M/M2M/M2L/L2L/L2P/P2P in FP32 on box-radius-scaled
+                    coefficients, compensated (two-sum) accumulation of leaf and
+                    local sums; rotation coefficients generated in FP64; final
+                    near + far combination in FP64                             */
+};
+
+enum {
+  FMM_TIE_TARGET = 1 /* equal average radii advance the target level (the
+                        same-vs-cross table of Sec. II.B) instead of the source
+                        level (the text of Sec. II.B, the default)            */
+};
+
+#define FMM_MAX_P 10 /* largest supported expansion order */
+
+/* Parameters of the hierarchy and the expansion (Sec. II.A-II.D, Listing 1). */
+typedef struct {
+  int p;          /* expansion order, 1..FMM_MAX_P                              */
+  int leaf_size;  /* N_max: levels are added until boxes hold <= N_max points;
+                     must be >= 2^splits                                         */
+  int splits;     /* s: bisections per level, 2^s children per box, 1..3        */
+  double theta;   /* well-separation parameter of Eq. 4, 0 < theta < 1          */
+  int precision;  /* FMM_FP64 or FMM_FP32C, used by the evaluation calls        */
+  int flags;      /* 0 or FMM_TIE_TARGET                                        */
+} fmm_params;
+
+typedef struct fmm_tree fmm_tree;
+
+typedef struct {
+  int64_t n;             /* points                                              */
+  int levels;            /* L: the leaf level; the root is level 0              */
+  int p, splits, leaf_size, precision;
+  double theta;
+  int64_t n_boxes;       /* sum over levels of 2^(s l)                          */
+  int64_t n_leaves;      /* 2^(s L)                                             */
+  int64_t n_m2l;         /* multipole-to-local interactions, all levels         */
+  int64_t n_p2p;         /* near-field leaf pairs (self pairs included)         */
+  int64_t n_p2p_pairs;   /* near-field point pairs: sum over leaf pairs |S||T|  */
+  size_t device_bytes;   /* device memory owned by the tree                     */
+  double build_ms;       /* wall time of fmm_build_tree                         */
+} fmm_stats;
+
+/* Thread-local description of the last failure on this thread. */
+const char* fmm_last_error(void);
+
+/* Number of levels L for n points (Sec. II.A step 4): the smallest l with
+ * ceil(n / 2^(splits l)) <= leaf_size.  Returns -1 on invalid arguments. */
+int fmm_num_levels(int64_t n, int leaf_size, int splits);
+
+/* Builds the hierarchy of Sec. II.A-II.B on the device: median-split tree
+ * (Listing 2: longest-extent axis, ties to the lowest axis; ceil(n/2) points
+ * to the lower child ordered by (coordinate, original index); leaf points in
+ * ascending original index), box centres (bounding-box midpoints) and radii
+ * (half diagonals) in FP64, level-march M2L lists and near-field lists, and
+ * the rotation coefficients of every M2M, M2L and L2L translation (FP64,
+ * also stored rounded to FP32).  -0.0 coordinates are treated as +0.0.
+ *   pos     device, n x 3 doubles, read only during the call
+ *   n       >= 1 points (< 2^31)
+ *   params  host pointer, copied
+ *   stream  work is enqueued on it; the call synchronises it before returning
+ *   out     receives the new tree; free with fmm_tree_free
+ * Errors: FMM_ERR_INVALID_ARG (n < 1, bad params, non-finite coordinate),
+ * FMM_ERR_OOM, FMM_ERR_CUDA.  On error *out is set to NULL. */
+int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void* stream,
+                   fmm_tree** out);
+
+/* Releases a tree and its device memory (synchronises the device first).
+ * NULL is accepted. */
+void fmm_tree_free(fmm_tree* tree);
+
+/* Selects the precision of later evaluation calls (FMM_FP64 or FMM_FP32C). */
+int fmm_tree_set_precision(fmm_tree* tree, int precision);
+
+/* Fills *stats (host pointer). */
+int fmm_tree_stats(const fmm_tree* tree, fmm_stats* stats);
+
+/* Synchronises `stream`, then returns and clears the status latched by the
+ * kernels of earlier evaluations of this tree (FMM_OK or FMM_ERR_TIMEOUT). */
+int fmm_tree_status(fmm_tree* tree, void* stream);
+
+/* Copies the hierarchy to HOST arrays for inspection; every pointer may be
+ * NULL.  Sizes: perm n (tree position -> original index); box_start,
+ * box_count, radius n_boxes; center 3 n_boxes; level_avg_radius levels+1;
+ * m2l_trg, m2l_src n_m2l (global box ids, box b of level l has id
+ * (2^(s l) - 1)/(2^s - 1) + b, sorted by (target, source)); p2p_trg, p2p_src
+ * n_p2p (leaf indices, sorted by (target, source)).  Synchronous. */
+int fmm_tree_export(const fmm_tree* tree, int32_t* perm, int64_t* box_start,
+                    int64_t* box_count, double* center, double* radius,
+                    double* level_avg_radius, int32_t* m2l_trg, int32_t* m2l_src,
+                    int32_t* p2p_trg, int32_t* p2p_src);
+
+/* Potential u (n doubles) of charges q (n doubles) at the tree's points:
+ * sort into tree order, P2M, M2M, M2L, L2L, L2P + P2P, inverse sort
+ * (the stages of Sec. III.A). */
+int fmm_eval_potential(const fmm_tree* tree, const double* q, double* u, void* stream);
+
+/* Field E = -grad u (n x 3 doubles) and, if u != NULL, the potential;
+ * L2P uses the gradient of the regular basis (App. A.3). */
+int fmm_eval_field(const fmm_tree* tree, const double* q, double* u, double* field,
+                   void* stream);
+
+/* Same as fmm_eval_potential with HOST buffers: copies q to the device,
+ * evaluates, copies u back and synchronises `stream`.  Pinned host memory
+ * gives the fastest copies. */
+int fmm_eval_potential_host(const fmm_tree* tree, const double* q_host, double* u_host,
+                            void* stream);
+
+/* Vector-Jacobian product of u = K q at the tree's fixed geometry, for a loss
+ * L(u) with grad_u = dL/du (n doubles):
+ *     grad_q   = K grad_u                               (K is symmetric)
+ *     grad_pos = grad_u_k * grad u(r_k) + q_k * grad v(r_k),  v = K grad_u
+ * grad_q (n) and grad_pos (n x 3) may each be NULL.  The tree is held fixed
+ * (gradients are taken with the hierarchy of the current positions). */
+int fmm_backward(const fmm_tree* tree, const double* q, const double* grad_u,
+                 double* grad_q, double* grad_pos, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_FMM_H */

@@ -4,6 +4,7 @@
  * fmm_oracle.h).
  *
  * Readings taken where the paper is silent or ambiguous:
+ *  - Coordinates equal to -0.0 are treated as +0.0.
  *  - Split (Sec. II.A steps 1-2, Listing 2): a box's axis is the one of largest
  *    extent of its points' bounding box, ties to the lowest axis index (as
  *    argmax does).  Its points are ordered by (coordinate on that axis,
@@ -206,6 +207,10 @@ orc_tree* orc_tree_build(const double* pos, int64_t n, int leaf_size, int s, dou
                          int tie_target) {
   if (n < 1 || s < 1 || leaf_size < (1 << s)) return NULL;
   orc_tree* t = (orc_tree*)calloc(1, sizeof(orc_tree));
+  /* -0.0 is treated as +0.0 (x + 0.0 rounds -0.0 to +0.0) */
+  double* canon = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  for (int64_t i = 0; i < 3 * n; i++) canon[i] = pos[i] + 0.0;
+  pos = canon;
   t->n = n;
   t->s = s;
   t->theta = theta;
@@ -288,6 +293,7 @@ orc_tree* orc_tree_build(const double* pos, int64_t n, int leaf_size, int s, dou
     free(tmp);
   }
   free(seg_start);
+  free(canon);
   build_lists(t);
   return t;
 }

@@ -1,0 +1,249 @@
+// C ABI of the FMM library (declarations and contracts in include/fmm.h).
+#include <cstdarg>
+#include <chrono>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fmm {
+
+namespace {
+thread_local char g_err[1024] = "";
+std::mutex g_init_mu;
+bool g_tables_ready[64] = {};
+
+void ensure_tables() {
+  int dev = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (dev >= 0 && dev < 64 && g_tables_ready[dev]) return;
+  init_tables_fp32();
+  init_tables_fp64();
+  if (dev >= 0 && dev < 64) g_tables_ready[dev] = true;
+}
+
+// grad_pos = g grad u + q grad v = -(g E_q + q E_g)
+__global__ void backward_combine_kernel(int64_t n, const double* __restrict__ q, const double* __restrict__ g,
+                                        const double* __restrict__ eq, const double* __restrict__ eg,
+                                        double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int a = 0; a < 3; a++) out[3 * i + a] = -(g[i] * eq[3 * i + a] + q[i] * eg[3 * i + a]);
+}
+
+void free_tree(fmm_tree* t) {
+  if (!t) return;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {t->perm,     t->box_start, t->box_count, t->center,   t->radius,   t->m2l_off,  t->m2l_src,
+                  t->m2l_trg,  t->m2l_order, t->p2p_off,   t->p2p_src,  t->p2p32,    t->leaf_order, t->pos_local,
+                  t->pos64,    t->inv_rho32, t->inv_rho64, t->geo32,    t->geo64,    t->m2m32,    t->m2m64,
+                  t->l2l32,    t->l2l64,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
+                  t->Lam64,    t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
+                  t->counters, t->status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete[] t->level_avg_host;
+  delete t;
+}
+
+void eval_any(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
+  if (t->prm.precision == FMM_FP32C) eval_fp32(t, q, u, field, st);
+  else eval_fp64(t, q, u, field, st);
+}
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    f();
+    return FMM_OK;
+  } catch (const Fail& e) {
+    return e.code;
+  } catch (...) {
+    set_error("unexpected C++ exception");
+    return FMM_ERR_CUDA;
+  }
+}
+
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+const char* last_error() { return g_err; }
+
+}  // namespace fmm
+
+using namespace fmm;
+
+extern "C" {
+
+const char* fmm_last_error(void) { return fmm::last_error(); }
+
+int fmm_num_levels(int64_t n, int leaf_size, int splits) {
+  if (n < 1 || splits < 1 || splits > 3 || leaf_size < (1 << splits)) return -1;
+  int L = 0;
+  for (;;) {
+    const int64_t boxes = (int64_t)1 << (splits * L);
+    if ((n + boxes - 1) / boxes <= leaf_size) return L;
+    L++;
+  }
+}
+
+int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void* stream, fmm_tree** out) {
+  if (out) *out = nullptr;
+  fmm_tree* t = nullptr;
+  int rc = guarded([&] {
+    require(out != nullptr, "out is NULL");
+    require(params != nullptr, "params is NULL");
+    require(pos != nullptr, "pos is NULL");
+    const fmm_params& p = *params;
+    require(n >= 1 && n < (int64_t)1 << 31, "n must be in [1, 2^31)");
+    require(p.p >= 1 && p.p <= FMM_MAX_P, "p must be in [1, FMM_MAX_P]");
+    require(p.splits >= 1 && p.splits <= 3, "splits must be 1, 2 or 3");
+    require(p.leaf_size >= (1 << p.splits) && p.leaf_size <= kMaxLeaf, "leaf_size must be in [2^splits, 256]");
+    require(p.theta > 0.0 && p.theta < 1.0, "theta must be in (0, 1)");
+    require(p.precision == FMM_FP64 || p.precision == FMM_FP32C, "precision must be FMM_FP64 or FMM_FP32C");
+    require((p.flags & ~FMM_TIE_TARGET) == 0, "unknown flags");
+    auto t0 = std::chrono::steady_clock::now();
+    ensure_tables();
+    t = new fmm_tree();
+    t->prm = p;
+    t->n = n;
+    t->L = fmm_num_levels(n, p.leaf_size, p.splits);
+    build_tree(t, pos, (cudaStream_t)stream);
+    t->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  });
+  if (rc != FMM_OK) {
+    free_tree(t);
+    return rc;
+  }
+  *out = t;
+  return FMM_OK;
+}
+
+void fmm_tree_free(fmm_tree* tree) { free_tree(tree); }
+
+int fmm_tree_set_precision(fmm_tree* tree, int precision) {
+  return guarded([&] {
+    require(tree != nullptr, "tree is NULL");
+    require(precision == FMM_FP64 || precision == FMM_FP32C, "precision must be FMM_FP64 or FMM_FP32C");
+    tree->prm.precision = precision;
+  });
+}
+
+int fmm_tree_stats(const fmm_tree* t, fmm_stats* s) {
+  return guarded([&] {
+    require(t != nullptr && s != nullptr, "NULL argument");
+    std::memset(s, 0, sizeof(*s));
+    s->n = t->n;
+    s->levels = t->L;
+    s->p = t->prm.p;
+    s->splits = t->prm.splits;
+    s->leaf_size = t->prm.leaf_size;
+    s->precision = t->prm.precision;
+    s->theta = t->prm.theta;
+    s->n_boxes = t->n_boxes;
+    s->n_leaves = t->n_leaves;
+    s->n_m2l = t->n_m2l;
+    s->n_p2p = t->n_p2p;
+    s->n_p2p_pairs = t->n_p2p_pairs;
+    s->device_bytes = t->device_bytes;
+    s->build_ms = t->build_ms;
+  });
+}
+
+int fmm_tree_status(fmm_tree* t, void* stream) {
+  int code = FMM_OK;
+  int rc = guarded([&] {
+    require(t != nullptr, "tree is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&h, t->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    FMM_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h & ST_TIMEOUT) {
+      set_error("a bounded device-side wait gave up (near-field tile copy)");
+      code = FMM_ERR_TIMEOUT;
+    }
+  });
+  return rc != FMM_OK ? rc : code;
+}
+
+int fmm_tree_export(const fmm_tree* t, int32_t* perm, int64_t* box_start, int64_t* box_count, double* center,
+                    double* radius, double* level_avg_radius, int32_t* m2l_trg, int32_t* m2l_src,
+                    int32_t* p2p_trg, int32_t* p2p_src) {
+  return guarded([&] {
+    require(t != nullptr, "tree is NULL");
+    auto cp = [](void* dst, const void* src, size_t bytes) {
+      if (dst && bytes) FMM_CUDA_TRY(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    };
+    cp(perm, t->perm, sizeof(int32_t) * t->n);
+    cp(box_start, t->box_start, sizeof(int64_t) * t->n_boxes);
+    if (box_count) {
+      std::vector<int32_t> c(t->n_boxes);
+      cp(c.data(), t->box_count, sizeof(int32_t) * t->n_boxes);
+      for (int64_t i = 0; i < t->n_boxes; i++) box_count[i] = c[i];
+    }
+    cp(center, t->center, sizeof(double) * 3 * t->n_boxes);
+    cp(radius, t->radius, sizeof(double) * t->n_boxes);
+    if (level_avg_radius) std::memcpy(level_avg_radius, t->level_avg_host, sizeof(double) * (t->L + 1));
+    cp(m2l_trg, t->m2l_trg, sizeof(int32_t) * t->n_m2l);
+    cp(m2l_src, t->m2l_src, sizeof(int32_t) * t->n_m2l);
+    cp(p2p_src, t->p2p_src, sizeof(int32_t) * t->n_p2p);
+    if (p2p_trg) {
+      std::vector<int64_t> off(t->n_leaves + 1);
+      cp(off.data(), t->p2p_off, sizeof(int64_t) * (t->n_leaves + 1));
+      for (int64_t l = 0; l < t->n_leaves; l++)
+        for (int64_t e = off[l]; e < off[l + 1]; e++) p2p_trg[e] = (int32_t)l;
+    }
+  });
+}
+
+int fmm_eval_potential(const fmm_tree* t, const double* q, double* u, void* stream) {
+  return guarded([&] {
+    require(t != nullptr && q != nullptr && u != nullptr, "NULL argument");
+    eval_any(t, q, u, nullptr, (cudaStream_t)stream);
+  });
+}
+
+int fmm_eval_field(const fmm_tree* t, const double* q, double* u, double* field, void* stream) {
+  return guarded([&] {
+    require(t != nullptr && q != nullptr && field != nullptr, "NULL argument");
+    eval_any(t, q, u, field, (cudaStream_t)stream);
+  });
+}
+
+int fmm_eval_potential_host(const fmm_tree* t, const double* q_host, double* u_host, void* stream) {
+  return guarded([&] {
+    require(t != nullptr && q_host != nullptr && u_host != nullptr, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    FMM_CUDA_TRY(cudaMemcpyAsync(t->q_stage, q_host, sizeof(double) * t->n, cudaMemcpyHostToDevice, st));
+    eval_any(t, t->q_stage, t->u_stage, nullptr, st);
+    FMM_CUDA_TRY(cudaMemcpyAsync(u_host, t->u_stage, sizeof(double) * t->n, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  });
+}
+
+int fmm_backward(const fmm_tree* t, const double* q, const double* grad_u, double* grad_q, double* grad_pos,
+                 void* stream) {
+  return guarded([&] {
+    require(t != nullptr && q != nullptr && grad_u != nullptr, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (grad_pos) {
+      eval_any(t, q, nullptr, t->f_stage, st);          // E of the charges
+      eval_any(t, grad_u, grad_q, t->g_stage, st);      // v = K grad_u and E of grad_u
+      backward_combine_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, q, grad_u, t->f_stage, t->g_stage,
+                                                                   grad_pos);
+      FMM_LAUNCH_CHECK();
+    } else if (grad_q) {
+      eval_any(t, grad_u, grad_q, nullptr, st);
+    }
+  });
+}
+
+}  // extern "C"

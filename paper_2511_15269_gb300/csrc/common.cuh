@@ -1,0 +1,202 @@
+// Internal declarations shared by the CUDA translation units of the FMM
+// library (C ABI in include/fmm.h).  Nothing here is part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/fmm.h"
+
+namespace fmm {
+
+// ---- error handling -------------------------------------------------------
+void set_error(const char* fmt, ...);
+const char* last_error();
+
+struct Fail {
+  int code;
+};
+
+#define FMM_CUDA_TRY(expr)                                                      \
+  do {                                                                          \
+    cudaError_t e_ = (expr);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      ::fmm::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),  \
+                       __FILE__, __LINE__);                                     \
+      throw ::fmm::Fail{e_ == cudaErrorMemoryAllocation ? FMM_ERR_OOM           \
+                                                        : FMM_ERR_CUDA};        \
+    }                                                                           \
+  } while (0)
+
+#define FMM_LAUNCH_CHECK() FMM_CUDA_TRY(cudaGetLastError())
+
+inline void require(bool ok, const char* what) {
+  if (!ok) {
+    set_error("invalid argument: %s", what);
+    throw Fail{FMM_ERR_INVALID_ARG};
+  }
+}
+
+// Device status bits latched by kernels (read by fmm_tree_status).
+enum : int { ST_TIMEOUT = 1 };
+
+// Bounded waits: iterations of mbarrier.try_wait before giving up.
+constexpr long long kWaitLimit = 1ll << 26;
+
+// ---- sizes -----------------------------------------------------------------
+constexpr int kMaxP = FMM_MAX_P;
+constexpr int kMaxLeaf = 256;     // largest leaf the leaf kernels accept
+constexpr int kSmallCap = 2048;   // segments up to this size finish in one CTA
+
+__host__ __device__ constexpr int ncoef(int p) { return (p + 1) * (p + 1); }
+// Coefficient rows are padded to a multiple of 4 reals for vector loads.
+__host__ __device__ constexpr int ncoef_pad(int p) { return (ncoef(p) + 3) & ~3; }
+
+// Per-interaction geometry fields (structure of arrays, field-major):
+//   M2L: [0] 1/r  [1] rho_S/r  [2] rho_T/r  then cos(m phi), sin(m phi),
+//        cos(m theta), sin(m theta) for m = 1..p
+//   edges (per child box, M2M and L2L each): [0] r/rho_P  [1] rho_C/rho_P
+//        then the same 4p trigonometric rows
+__host__ __device__ constexpr int m2l_fields(int p) { return 3 + 4 * p; }
+__host__ __device__ constexpr int edge_fields(int p) { return 2 + 4 * p; }
+
+// Near-field entry for the FP32 path: source leaf (bit 31 set when the two
+// leaves' bounding boxes touch, so coincident points are possible) and the
+// centre offset c_T - c_S rounded to FP32.
+struct __align__(16) P2PEntry {
+  int src;
+  float dx, dy, dz;
+};
+
+// Tree-ordered FP64 point record (x, y, z, charge), 32-byte aligned for
+// bulk copies.
+struct __align__(32) dvec4 {
+  double x, y, z, w;
+};
+
+}  // namespace fmm
+
+struct fmm_tree {
+  fmm_params prm;
+  int64_t n = 0;
+  int L = 0;
+  int s = 2;
+  int64_t n_boxes = 0, n_leaves = 0;
+  int64_t n_m2l = 0, n_p2p = 0, n_p2p_pairs = 0;
+  int max_leaf = 0;          // largest leaf point count
+  double build_ms = 0;
+  size_t device_bytes = 0;
+  double* level_avg_host = nullptr;  // L + 1
+
+  // hierarchy (device)
+  int32_t* perm = nullptr;       // n: tree position -> original index
+  int64_t* box_start = nullptr;  // n_boxes
+  int32_t* box_count = nullptr;  // n_boxes
+  double* center = nullptr;      // 3 n_boxes
+  double* radius = nullptr;      // n_boxes
+  int64_t* m2l_off = nullptr;    // n_boxes + 1, CSR by target global box
+  int32_t* m2l_src = nullptr;    // n_m2l
+  int32_t* m2l_trg = nullptr;    // n_m2l
+  int32_t* m2l_order = nullptr;  // n_boxes: target boxes, longest list first
+  int64_t* p2p_off = nullptr;    // n_leaves + 1, CSR by target leaf
+  int32_t* p2p_src = nullptr;    // n_p2p
+  fmm::P2PEntry* p2p32 = nullptr;  // n_p2p
+  int32_t* leaf_order = nullptr;   // n_leaves: target leaves, most work first
+
+  // per-point and per-box constants
+  float4* pos_local = nullptr;   // n: tree order, x - c_leaf (FP32), w = 0
+  fmm::dvec4* pos64 = nullptr;   // n: tree order, x (FP64), w = 0
+  float* inv_rho32 = nullptr;    // n_boxes: 1 / scaling radius (0 if radius 0)
+  double* inv_rho64 = nullptr;
+
+  // rotation / translation coefficients
+  float* geo32 = nullptr;        // m2l_fields(p) x n_m2l
+  double* geo64 = nullptr;
+  float* m2m32 = nullptr;        // edge_fields(p) x n_boxes (row = child id)
+  double* m2m64 = nullptr;
+  float* l2l32 = nullptr;
+  double* l2l64 = nullptr;
+
+  // evaluation workspace
+  float4* src32 = nullptr;       // n: (x_local, q) in tree order
+  fmm::dvec4* src64 = nullptr;   // n: (x, q) in tree order
+  float* M32 = nullptr;          // n_boxes x ncoef_pad(p)
+  float* Lam32 = nullptr;
+  double* M64 = nullptr;
+  double* Lam64 = nullptr;
+  void* near_u = nullptr;        // n x 8 bytes: near-field potential sums
+  void* near_f = nullptr;        // 3n x 8 bytes: near-field gradient sums
+  double* q_stage = nullptr;     // n (host-buffer entry points, backward)
+  double* u_stage = nullptr;     // n
+  double* f_stage = nullptr;     // 3 n (backward)
+  double* g_stage = nullptr;     // 3 n (backward)
+  int* counters = nullptr;       // work counters, reset before each launch
+  int* status = nullptr;         // latched kernel status bits
+};
+
+namespace fmm {
+
+// tree_build.cu
+void build_tree(fmm_tree* t, const double* pos, cudaStream_t st);
+
+// eval_f32.cu / eval_f64.cu: the evaluation pipelines.
+//   q: device, original order; u / field: device outputs (nullable)
+void eval_fp32(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st);
+void eval_fp64(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st);
+// Per-precision one-time set-up: constant tables for every order.
+void init_tables_fp32();
+void init_tables_fp64();
+
+// tables.cu: host-side FP64 constant tables (see there for the formulas).
+struct HostTables {
+  // dense per degree n: (2n+1)^2 entries at offset b_off(n)
+  double B[1771], Binv[1771];
+  double ax_m2l[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];  // [n][k][|m|]
+  double ax_m2m[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];
+  double ax_l2l[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];
+  double r_diag[kMaxP + 1];                 // regular-basis recursion constants
+  double r_sub[kMaxP + 1];
+  double r_a[(kMaxP + 1) * (kMaxP + 1)];    // [n][|m|]
+  double r_b[(kMaxP + 1) * (kMaxP + 1)];
+};
+const HostTables& host_tables();
+__host__ __device__ constexpr int b_off(int n) {
+  // sum_{j<n} (2j+1)^2 = n (4n^2 - 1) / 3
+  return n * (4 * n * n - 1) / 3;
+}
+
+// scan.cu: exclusive prefix sum of n int64 values (in place allowed);
+// returns the total (synchronises the stream).
+int64_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+void exclusive_scan_async(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
+                          cudaStream_t st);
+
+template <class T>
+T* dev_alloc(fmm_tree* t, size_t count) {
+  T* p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
+    throw Fail{FMM_ERR_OOM};
+  }
+  if (t) t->device_bytes += sizeof(T) * count;
+  return p;
+}
+
+template <class T>
+T* scratch_alloc(size_t count) {
+  return dev_alloc<T>(nullptr, count);
+}
+
+inline int grid_for(int64_t n, int block, int cap = 152 * 64) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace fmm

@@ -1,0 +1,711 @@
+// Evaluation kernels of the FMM (stages of Sec. III.A: sort, P2M, M2M, M2L,
+// L2L, L2P, P2P, inverse sort), compiled once per precision.  The including
+// translation unit defines `real`, FMM_EVAL_FN and FMM_INIT_FN.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "expansion.cuh"
+
+namespace fmm {
+namespace {
+
+constexpr bool kF32 = std::is_same<real, float>::value;
+using vec4 = typename std::conditional<kF32, float4, dvec4>::type;
+constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
+
+// ---- small helpers ----------------------------------------------------------
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Knuth's two-sum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(real& s, real& e, real b) {
+  real a = s;
+  real t = a + b;
+  real bb = t - a;
+  real err = (a - (t - bb)) + (b - bb);
+  s = t;
+  e += err;
+}
+
+__device__ __forceinline__ const real* m2l_row(const real* base, int64_t stride, int f) {
+  return base + (int64_t)f * stride;
+}
+
+template <int P>
+__device__ __forceinline__ void load_trig(const real* geo, int64_t stride, int64_t e, int f0,
+                                          real (&cp)[P], real (&sp)[P], real (&ct)[P], real (&st)[P]) {
+#pragma unroll
+  for (int m = 0; m < P; m++) {
+    cp[m] = geo[(int64_t)(f0 + m) * stride + e];
+    sp[m] = geo[(int64_t)(f0 + P + m) * stride + e];
+    ct[m] = geo[(int64_t)(f0 + 2 * P + m) * stride + e];
+    st[m] = geo[(int64_t)(f0 + 3 * P + m) * stride + e];
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void load_coef(const real* src, real (&v)[ncoef(P)]) {
+#pragma unroll
+  for (int c = 0; c < ncoef(P); c++) v[c] = src[c];
+}
+
+// ---- E0: sort charges into tree order ----------------------------------------
+__global__ void gather_kernel(int64_t n, const int32_t* __restrict__ perm,
+                              const double* __restrict__ q, const vec4* __restrict__ pos,
+                              vec4* __restrict__ src) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    vec4 p = pos[i];
+    p.w = (real)q[perm[i]];
+    src[i] = p;
+  }
+}
+
+// ---- E1: P2M, one warp per leaf ----------------------------------------------
+// M^m_n = sum_i q_i Rt^m_n((x_i - c) / rho)   (Sec. II.C in the scaled basis)
+template <int P>
+__global__ void __launch_bounds__(128) p2m_kernel(int64_t n_leaves, int64_t leaf_off,
+                                                  const int64_t* __restrict__ box_start,
+                                                  const int32_t* __restrict__ box_count,
+                                                  const double* __restrict__ center,
+                                                  const vec4* __restrict__ src,
+                                                  const real* __restrict__ inv_rho,
+                                                  real* __restrict__ M) {
+  constexpr int NC = ncoef(P);
+  const int lane = lane_id();
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves;
+       leaf += warps) {
+    const int64_t g = leaf_off + leaf;
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    const real ir = inv_rho[g];
+    real cx = 0, cy = 0, cz = 0;
+    if (!kF32) {
+      cx = (real)center[3 * g];
+      cy = (real)center[3 * g + 1];
+      cz = (real)center[3 * g + 2];
+    }
+    real acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) acc[c] = real(0);
+    for (int i = lane; i < cnt; i += 32) {
+      const vec4 s = src[start + i];
+      const real x = ((real)s.x - cx) * ir, y = ((real)s.y - cy) * ir, z = ((real)s.z - cz) * ir;
+      const real q = (real)s.w;
+      real R[NC];
+      regular_basis<P>(x, y, z, R, [&](auto nn) {
+        constexpr int n = decltype(nn)::value;
+#pragma unroll
+        for (int c = n * n; c < (n + 1) * (n + 1); c++) acc[c] = fmar(q, R[c], acc[c]);
+      });
+    }
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      real v = acc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[c] = v;
+    }
+    real* out = M + g * ncoef_pad(P);
+#pragma unroll
+    for (int c = 0; c < NC; c++)
+      if ((c & 31) == lane) out[c] = acc[c];
+  }
+}
+
+// ---- E2: M2M, one thread per child box of level l+1 -------------------------
+template <int P>
+__global__ void __launch_bounds__(128) m2m_kernel(int64_t n_child, int64_t child_off,
+                                                  int64_t par_off, int nch,
+                                                  const real* __restrict__ edge,
+                                                  int64_t edge_stride, real* __restrict__ M) {
+  constexpr int NC = ncoef(P);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool active = t < n_child;
+  real v[NC];
+  if (active) {
+    const int64_t g = child_off + t;
+    load_coef<P>(M + g * ncoef_pad(P), v);
+    const real a = edge[0 * edge_stride + g], b = edge[1 * edge_stride + g];
+    real cp[P], sp[P], ct[P], st[P];
+    load_trig<P>(edge, edge_stride, g, 2, cp, sp, ct, st);
+    rotate_to_z<P>(v, cp, sp, ct, st);
+    axial_m2m<P>(v, a, b);
+    rotate_from_z<P>(v, cp, sp, ct, st);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; c++) v[c] = real(0);
+  }
+  // sum the 2^s children (consecutive lanes) of each parent
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    real x = v[c];
+    for (int o = 1; o < nch; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    v[c] = x;
+  }
+  if (active && (t % nch) == 0) {
+    real* out = M + (par_off + t / nch) * ncoef_pad(P);
+#pragma unroll
+    for (int c = 0; c < NC; c++) out[c] = v[c];
+  }
+}
+
+// ---- E3: M2L, persistent; one warp per target box, lanes over its list ------
+template <int P>
+__global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
+                                                  const int32_t* __restrict__ order,
+                                                  const int64_t* __restrict__ off,
+                                                  const int32_t* __restrict__ src,
+                                                  const real* __restrict__ geo, int64_t n_m2l,
+                                                  const real* __restrict__ M,
+                                                  real* __restrict__ Lam,
+                                                  int* __restrict__ counter) {
+  constexpr int NC = ncoef(P);
+  constexpr int NCP = ncoef_pad(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  real* acc = reinterpret_cast<real*>(smem_raw) + (size_t)warp * NC * 32;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_targets) break;
+    const int64_t g = order[t];
+    const int64_t b = off[g], e = off[g + 1];
+#pragma unroll
+    for (int c = 0; c < NC; c++) acc[c * 32 + lane] = real(0);
+    for (int64_t i = b + lane; i < e; i += 32) {
+      const int64_t s = src[i];
+      real v[NC];
+      load_coef<P>(M + s * NCP, v);
+      const real rinv = geo[i], uS = geo[n_m2l + i], uT = geo[2 * n_m2l + i];
+      real cp[P], sp[P], ct[P], st[P];
+      load_trig<P>(geo, n_m2l, i, 3, cp, sp, ct, st);
+      rotate_to_z<P>(v, cp, sp, ct, st);
+      axial_m2l<P>(v, uS, uT, rinv);
+      rotate_from_z<P>(v, cp, sp, ct, st);
+#pragma unroll
+      for (int c = 0; c < NC; c++) acc[c * 32 + lane] += v[c];
+    }
+    __syncwarp();
+    real* out = Lam + g * NCP;
+    for (int c = lane; c < NCP; c += 32) {
+      real s = real(0), err = real(0);
+      if (c < NC) {
+        const real* row = acc + c * 32;
+#pragma unroll 8
+        for (int j = 0; j < 32; j++) {
+          if (kF32) two_sum(s, err, row[(j + lane) & 31]);
+          else s += row[(j + lane) & 31];
+        }
+      }
+      out[c] = s + err;
+    }
+    __syncwarp();
+  }
+}
+
+// ---- E4: L2L, one thread per box of level l; adds into its own M2L local ----
+template <int P>
+__global__ void __launch_bounds__(128) l2l_kernel(int64_t n_box, int64_t off, int64_t par_off,
+                                                  int s, const real* __restrict__ edge,
+                                                  int64_t edge_stride, real* __restrict__ Lam) {
+  constexpr int NC = ncoef(P);
+  constexpr int NCP = ncoef_pad(P);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_box) return;
+  const int64_t g = off + t;
+  const int64_t gp = par_off + (t >> s);
+  real v[NC];
+  load_coef<P>(Lam + gp * NCP, v);
+  const real a = edge[0 * edge_stride + g], b = edge[1 * edge_stride + g];
+  real cp[P], sp[P], ct[P], st[P];
+  load_trig<P>(edge, edge_stride, g, 2, cp, sp, ct, st);
+  rotate_to_z<P>(v, cp, sp, ct, st);
+  axial_l2l<P>(v, a, b);
+  rotate_from_z<P>(v, cp, sp, ct, st);
+  real* out = Lam + g * NCP;
+#pragma unroll
+  for (int c = 0; c < NC; c++) out[c] = out[c] + v[c];
+}
+
+// ---- E6: P2P, persistent; one warp per target leaf ---------------------------
+// Source leaves are staged in shared memory by 1D TMA bulk copies
+// (cp.async.bulk) completing on per-warp mbarriers, double buffered.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Waits for phase `parity` of the barrier; gives up after about a second of
+// clock cycles and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000ll) return false;
+  }
+}
+
+template <bool MASK, bool FIELD, int TPL>
+__device__ __forceinline__ void p2p_tile(const vec4* sb, int scount, const real (&tx)[TPL],
+                                         const real (&ty)[TPL], const real (&tz)[TPL],
+                                         real (&pu)[TPL], real (&fx)[TPL], real (&fy)[TPL],
+                                         real (&fz)[TPL]) {
+#pragma unroll 2
+  for (int j = 0; j < scount; j++) {
+    const vec4 s = sb[j];
+#pragma unroll
+    for (int k = 0; k < TPL; k++) {
+      const real dx = tx[k] - (real)s.x, dy = ty[k] - (real)s.y, dz = tz[k] - (real)s.z;
+      const real r2 = fmar(dz, dz, fmar(dy, dy, dx * dx));
+      real ri;
+      if (kF32) {
+        ri = rsqrtf((float)r2);
+      } else {
+        // FP32 seed refined by two Newton steps for 1/sqrt in FP64
+        double y0 = (double)rsqrtf((float)r2);
+        const double h = 0.5 * (double)r2;
+        y0 = y0 * fma(-h * y0, y0, 1.5);
+        y0 = y0 * fma(-h * y0, y0, 1.5);
+        if (r2 < 1e-30) y0 = (r2 > 0) ? 1.0 / sqrt((double)r2) : 0.0;
+        ri = (real)y0;
+      }
+      if (MASK) ri = (r2 > real(0)) ? ri : real(0);
+      pu[k] = fmar((real)s.w, ri, pu[k]);
+      if (FIELD) {
+        const real w = (real)s.w * ri * ri * ri;
+        fx[k] = fmar(w, dx, fx[k]);
+        fy[k] = fmar(w, dy, fy[k]);
+        fz[k] = fmar(w, dz, fz[k]);
+      }
+    }
+  }
+}
+
+struct P2PArgs {
+  int64_t n_leaves, leaf_off;
+  const int32_t* order;
+  const int64_t* off;
+  const P2PEntry* ent32;
+  const int32_t* ent_src;
+  const int64_t* box_start;
+  const int32_t* box_count;
+  const vec4* src;
+  real* near_u;   // 2 per point (FP32: hi, lo) or 1 (FP64)
+  real* near_f;   // 3 per point (FIELD)
+  int* counter;
+  int* status;
+};
+
+template <int TPL, bool FIELD>
+__global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
+  constexpr int CAP = TPL * 32;
+  constexpr int WARPS = 4;
+  extern __shared__ __align__(128) unsigned char p2p_smem[];
+  vec4 (*sbuf)[2][CAP] = reinterpret_cast<vec4 (*)[2][CAP]>(p2p_smem);  // [WARPS][2][CAP]
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  uint32_t phase = 0;  // bit b: parity of the next completion of barrier b
+  bool ok = true;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= a.n_leaves || !ok) break;
+    const int64_t leaf = a.order[t];
+    const int64_t g = a.leaf_off + leaf;
+    const int64_t tstart = a.box_start[g];
+    const int tcnt = a.box_count[g];
+    real tx0[TPL], ty0[TPL], tz0[TPL];
+#pragma unroll
+    for (int k = 0; k < TPL; k++) {
+      const int i = lane + 32 * k;
+      if (i < tcnt) {
+        const vec4 p = a.src[tstart + i];
+        tx0[k] = (real)p.x;
+        ty0[k] = (real)p.y;
+        tz0[k] = (real)p.z;
+      } else {
+        tx0[k] = ty0[k] = tz0[k] = real(0);
+      }
+    }
+    real hi[TPL], lo[TPL], fx[TPL], fy[TPL], fz[TPL];
+#pragma unroll
+    for (int k = 0; k < TPL; k++) hi[k] = lo[k] = fx[k] = fy[k] = fz[k] = real(0);
+    const int64_t eb = a.off[leaf], ee = a.off[leaf + 1];
+    auto src_leaf = [&](int64_t e) -> int {
+      return kF32 ? (a.ent32[e].src & 0x7fffffff) : a.ent_src[e];
+    };
+    auto issue = [&](int64_t e, int buf) {
+      const int64_t gs = a.leaf_off + src_leaf(e);
+      if (lane == 0) {
+        fence_proxy_async();
+        tma_load_1d(sbuf[warp][buf], a.src + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(vec4)),
+                    &bar[buf]);
+      }
+    };
+    if (eb < ee) issue(eb, 0);
+    for (int64_t e = eb; e < ee; e++) {
+      const int buf = (int)((e - eb) & 1);
+      if (e + 1 < ee) issue(e + 1, buf ^ 1);
+      const bool got = mbar_wait(&bar[buf], (phase >> buf) & 1u);
+      if (!got) {
+        if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+        // copies still in flight into this warp's buffers must land first
+        mbar_wait(&bar[buf], (phase >> buf) & 1u);
+        if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+        ok = false;
+        break;
+      }
+      phase ^= 1u << buf;
+      const int ls = src_leaf(e);
+      const int scount = a.box_count[a.leaf_off + ls];
+      real tx[TPL], ty[TPL], tz[TPL];
+      bool mask;
+      if (kF32) {
+        const P2PEntry en = a.ent32[e];
+        mask = (en.src < 0) || (ls == (int)leaf);
+#pragma unroll
+        for (int k = 0; k < TPL; k++) {
+          tx[k] = tx0[k] + (real)en.dx;
+          ty[k] = ty0[k] + (real)en.dy;
+          tz[k] = tz0[k] + (real)en.dz;
+        }
+      } else {
+        mask = true;
+#pragma unroll
+        for (int k = 0; k < TPL; k++) {
+          tx[k] = tx0[k];
+          ty[k] = ty0[k];
+          tz[k] = tz0[k];
+        }
+      }
+      real pu[TPL], px[TPL], py[TPL], pz[TPL];
+#pragma unroll
+      for (int k = 0; k < TPL; k++) pu[k] = px[k] = py[k] = pz[k] = real(0);
+      if (mask) p2p_tile<true, FIELD, TPL>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz);
+      else p2p_tile<false, FIELD, TPL>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz);
+#pragma unroll
+      for (int k = 0; k < TPL; k++) {
+        if (kF32) two_sum(hi[k], lo[k], pu[k]);
+        else hi[k] += pu[k];
+        fx[k] += px[k];
+        fy[k] += py[k];
+        fz[k] += pz[k];
+      }
+      __syncwarp();
+    }
+    if (!ok) break;
+#pragma unroll
+    for (int k = 0; k < TPL; k++) {
+      const int i = lane + 32 * k;
+      if (i < tcnt) {
+        const int64_t pidx = tstart + i;
+        if (kF32) {
+          a.near_u[2 * pidx] = hi[k];
+          a.near_u[2 * pidx + 1] = lo[k];
+        } else {
+          a.near_u[pidx] = hi[k];
+        }
+        if (FIELD) {
+          a.near_f[3 * pidx] = fx[k];
+          a.near_f[3 * pidx + 1] = fy[k];
+          a.near_f[3 * pidx + 2] = fz[k];
+        }
+      }
+    }
+  }
+}
+
+// ---- E5 + E7: L2P, near + far combination and inverse sort --------------------
+// u = -1/(4 pi) (far + near);  E = -grad u = 1/(4 pi) (grad far - sum q d / r^3).
+template <int P, bool FIELD>
+__global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, int64_t leaf_off,
+                                                  const int64_t* __restrict__ box_start,
+                                                  const int32_t* __restrict__ box_count,
+                                                  const double* __restrict__ center,
+                                                  const int32_t* __restrict__ perm,
+                                                  const vec4* __restrict__ src,
+                                                  const real* __restrict__ inv_rho,
+                                                  const real* __restrict__ Lam,
+                                                  const real* __restrict__ near_u,
+                                                  const real* __restrict__ near_f,
+                                                  double* __restrict__ u_out,
+                                                  double* __restrict__ f_out) {
+  constexpr int NC = ncoef(P);
+  constexpr int NG = P * P;  // gradient coefficients reach degree P-1
+  __shared__ real sL[4][NC];
+  __shared__ real sG[4][FIELD ? 3 * NG : 1];
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves;
+       leaf += warps) {
+    const int64_t g = leaf_off + leaf;
+    const real* L = Lam + g * ncoef_pad(P);
+    for (int c = lane; c < NC; c += 32) sL[warp][c] = L[c];
+    __syncwarp();
+    if (FIELD) {
+      // per-leaf differentiated locals: d/dx, d/dy, d/dz of sum w L Rt as
+      // sums of G Rt over degrees < P (ladder relations of the regular basis)
+      for (int id = lane; id < NG; id += 32) {
+        int n1 = 0;
+        while ((n1 + 1) * (n1 + 1) <= id) n1++;
+        const int m = id - n1 * n1 - n1;
+        const int n = n1 + 1;
+        const int mp = m < 0 ? -m : m;
+        const real kp = sqrt((real)((n + mp + 1) * (n + mp)));
+        const real km = sqrt((real)((n - mp + 1) * (n - mp)));
+        const real kz = sqrt((real)((n - mp) * (n + mp)));
+        auto Lv = [&](int mm) -> real { return sL[warp][n * n + n + mm]; };
+        real gx, gy, gz;
+        if (m >= 0) {
+          gx = kp * Lv(mp + 1) - (mp >= 1 ? km * Lv(mp - 1) : real(0));
+          gy = -(kp * Lv(-(mp + 1)) + (mp >= 2 ? km * Lv(-(mp - 1)) : real(0)));
+          gz = (mp == 0 ? real(1) : real(2)) * kz * Lv(mp);
+        } else {
+          gx = kp * Lv(-(mp + 1)) - (mp >= 2 ? km * Lv(-(mp - 1)) : real(0));
+          gy = kp * Lv(mp + 1) + km * Lv(mp - 1);
+          gz = real(2) * kz * Lv(-mp);
+        }
+        sG[warp][id] = gx;
+        sG[warp][NG + id] = gy;
+        sG[warp][2 * NG + id] = gz;
+      }
+      __syncwarp();
+    }
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    const real ir = inv_rho[g];
+    real cx = 0, cy = 0, cz = 0;
+    if (!kF32) {
+      cx = (real)center[3 * g];
+      cy = (real)center[3 * g + 1];
+      cz = (real)center[3 * g + 2];
+    }
+    for (int i = lane; i < cnt; i += 32) {
+      const int64_t pidx = start + i;
+      const vec4 s = src[pidx];
+      const real x = ((real)s.x - cx) * ir, y = ((real)s.y - cy) * ir, z = ((real)s.z - cz) * ir;
+      real u0 = real(0), um = real(0), gx = real(0), gy = real(0), gz = real(0);
+      real R[NC];
+      regular_basis<P>(x, y, z, R, [&](auto nn) {
+        constexpr int n = decltype(nn)::value;
+        u0 = fmar(sL[warp][n * n + n], R[n * n + n], u0);
+#pragma unroll
+        for (int c = n * n; c < (n + 1) * (n + 1); c++)
+          if (c != n * n + n) um = fmar(sL[warp][c], R[c], um);
+        if (FIELD && n < P) {
+#pragma unroll
+          for (int c = n * n; c < (n + 1) * (n + 1); c++) {
+            gx = fmar(sG[warp][c], R[c], gx);
+            gy = fmar(sG[warp][NG + c], R[c], gy);
+            gz = fmar(sG[warp][2 * NG + c], R[c], gz);
+          }
+        }
+      });
+      const double far = (double)u0 + 2.0 * (double)um;
+      double nearv = kF32 ? (double)near_u[2 * pidx] + (double)near_u[2 * pidx + 1] : (double)near_u[pidx];
+      const int64_t o = perm[pidx];
+      if (u_out) u_out[o] = -kInv4Pi * (far + nearv);
+      if (FIELD) {
+        const double irr = (double)ir;
+        f_out[3 * o] = kInv4Pi * ((double)gx * irr - (double)near_f[3 * pidx]);
+        f_out[3 * o + 1] = kInv4Pi * ((double)gy * irr - (double)near_f[3 * pidx + 1]);
+        f_out[3 * o + 2] = kInv4Pi * ((double)gz * irr - (double)near_f[3 * pidx + 2]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---- host side ----------------------------------------------------------------
+struct Ptrs {
+  vec4* pos;
+  vec4* src;
+  const real* inv_rho;
+  const real* geo;
+  const real* m2m;
+  const real* l2l;
+  real* M;
+  real* Lam;
+};
+
+Ptrs ptrs(const fmm_tree* t);
+
+template <int P>
+void run_far(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+  const int s = t->s, L = t->L;
+  const int nch = 1 << s;
+  auto loff = [&](int l) {
+    int64_t o = 0;
+    for (int i = 0; i < l; i++) o += (int64_t)1 << (s * i);
+    return o;
+  };
+  const int64_t leaf_off = loff(L);
+  p2m_kernel<P><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
+      t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, pp.src, pp.inv_rho, pp.M);
+  FMM_LAUNCH_CHECK();
+  for (int l = L - 1; l >= 0; l--) {
+    const int64_t nchild = (int64_t)1 << (s * (l + 1));
+    m2m_kernel<P><<<grid_for(nchild, 128, 1 << 30), 128, 0, st>>>(nchild, loff(l + 1), loff(l), nch,
+                                                                 pp.m2m, t->n_boxes, pp.M);
+    FMM_LAUNCH_CHECK();
+  }
+  const size_t smem = (size_t)4 * ncoef(P) * 32 * sizeof(real);
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  FMM_CUDA_TRY(cudaMemsetAsync(t->counters, 0, sizeof(int), st));
+  int dev = 0, nsm = 0, occ = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, m2l_kernel<P>, 128, smem));
+  if (occ < 1) occ = 1;
+  int64_t blocks = (int64_t)nsm * occ;
+  const int64_t need = (t->n_boxes + 3) / 4;
+  if (blocks > need) blocks = need;
+  m2l_kernel<P><<<(int)blocks, 128, smem, st>>>(t->n_boxes, t->m2l_order, t->m2l_off, t->m2l_src,
+                                                pp.geo, t->n_m2l, pp.M, pp.Lam, t->counters);
+  FMM_LAUNCH_CHECK();
+  for (int l = 1; l <= L; l++) {
+    const int64_t nb = (int64_t)1 << (s * l);
+    l2l_kernel<P><<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(nb, loff(l), loff(l - 1), s, pp.l2l,
+                                                             t->n_boxes, pp.Lam);
+    FMM_LAUNCH_CHECK();
+  }
+}
+
+template <int P>
+void run_l2p(const fmm_tree* t, const Ptrs& pp, const real* near_u, const real* near_f, double* u,
+             double* field, cudaStream_t st) {
+  int64_t leaf_off = 0;
+  for (int i = 0; i < t->L; i++) leaf_off += (int64_t)1 << (t->s * i);
+  if (field)
+    l2p_kernel<P, true><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
+        t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
+        pp.Lam, near_u, near_f, u, field);
+  else
+    l2p_kernel<P, false><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
+        t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
+        pp.Lam, near_u, near_f, u, field);
+  FMM_LAUNCH_CHECK();
+}
+
+template <int TPL>
+void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool field,
+                 cudaStream_t st) {
+  P2PArgs a;
+  a.n_leaves = t->n_leaves;
+  a.leaf_off = 0;
+  for (int i = 0; i < t->L; i++) a.leaf_off += (int64_t)1 << (t->s * i);
+  a.order = t->leaf_order;
+  a.off = t->p2p_off;
+  a.ent32 = t->p2p32;
+  a.ent_src = t->p2p_src;
+  a.box_start = t->box_start;
+  a.box_count = t->box_count;
+  a.src = pp.src;
+  a.near_u = near_u;
+  a.near_f = near_f;
+  a.counter = t->counters + 1;
+  a.status = t->status;
+  FMM_CUDA_TRY(cudaMemsetAsync(t->counters + 1, 0, sizeof(int), st));
+  const size_t smem = (size_t)4 * 2 * TPL * 32 * sizeof(vec4);
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  int dev = 0, nsm = 0, occ = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (field) FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_kernel<TPL, true>, 128, smem));
+  else FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_kernel<TPL, false>, 128, smem));
+  if (occ < 1) occ = 1;
+  int64_t blocks = (int64_t)nsm * occ;
+  const int64_t need = (t->n_leaves + 3) / 4;
+  if (blocks > need) blocks = need;
+  if (field) p2p_kernel<TPL, true><<<(int)blocks, 128, smem, st>>>(a);
+  else p2p_kernel<TPL, false><<<(int)blocks, 128, smem, st>>>(a);
+  FMM_LAUNCH_CHECK();
+}
+
+void run_p2p(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool field, cudaStream_t st) {
+  if (t->max_leaf <= 32) run_p2p_tpl<1>(t, pp, near_u, near_f, field, st);
+  else if (t->max_leaf <= 64) run_p2p_tpl<2>(t, pp, near_u, near_f, field, st);
+  else if (t->max_leaf <= 128) run_p2p_tpl<4>(t, pp, near_u, near_f, field, st);
+  else run_p2p_tpl<8>(t, pp, near_u, near_f, field, st);
+}
+
+template <class F>
+void dispatch_p(int p, F&& f) {
+  switch (p) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 9: f(std::integral_constant<int, 9>{}); break;
+    case 10: f(std::integral_constant<int, 10>{}); break;
+    default: set_error("unsupported expansion order %d", p); throw Fail{FMM_ERR_INVALID_ARG};
+  }
+}
+
+void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
+  Ptrs pp = ptrs(t);
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->perm, q, pp.pos, pp.src);
+  FMM_LAUNCH_CHECK();
+  // near field first (largest kernel), then the far-field chain
+  real* near_u = reinterpret_cast<real*>(t->near_u);
+  real* near_f = reinterpret_cast<real*>(t->near_f);
+  run_p2p(t, pp, near_u, near_f, field != nullptr, st);
+  dispatch_p(t->prm.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    run_far<P>(t, pp, st);
+    run_l2p<P>(t, pp, near_u, near_f, u, field, st);
+  });
+}
+
+}  // namespace
+}  // namespace fmm

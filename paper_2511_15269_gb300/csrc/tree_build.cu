@@ -1,0 +1,1161 @@
+// Device construction of the FMM hierarchy (Sec. II.A, II.B, Listing 2):
+// median-split 2^s-tree, box geometry, level-marching interaction lists and
+// the rotation coefficients of every translation.
+//
+// Tree.  Each bisection round splits every segment of the current tree order
+// in two: the axis of largest extent of the segment's bounding box (ties to
+// the lowest axis), then the ceil(n/2) points smallest in (coordinate, original
+// index) form the lower child.  The split point is found by radix selection
+// on 96-bit keys (order-preserving 64-bit image of the FP64 coordinate, then
+// the 32-bit index), 8 bits per pass with early exit once the bin holding the
+// pivot is a single point; points are then partitioned around it.  Segments
+// small enough for one CTA (kSmallCap points) finish all their remaining
+// rounds inside that CTA with bitonic sorts in shared memory, and every leaf
+// is finally sorted by original index.  The result depends only on the point
+// sets, never on the order inside a segment, so it is deterministic.
+//
+// Geometry.  Bounding boxes are exact min/max; centre = (lo + hi) * 0.5 and
+// radius = sqrt((ex^2 + ey^2) + ez^2) * 0.5 with every FP64 operation rounded
+// separately (no contraction), as is the well-separation test
+// R + theta r <= theta d (Eq. 4, with d > 0 required).
+//
+// Lists.  Level march (Sec. II.B): start from (root, root); each step moves
+// well-separated candidate pairs to the M2L list and replaces the others by
+// the children of the side whose level has the larger average radius (ties:
+// source, or target with FMM_TIE_TARGET); pairs left when both sides reach
+// the leaf level form the near field.  Average radii are adjacent-pair sums
+// repeated down to one value, divided by the box count.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fmm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 8;
+constexpr int kChunk = kThreads * kItems;
+
+__host__ __device__ inline int64_t level_offset(int l, int s) {
+  int64_t o = 0;
+  for (int i = 0; i < l; i++) o += (int64_t)1 << (s * i);
+  return o;
+}
+
+__device__ __forceinline__ unsigned long long okey(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_inv(unsigned long long k) {
+  unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// index of the segment containing position i: largest j with starts[j] <= i
+__device__ __forceinline__ int seg_of(const int64_t* starts, int nseg, int64_t i) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---- input: SoA copy with -0.0 -> +0.0, finiteness check ----------------------
+__global__ void canon_kernel(const double* __restrict__ pos, int64_t n, double* __restrict__ X,
+                             int32_t* __restrict__ idx, int* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int a = 0; a < 3; a++) {
+      double v = __dadd_rn(pos[3 * i + a], 0.0);
+      if (!isfinite(v)) atomicOr(bad, 1);
+      X[a * n + i] = v;
+    }
+    idx[i] = (int32_t)i;
+  }
+}
+
+// ---- segment boundaries of round r+1 from round r (closed form) --------------
+__global__ void split_starts_kernel(const int64_t* __restrict__ st, int nseg, int64_t* __restrict__ nx) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nseg) {
+    int64_t a = st[j], b = st[j + 1];
+    nx[2 * j] = a;
+    nx[2 * j + 1] = a + (b - a + 1) / 2;
+    if (j == nseg - 1) nx[2 * nseg] = b;
+  }
+}
+
+// ---- bounding boxes of segments (large rounds) ---------------------------------
+__global__ void __launch_bounds__(kThreads) seg_bbox_kernel(const double* __restrict__ X, int64_t n,
+                                                            const int64_t* __restrict__ starts, int nseg,
+                                                            unsigned long long* __restrict__ bmin,
+                                                            unsigned long long* __restrict__ bmax) {
+  const int64_t c0 = (int64_t)blockIdx.x * kChunk;
+  const int64_t c1 = min(c0 + kChunk, n);
+  if (c0 >= n) return;
+  const int s0 = seg_of(starts, nseg, c0), s1 = seg_of(starts, nseg, c1 - 1);
+  if (s0 == s1) {
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += kThreads)
+      for (int a = 0; a < 3; a++) {
+        unsigned long long k = okey(X[a * n + i]);
+        mn[a] = min(mn[a], k);
+        mx[a] = max(mx[a], k);
+      }
+    __shared__ unsigned long long sm[6][kThreads / 32];
+    for (int a = 0; a < 3; a++) {
+      for (int o = 16; o > 0; o >>= 1) {
+        mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+        mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+      }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+      for (int a = 0; a < 3; a++) {
+        sm[a][warp] = mn[a];
+        sm[3 + a][warp] = mx[a];
+      }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      int a = threadIdx.x;
+      unsigned long long m0 = ~0ull, m1 = 0;
+      for (int w = 0; w < kThreads / 32; w++) {
+        m0 = min(m0, sm[a][w]);
+        m1 = max(m1, sm[3 + a][w]);
+      }
+      atomicMin(&bmin[3 * s0 + a], m0);
+      atomicMax(&bmax[3 * s0 + a], m1);
+    }
+  } else {
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += kThreads) {
+      int sg = seg_of(starts, nseg, i);
+      for (int a = 0; a < 3; a++) {
+        unsigned long long k = okey(X[a * n + i]);
+        atomicMin(&bmin[3 * sg + a], k);
+        atomicMax(&bmax[3 * sg + a], k);
+      }
+    }
+  }
+}
+
+// Radix-select state of one segment.
+struct Sel {
+  unsigned long long phi;  // prefix of the 96-bit key (left aligned), high word
+  unsigned int plo;        // low word
+  int bits;                // prefix bits fixed so far
+  long long krem;          // rank of the pivot among keys with this prefix
+  int resolved;            // 1 once the prefix names exactly one point
+  int axis;
+};
+
+__global__ void seg_axis_kernel(const unsigned long long* __restrict__ bmin,
+                                const unsigned long long* __restrict__ bmax,
+                                const int64_t* __restrict__ starts, int nseg, Sel* __restrict__ sel) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nseg) return;
+  double e[3];
+  for (int a = 0; a < 3; a++) e[a] = __dsub_rn(okey_inv(bmax[3 * j + a]), okey_inv(bmin[3 * j + a]));
+  int ax = 0;
+  if (e[1] > e[ax]) ax = 1;
+  if (e[2] > e[ax]) ax = 2;
+  const int64_t cnt = starts[j + 1] - starts[j];
+  Sel s;
+  s.phi = 0;
+  s.plo = 0;
+  s.bits = 0;
+  s.krem = (cnt + 1) / 2 - 1;
+  s.resolved = (cnt <= 1);
+  s.axis = ax;
+  sel[j] = s;
+}
+
+__device__ __forceinline__ unsigned digit_of(unsigned long long hi, unsigned lo, int d) {
+  return d < 8 ? (unsigned)((hi >> (56 - 8 * d)) & 0xffu) : ((lo >> (24 - 8 * (d - 8))) & 0xffu);
+}
+// -1, 0, 1: top `bits` bits of (hi, lo) below, equal to, above the prefix
+__device__ __forceinline__ int cmp_prefix(unsigned long long hi, unsigned lo, const Sel& s) {
+  const int b = s.bits;
+  if (b <= 64) {
+    unsigned long long m = (b == 0) ? 0ull : (~0ull << (64 - b));
+    unsigned long long kh = hi & m;
+    return kh < s.phi ? -1 : (kh > s.phi ? 1 : 0);
+  }
+  if (hi != s.phi) return hi < s.phi ? -1 : 1;
+  unsigned m = (b >= 96) ? ~0u : (~0u << (96 - b));
+  unsigned kl = lo & m;
+  return kl < s.plo ? -1 : (kl > s.plo ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(kThreads) radix_hist_kernel(const double* __restrict__ X,
+                                                              const int32_t* __restrict__ idx, int64_t n,
+                                                              const int64_t* __restrict__ starts, int nseg,
+                                                              const Sel* __restrict__ sel, int d,
+                                                              unsigned* __restrict__ hist) {
+  const int64_t c0 = (int64_t)blockIdx.x * kChunk;
+  const int64_t c1 = min(c0 + kChunk, n);
+  if (c0 >= n) return;
+  const int s0 = seg_of(starts, nseg, c0), s1 = seg_of(starts, nseg, c1 - 1);
+  __shared__ unsigned sh[256];
+  if (s0 == s1) {
+    const Sel s = sel[s0];
+    if (s.resolved) return;
+    for (int i = threadIdx.x; i < 256; i += kThreads) sh[i] = 0;
+    __syncthreads();
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += kThreads) {
+      unsigned long long hi = okey(X[s.axis * n + i]);
+      unsigned lo = (unsigned)idx[i];
+      if (cmp_prefix(hi, lo, s) == 0) atomicAdd(&sh[digit_of(hi, lo, d)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += kThreads)
+      if (sh[i]) atomicAdd(&hist[(size_t)s0 * 256 + i], sh[i]);
+  } else {
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += kThreads) {
+      int sg = seg_of(starts, nseg, i);
+      const Sel s = sel[sg];
+      if (s.resolved) continue;
+      unsigned long long hi = okey(X[s.axis * n + i]);
+      unsigned lo = (unsigned)idx[i];
+      if (cmp_prefix(hi, lo, s) == 0) atomicAdd(&hist[(size_t)sg * 256 + digit_of(hi, lo, d)], 1u);
+    }
+  }
+}
+
+__global__ void radix_select_kernel(Sel* __restrict__ sel, int nseg, int d, unsigned* __restrict__ hist,
+                                    int* __restrict__ unresolved) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nseg) return;
+  Sel s = sel[j];
+  unsigned* h = hist + (size_t)j * 256;
+  if (!s.resolved) {
+    long long cum = 0;
+    int dig = 255;
+    unsigned cnt = 0;
+    for (int b = 0; b < 256; b++) {
+      if (cum + h[b] > s.krem) {
+        dig = b;
+        cnt = h[b];
+        break;
+      }
+      cum += h[b];
+    }
+    s.krem -= cum;
+    if (d < 8) s.phi |= (unsigned long long)dig << (56 - 8 * d);
+    else s.plo |= (unsigned)dig << (24 - 8 * (d - 8));
+    s.bits += 8;
+    if (cnt <= 1) s.resolved = 1;
+    else atomicOr(unresolved, 1);
+    sel[j] = s;
+  }
+  for (int b = 0; b < 256; b++) h[b] = 0;
+}
+
+// Points with key prefix <= the pivot's go to the lower child.
+__global__ void __launch_bounds__(kThreads) partition_kernel(const double* __restrict__ X,
+                                                             const int32_t* __restrict__ idx, int64_t n,
+                                                             const int64_t* __restrict__ starts, int nseg,
+                                                             const Sel* __restrict__ sel,
+                                                             unsigned long long* __restrict__ ctr,
+                                                             double* __restrict__ Xo,
+                                                             int32_t* __restrict__ idxo) {
+  const int64_t c0 = (int64_t)blockIdx.x * kChunk;
+  const int64_t c1 = min(c0 + kChunk, n);
+  if (c0 >= n) return;
+  const int s0 = seg_of(starts, nseg, c0), s1 = seg_of(starts, nseg, c1 - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (s0 == s1) {
+    const Sel s = sel[s0];
+    const int64_t a = starts[s0], b = starts[s0 + 1];
+    const int64_t half = (b - a + 1) / 2;
+    __shared__ unsigned wl[kThreads / 32], wu[kThreads / 32];
+    __shared__ unsigned long long base_lo, base_hi;
+    for (int64_t it = c0; it < c1; it += kThreads) {
+      const int64_t i = it + threadIdx.x;
+      const bool valid = i < c1;
+      bool lower = false;
+      if (valid) {
+        unsigned long long hi = okey(X[s.axis * n + i]);
+        lower = cmp_prefix(hi, (unsigned)idx[i], s) <= 0;
+      }
+      const unsigned bl = __ballot_sync(0xffffffffu, valid && lower);
+      const unsigned bu = __ballot_sync(0xffffffffu, valid && !lower);
+      if (lane == 0) {
+        wl[warp] = __popc(bl);
+        wu[warp] = __popc(bu);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned tl = 0, tu = 0;
+        for (int w = 0; w < kThreads / 32; w++) {
+          unsigned x = wl[w], y = wu[w];
+          wl[w] = tl;
+          wu[w] = tu;
+          tl += x;
+          tu += y;
+        }
+        base_lo = atomicAdd(&ctr[2 * s0], (unsigned long long)tl);
+        base_hi = atomicAdd(&ctr[2 * s0 + 1], (unsigned long long)tu);
+      }
+      __syncthreads();
+      if (valid) {
+        const unsigned mask_lt = (1u << lane) - 1u;
+        int64_t dst = lower ? a + (int64_t)base_lo + wl[warp] + __popc(bl & mask_lt)
+                            : a + half + (int64_t)base_hi + wu[warp] + __popc(bu & mask_lt);
+        for (int ax = 0; ax < 3; ax++) Xo[ax * n + dst] = X[ax * n + i];
+        idxo[dst] = idx[i];
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += kThreads) {
+      const int sg = seg_of(starts, nseg, i);
+      const Sel s = sel[sg];
+      const int64_t a = starts[sg], b = starts[sg + 1];
+      const int64_t half = (b - a + 1) / 2;
+      unsigned long long hi = okey(X[s.axis * n + i]);
+      const bool lower = cmp_prefix(hi, (unsigned)idx[i], s) <= 0;
+      int64_t dst = lower ? a + (int64_t)atomicAdd(&ctr[2 * sg], 1ull)
+                          : a + half + (int64_t)atomicAdd(&ctr[2 * sg + 1], 1ull);
+      for (int ax = 0; ax < 3; ax++) Xo[ax * n + dst] = X[ax * n + i];
+      idxo[dst] = idx[i];
+    }
+  }
+}
+
+// ---- small segments: all remaining rounds and the leaf sort in one CTA ---------
+constexpr int kSmallThreads = 512;
+
+__device__ void bitonic_sort(unsigned long long* kh, unsigned long long* kl, int size) {
+  for (int k = 2; k <= size; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < size; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool asc = (i & k) == 0;
+          const bool gt = (kh[i] > kh[ixj]) || (kh[i] == kh[ixj] && kl[i] > kl[ixj]);
+          if (gt == asc) {
+            unsigned long long t = kh[i];
+            kh[i] = kh[ixj];
+            kh[ixj] = t;
+            t = kl[i];
+            kl[i] = kl[ixj];
+            kl[ixj] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
+    const double* __restrict__ X, const int32_t* __restrict__ idx, int64_t n,
+    const int64_t* __restrict__ starts, int rounds, double* __restrict__ Xo, int32_t* __restrict__ perm) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int64_t g0 = starts[blockIdx.x], g1 = starts[blockIdx.x + 1];
+  const int cnt = (int)(g1 - g0);
+  int size = 1;
+  while (size < cnt) size <<= 1;
+  const int nsub_max = 1 << rounds;
+  // 8-byte items first, then 4-byte ones
+  unsigned long long* kh = reinterpret_cast<unsigned long long*>(sm);
+  unsigned long long* kl = kh + kSmallCap;
+  double* xa = reinterpret_cast<double*>(kl + kSmallCap);  // 3 x kSmallCap
+  double* xb = xa + 3 * kSmallCap;                         // 3 x kSmallCap
+  unsigned long long* bb = reinterpret_cast<unsigned long long*>(xb + 3 * kSmallCap);  // 6 x nsub_max
+  int32_t* ia = reinterpret_cast<int32_t*>(bb + 6 * nsub_max);
+  int32_t* ib = ia + kSmallCap;
+  int* st = ib + kSmallCap;                                // nsub_max + 2
+  int* axis = st + nsub_max + 2;                           // nsub_max
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    for (int a = 0; a < 3; a++) xa[a * kSmallCap + i] = X[a * n + g0 + i];
+    ia[i] = idx[g0 + i];
+  }
+  if (threadIdx.x == 0) {
+    st[0] = 0;
+    st[1] = cnt;
+  }
+  __syncthreads();
+  for (int r = 0; r < rounds; r++) {
+    const int nsub = 1 << r;
+    for (int j = threadIdx.x; j < nsub; j += blockDim.x)
+      for (int a = 0; a < 3; a++) {
+        bb[6 * j + a] = ~0ull;
+        bb[6 * j + 3 + a] = 0ull;
+      }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      int lo = 0, hi = nsub - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (st[mid] <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      for (int a = 0; a < 3; a++) {
+        unsigned long long k = okey(xa[a * kSmallCap + i]);
+        atomicMin(&bb[6 * lo + a], k);
+        atomicMax(&bb[6 * lo + 3 + a], k);
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nsub; j += blockDim.x) {
+      double e[3];
+      for (int a = 0; a < 3; a++) e[a] = __dsub_rn(okey_inv(bb[6 * j + 3 + a]), okey_inv(bb[6 * j + a]));
+      int ax = 0;
+      if (e[1] > e[ax]) ax = 1;
+      if (e[2] > e[ax]) ax = 2;
+      axis[j] = ax;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < size; i += blockDim.x) {
+      if (i < cnt) {
+        int lo = 0, hi = nsub - 1;
+        while (lo < hi) {
+          int mid = (lo + hi + 1) >> 1;
+          if (st[mid] <= i) lo = mid;
+          else hi = mid - 1;
+        }
+        unsigned long long k = okey(xa[axis[lo] * kSmallCap + i]);
+        kh[i] = ((unsigned long long)lo << 52) | (k >> 12);
+        kl[i] = ((k & 0xfffull) << 44) | ((unsigned long long)(uint32_t)ia[i] << 12) | (unsigned long long)i;
+      } else {
+        kh[i] = ~0ull;
+        kl[i] = ~0ull;
+      }
+    }
+    __syncthreads();
+    bitonic_sort(kh, kl, size);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const int slot = (int)(kl[i] & 0xfffull);
+      for (int a = 0; a < 3; a++) xb[a * kSmallCap + i] = xa[a * kSmallCap + slot];
+      ib[i] = ia[slot];
+    }
+    __syncthreads();
+    {
+      double* t = xa;
+      xa = xb;
+      xb = t;
+      int32_t* u = ia;
+      ia = ib;
+      ib = u;
+    }
+    // next round's boundaries: ceil half to the lower child
+    if (threadIdx.x == 0) {
+      for (int j = nsub - 1; j >= 0; j--) {
+        const int a = st[j], b = st[j + 1];
+        st[2 * j + 2] = b;
+        st[2 * j + 1] = a + (b - a + 1) / 2;
+        st[2 * j] = a;
+      }
+    }
+    __syncthreads();
+  }
+  // leaves in ascending original index (Listing 2, last line)
+  const int nleaf = 1 << rounds;
+  for (int i = threadIdx.x; i < size; i += blockDim.x) {
+    if (i < cnt) {
+      int lo = 0, hi = nleaf - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (st[mid] <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      kh[i] = ((unsigned long long)lo << 32) | (unsigned long long)(uint32_t)ia[i];
+      kl[i] = (unsigned long long)i;
+    } else {
+      kh[i] = ~0ull;
+      kl[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  bitonic_sort(kh, kl, size);
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int slot = (int)kl[i];
+    for (int a = 0; a < 3; a++) Xo[a * n + g0 + i] = xa[a * kSmallCap + slot];
+    perm[g0 + i] = ia[slot];
+  }
+}
+
+size_t small_smem_bytes(int rounds) {
+  const size_t nsub = (size_t)1 << rounds;
+  return (size_t)kSmallCap * (8 + 8 + 24 + 24 + 4 + 4) + nsub * 48 + sizeof(int) * (2 * nsub + 2);
+}
+
+// ---- geometry --------------------------------------------------------------------
+// leaf bounding boxes: one warp per leaf
+__global__ void leaf_bbox_kernel(const double* __restrict__ X, int64_t n, const int64_t* __restrict__ bs,
+                                 const int32_t* __restrict__ bc, int64_t leaf_off, int64_t n_leaves,
+                                 double* __restrict__ lo, double* __restrict__ hi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= n_leaves) return;
+  const int64_t g = leaf_off + w;
+  const int64_t a = bs[g];
+  const int c = bc[g];
+  for (int ax = 0; ax < 3; ax++) {
+    double mn = INFINITY, mx = -INFINITY;
+    for (int i = lane; i < c; i += 32) {
+      double v = X[ax * n + a + i];
+      mn = fmin(mn, v);
+      mx = fmax(mx, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+      lo[3 * g + ax] = mn;
+      hi[3 * g + ax] = mx;
+    }
+  }
+}
+
+// parent boxes: union of the 2^s children (exact)
+__global__ void parent_bbox_kernel(int64_t nb, int64_t off, int64_t coff, int nch, double* __restrict__ lo,
+                                   double* __restrict__ hi) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const int64_t g = off + b;
+  for (int ax = 0; ax < 3; ax++) {
+    double mn = INFINITY, mx = -INFINITY;
+    for (int c = 0; c < nch; c++) {
+      const int64_t gc = coff + b * nch + c;
+      mn = fmin(mn, lo[3 * gc + ax]);
+      mx = fmax(mx, hi[3 * gc + ax]);
+    }
+    lo[3 * g + ax] = mn;
+    hi[3 * g + ax] = mx;
+  }
+}
+
+__global__ void centre_radius_kernel(int64_t nbox, const double* __restrict__ lo, const double* __restrict__ hi,
+                                     double* __restrict__ center, double* __restrict__ radius,
+                                     float* __restrict__ ir32, double* __restrict__ ir64) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nbox) return;
+  double e[3];
+  for (int a = 0; a < 3; a++) {
+    center[3 * g + a] = __dmul_rn(__dadd_rn(lo[3 * g + a], hi[3 * g + a]), 0.5);
+    e[a] = __dsub_rn(hi[3 * g + a], lo[3 * g + a]);
+  }
+  double d2 = __dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1]));
+  d2 = __dadd_rn(d2, __dmul_rn(e[2], e[2]));
+  const double r = __dmul_rn(__dsqrt_rn(d2), 0.5);
+  radius[g] = r;
+  ir64[g] = (r > 0.0) ? 1.0 / r : 0.0;
+  ir32[g] = (r > 1e-30) ? (float)(1.0 / r) : 0.0f;
+}
+
+// boxes' start offsets for one level from the segment boundaries of its round
+__global__ void box_range_kernel(const int64_t* __restrict__ st, int64_t nb, int64_t off,
+                                 int64_t* __restrict__ bs, int32_t* __restrict__ bc) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  bs[off + b] = st[b];
+  bc[off + b] = (int32_t)(st[b + 1] - st[b]);
+}
+
+// adjacent-pair sums, one stage
+__global__ void pair_sum_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t m) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) out[i] = __dadd_rn(in[2 * i], in[2 * i + 1]);
+}
+
+// ---- lists -----------------------------------------------------------------------
+__device__ __forceinline__ bool well_separated(const double* __restrict__ c, const double* __restrict__ rad,
+                                               int64_t gs, int64_t gt, double theta) {
+  const double dx = __dsub_rn(c[3 * gs], c[3 * gt]);
+  const double dy = __dsub_rn(c[3 * gs + 1], c[3 * gt + 1]);
+  const double dz = __dsub_rn(c[3 * gs + 2], c[3 * gt + 2]);
+  double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  d2 = __dadd_rn(d2, __dmul_rn(dz, dz));
+  const double d = __dsqrt_rn(d2);
+  const double rs = rad[gs], rt = rad[gt];
+  const double R = rs > rt ? rs : rt;
+  const double r = rs > rt ? rt : rs;
+  const double lhs = __dadd_rn(R, __dmul_rn(theta, r));
+  const double rhs = __dmul_rn(theta, d);
+  return d > 0.0 && lhs <= rhs;
+}
+
+__global__ void ws_kernel(const int32_t* __restrict__ ct, const int32_t* __restrict__ cs, int64_t nc,
+                          int64_t offt, int64_t offs, const double* __restrict__ center,
+                          const double* __restrict__ radius, double theta, int64_t* __restrict__ fws,
+                          int64_t* __restrict__ fkeep) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
+    const bool w = well_separated(center, radius, offs + cs[e], offt + ct[e], theta);
+    fws[e] = w ? 1 : 0;
+    fkeep[e] = w ? 0 : 1;
+  }
+}
+
+__global__ void emit_kernel(const int32_t* __restrict__ ct, const int32_t* __restrict__ cs, int64_t nc,
+                            int64_t offt, int64_t offs, const int64_t* __restrict__ fws,
+                            const int64_t* __restrict__ pws, const int64_t* __restrict__ pkeep,
+                            int32_t* __restrict__ mt, int32_t* __restrict__ ms, int32_t* __restrict__ kt,
+                            int32_t* __restrict__ ks) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
+    if (fws[e]) {
+      mt[pws[e]] = (int32_t)(offt + ct[e]);
+      ms[pws[e]] = (int32_t)(offs + cs[e]);
+    } else {
+      kt[pkeep[e]] = ct[e];
+      ks[pkeep[e]] = cs[e];
+    }
+  }
+}
+
+__device__ __forceinline__ int64_t lower_bound32(const int32_t* a, int64_t n, int32_t v) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// children of the advanced side; the result stays sorted by (target, source)
+__global__ void expand_kernel(const int32_t* __restrict__ kt, const int32_t* __restrict__ ks, int64_t nk,
+                              int nch, int adv_src, int32_t* __restrict__ ct, int32_t* __restrict__ cs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = kt[e], s = ks[e];
+    if (adv_src) {
+      for (int c = 0; c < nch; c++) {
+        ct[nch * e + c] = t;
+        cs[nch * e + c] = nch * s + c;
+      }
+    } else {
+      const int64_t first = lower_bound32(kt, nk, t);
+      const int64_t last = lower_bound32(kt, nk, t + 1);
+      const int64_t k = last - first;
+      for (int c = 0; c < nch; c++) {
+        const int64_t o = nch * first + c * k + (e - first);
+        ct[o] = nch * t + c;
+        cs[o] = s;
+      }
+    }
+  }
+}
+
+__global__ void count_kernel(const int32_t* __restrict__ key, int64_t n, int64_t* __restrict__ cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[key[e]]), 1ull);
+}
+
+__global__ void m2l_scatter_kernel(const int32_t* __restrict__ mt, const int32_t* __restrict__ ms, int64_t nm,
+                                   const int64_t* __restrict__ off, const int64_t* __restrict__ fill,
+                                   int32_t* __restrict__ out_t, int32_t* __restrict__ out_s) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nm; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = mt[e];
+    const int64_t first = lower_bound32(mt, nm, g);
+    const int64_t pos = off[g] + fill[g] + (e - first);
+    out_t[pos] = g;
+    out_s[pos] = ms[e];
+  }
+}
+
+__global__ void m2l_fill_kernel(const int32_t* __restrict__ mt, int64_t nm, int64_t* __restrict__ fill) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nm; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = mt[e];
+    if (e == 0 || mt[e - 1] != g) fill[g] += lower_bound32(mt, nm, g + 1) - e;
+  }
+}
+
+// ---- rotation coefficients -----------------------------------------------------------
+// For t = c_old - c_new: 1/r and cos/sin of the multiples of the polar angle
+// theta and azimuth phi of t, in FP64 by angle addition, stored in FP64 and
+// rounded to FP32.
+__device__ void trig_rows(const double t[3], int p, int64_t e, int64_t stride, int f0, double* g64, float* g32,
+                          double* rout) {
+  const double rxy = sqrt(t[0] * t[0] + t[1] * t[1]);
+  const double r = sqrt(rxy * rxy + t[2] * t[2]);
+  double ct = 1.0, st = 0.0, cp = 1.0, sp = 0.0;
+  if (r > 0.0) {
+    ct = t[2] / r;
+    st = rxy / r;
+  }
+  if (rxy > 0.0) {
+    cp = t[0] / rxy;
+    sp = t[1] / rxy;
+  }
+  double cpm = 1.0, spm = 0.0, ctm = 1.0, stm = 0.0;
+  for (int m = 1; m <= p; m++) {
+    double a = cpm * cp - spm * sp, b = spm * cp + cpm * sp;
+    cpm = a;
+    spm = b;
+    a = ctm * ct - stm * st;
+    b = stm * ct + ctm * st;
+    ctm = a;
+    stm = b;
+    const int64_t rows[4] = {f0 + m - 1, f0 + p + m - 1, f0 + 2 * p + m - 1, f0 + 3 * p + m - 1};
+    const double vals[4] = {cpm, spm, ctm, stm};
+    for (int k = 0; k < 4; k++) {
+      g64[rows[k] * stride + e] = vals[k];
+      g32[rows[k] * stride + e] = (float)vals[k];
+    }
+  }
+  *rout = r;
+}
+
+__global__ void m2l_geo_kernel(const int32_t* __restrict__ mt, const int32_t* __restrict__ ms, int64_t nm,
+                               const double* __restrict__ center, const double* __restrict__ radius, int p,
+                               double* __restrict__ g64, float* __restrict__ g32) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nm; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gt = mt[e], gs = ms[e];
+    const double t[3] = {center[3 * gs] - center[3 * gt], center[3 * gs + 1] - center[3 * gt + 1],
+                         center[3 * gs + 2] - center[3 * gt + 2]};
+    double r;
+    trig_rows(t, p, e, nm, 3, g64, g32, &r);
+    const double vals[3] = {1.0 / r, radius[gs] / r, radius[gt] / r};
+    for (int k = 0; k < 3; k++) {
+      g64[k * nm + e] = vals[k];
+      g32[k * nm + e] = (float)vals[k];
+    }
+  }
+}
+
+// M2M (t = c_child - c_parent) and L2L (t = c_parent - c_child) per child box.
+__global__ void edge_geo_kernel(int64_t nbox, int s, const double* __restrict__ center,
+                                const double* __restrict__ radius, int p, double* __restrict__ m64,
+                                float* __restrict__ m32, double* __restrict__ l64, float* __restrict__ l32) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nbox) return;
+  if (g == 0) {
+    for (int f = 0; f < 2 + 4 * p; f++) m64[f * nbox] = m32[f * nbox] = l64[f * nbox] = l32[f * nbox] = 0;
+    return;
+  }
+  int l = 0;
+  while (level_offset(l + 1, s) <= g) l++;
+  const int64_t b = g - level_offset(l, s);
+  const int64_t gp = level_offset(l - 1, s) + (b >> s);
+  const double t[3] = {center[3 * g] - center[3 * gp], center[3 * g + 1] - center[3 * gp + 1],
+                       center[3 * g + 2] - center[3 * gp + 2]};
+  const double tn[3] = {-t[0], -t[1], -t[2]};
+  double r;
+  trig_rows(t, p, g, nbox, 2, m64, m32, &r);
+  trig_rows(tn, p, g, nbox, 2, l64, l32, &r);
+  const double rp = radius[gp];
+  const double a = rp > 0.0 ? r / rp : 0.0, bb = rp > 0.0 ? radius[g] / rp : 0.0;
+  m64[g] = l64[g] = a;
+  m32[g] = l32[g] = (float)a;
+  m64[nbox + g] = l64[nbox + g] = bb;
+  m32[nbox + g] = l32[nbox + g] = (float)bb;
+}
+
+// near-field entries: source leaf, FP32 centre offset, touching-box flag
+__global__ void p2p_entry_kernel(const int32_t* __restrict__ pt, const int32_t* __restrict__ ps, int64_t np,
+                                 int64_t leaf_off, const double* __restrict__ center,
+                                 const double* __restrict__ lo, const double* __restrict__ hi,
+                                 const int32_t* __restrict__ bc, P2PEntry* __restrict__ ent,
+                                 unsigned long long* __restrict__ pairs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gt = leaf_off + pt[e], gs = leaf_off + ps[e];
+    bool touch = true;
+    for (int a = 0; a < 3; a++) touch = touch && lo[3 * gt + a] <= hi[3 * gs + a] && lo[3 * gs + a] <= hi[3 * gt + a];
+    P2PEntry en;
+    en.src = ps[e] | (touch ? (int)0x80000000 : 0);
+    en.dx = (float)(center[3 * gt] - center[3 * gs]);
+    en.dy = (float)(center[3 * gt + 1] - center[3 * gs + 1]);
+    en.dz = (float)(center[3 * gt + 2] - center[3 * gs + 2]);
+    ent[e] = en;
+    atomicAdd(pairs, (unsigned long long)bc[gt] * (unsigned long long)bc[gs]);
+  }
+}
+
+// tree-ordered point records: FP64 position and FP32 offset from the leaf centre
+__global__ void point_records_kernel(const double* __restrict__ X, int64_t n, const int64_t* __restrict__ bs,
+                                     const int32_t* __restrict__ bc, int64_t leaf_off, int64_t n_leaves,
+                                     const double* __restrict__ center, float4* __restrict__ loc,
+                                     dvec4* __restrict__ p64) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= n_leaves) return;
+  const int64_t g = leaf_off + w;
+  const int64_t a = bs[g];
+  const int c = bc[g];
+  for (int i = lane; i < c; i += 32) {
+    const int64_t k = a + i;
+    const double x = X[k], y = X[n + k], z = X[2 * n + k];
+    p64[k] = dvec4{x, y, z, 0.0};
+    loc[k] = make_float4((float)(x - center[3 * g]), (float)(y - center[3 * g + 1]),
+                         (float)(z - center[3 * g + 2]), 0.0f);
+  }
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <class T>
+std::vector<T> to_host(const T* d, int64_t n, cudaStream_t st) {
+  std::vector<T> h((size_t)std::max<int64_t>(n, 0));
+  if (n > 0) FMM_CUDA_TRY(cudaMemcpyAsync(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost, st));
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  return h;
+}
+
+}  // namespace
+
+void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
+  const int64_t n = t->n;
+  const int s = t->prm.splits;
+  const int nch = 1 << s;
+  const int L = t->L;
+  const int R = L * s;
+  t->s = s;
+  t->n_boxes = level_offset(L + 1, s);
+  t->n_leaves = (int64_t)1 << (s * L);
+  const int64_t NB = t->n_boxes, NL = t->n_leaves;
+  const int64_t leaf_off = level_offset(L, s);
+  t->max_leaf = (int)((n + NL - 1) / NL);
+
+  // ---- canonical SoA copy, validation ----
+  double* Xa = scratch_alloc<double>(3 * (size_t)n);
+  double* Xb = scratch_alloc<double>(3 * (size_t)n);
+  int32_t* Ia = scratch_alloc<int32_t>(n);
+  int32_t* Ib = scratch_alloc<int32_t>(n);
+  int* flag = scratch_alloc<int>(4);
+  FMM_CUDA_TRY(cudaMemsetAsync(flag, 0, 4 * sizeof(int), st));
+  canon_kernel<<<grid_for(n, 256), 256, 0, st>>>(pos, n, Xa, Ia, flag);
+  FMM_LAUNCH_CHECK();
+  int hflag = 0;
+  FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hflag) {
+    cudaFree(Xa), cudaFree(Xb), cudaFree(Ia), cudaFree(Ib), cudaFree(flag);
+    require(false, "positions must be finite");
+  }
+
+  // ---- segment boundaries of every round (closed form) ----
+  std::vector<int64_t> round_off(R + 2);
+  int64_t tot = 0;
+  for (int r = 0; r <= R; r++) {
+    round_off[r] = tot;
+    tot += ((int64_t)1 << r) + 1;
+  }
+  int64_t* starts = dev_alloc<int64_t>(nullptr, tot);
+  {
+    int64_t h0[2] = {0, n};
+    FMM_CUDA_TRY(cudaMemcpyAsync(starts, h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+    for (int r = 0; r < R; r++) {
+      const int ns = 1 << r;
+      split_starts_kernel<<<(ns + 255) / 256, 256, 0, st>>>(starts + round_off[r], ns, starts + round_off[r + 1]);
+      FMM_LAUNCH_CHECK();
+    }
+  }
+
+  // ---- large rounds ----
+  int r0 = 0;
+  while (r0 < R && (n + ((int64_t)1 << r0) - 1) / ((int64_t)1 << r0) > kSmallCap) r0++;
+  if (r0 > 0) {
+    const int maxseg = 1 << (r0 - 1);
+    unsigned long long* bmin = scratch_alloc<unsigned long long>(3 * (size_t)maxseg);
+    unsigned long long* bmax = scratch_alloc<unsigned long long>(3 * (size_t)maxseg);
+    unsigned long long* ctr = scratch_alloc<unsigned long long>(2 * (size_t)maxseg);
+    unsigned* hist = scratch_alloc<unsigned>(256 * (size_t)maxseg);
+    Sel* sel = scratch_alloc<Sel>(maxseg);
+    FMM_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned) * 256 * (size_t)maxseg, st));
+    const int nblk = (int)((n + kChunk - 1) / kChunk);
+    for (int r = 0; r < r0; r++) {
+      const int ns = 1 << r;
+      const int64_t* stt = starts + round_off[r];
+      FMM_CUDA_TRY(cudaMemsetAsync(bmin, 0xff, sizeof(unsigned long long) * 3 * ns, st));
+      FMM_CUDA_TRY(cudaMemsetAsync(bmax, 0, sizeof(unsigned long long) * 3 * ns, st));
+      seg_bbox_kernel<<<nblk, kThreads, 0, st>>>(Xa, n, stt, ns, bmin, bmax);
+      FMM_LAUNCH_CHECK();
+      seg_axis_kernel<<<(ns + 255) / 256, 256, 0, st>>>(bmin, bmax, stt, ns, sel);
+      FMM_LAUNCH_CHECK();
+      for (int d = 0; d < 12; d++) {
+        FMM_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+        radix_hist_kernel<<<nblk, kThreads, 0, st>>>(Xa, Ia, n, stt, ns, sel, d, hist);
+        FMM_LAUNCH_CHECK();
+        radix_select_kernel<<<(ns + 255) / 256, 256, 0, st>>>(sel, ns, d, hist, flag);
+        FMM_LAUNCH_CHECK();
+        FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!hflag) break;
+      }
+      FMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 2 * ns, st));
+      partition_kernel<<<nblk, kThreads, 0, st>>>(Xa, Ia, n, stt, ns, sel, ctr, Xb, Ib);
+      FMM_LAUNCH_CHECK();
+      std::swap(Xa, Xb);
+      std::swap(Ia, Ib);
+    }
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(bmin), cudaFree(bmax), cudaFree(ctr), cudaFree(hist), cudaFree(sel);
+  }
+
+  // ---- remaining rounds and the leaf sort, one CTA per segment ----
+  t->perm = dev_alloc<int32_t>(t, n);
+  {
+    const int rounds = R - r0;
+    const size_t smem = small_smem_bytes(rounds);
+    FMM_CUDA_TRY(cudaFuncSetAttribute(small_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    small_segment_kernel<<<1 << r0, kSmallThreads, smem, st>>>(Xa, Ia, n, starts + round_off[r0], rounds, Xb,
+                                                               t->perm);
+    FMM_LAUNCH_CHECK();
+    std::swap(Xa, Xb);  // Xa: positions in tree order
+  }
+
+  // ---- box ranges and geometry ----
+  t->box_start = dev_alloc<int64_t>(t, NB);
+  t->box_count = dev_alloc<int32_t>(t, NB);
+  t->center = dev_alloc<double>(t, 3 * NB);
+  t->radius = dev_alloc<double>(t, NB);
+  t->inv_rho32 = dev_alloc<float>(t, NB);
+  t->inv_rho64 = dev_alloc<double>(t, NB);
+  double* blo = dev_alloc<double>(t, 3 * NB);
+  double* bhi = dev_alloc<double>(t, 3 * NB);
+  for (int l = 0; l <= L; l++) {
+    const int64_t nb = (int64_t)1 << (s * l);
+    box_range_kernel<<<grid_for(nb, 256, 1 << 30), 256, 0, st>>>(starts + round_off[l * s], nb, level_offset(l, s),
+                                                                 t->box_start, t->box_count);
+    FMM_LAUNCH_CHECK();
+  }
+  leaf_bbox_kernel<<<grid_for(NL * 32, 256, 1 << 30), 256, 0, st>>>(Xa, n, t->box_start, t->box_count, leaf_off, NL,
+                                                                    blo, bhi);
+  FMM_LAUNCH_CHECK();
+  for (int l = L - 1; l >= 0; l--) {
+    const int64_t nb = (int64_t)1 << (s * l);
+    parent_bbox_kernel<<<grid_for(nb, 256, 1 << 30), 256, 0, st>>>(nb, level_offset(l, s), level_offset(l + 1, s), nch,
+                                                                   blo, bhi);
+    FMM_LAUNCH_CHECK();
+  }
+  centre_radius_kernel<<<grid_for(NB, 256, 1 << 30), 256, 0, st>>>(NB, blo, bhi, t->center, t->radius, t->inv_rho32,
+                                                                   t->inv_rho64);
+  FMM_LAUNCH_CHECK();
+
+  // ---- average radius per level ----
+  t->level_avg_host = new double[L + 1];
+  {
+    double* pa = scratch_alloc<double>(std::max<int64_t>(NL, 1));
+    double* pb = scratch_alloc<double>(std::max<int64_t>(NL / 2, 1));
+    for (int l = 0; l <= L; l++) {
+      int64_t m = (int64_t)1 << (s * l);
+      FMM_CUDA_TRY(cudaMemcpyAsync(pa, t->radius + level_offset(l, s), sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+      while (m > 1) {
+        pair_sum_kernel<<<grid_for(m / 2, 256, 1 << 30), 256, 0, st>>>(pa, pb, m / 2);
+        FMM_LAUNCH_CHECK();
+        std::swap(pa, pb);
+        m /= 2;
+      }
+      double sum = 0;
+      FMM_CUDA_TRY(cudaMemcpyAsync(&sum, pa, sizeof(double), cudaMemcpyDeviceToHost, st));
+      FMM_CUDA_TRY(cudaStreamSynchronize(st));
+      t->level_avg_host[l] = sum / (double)((int64_t)1 << (s * l));
+    }
+    cudaFree(pa), cudaFree(pb);
+  }
+
+  // ---- level march ----
+  struct Step {
+    int32_t *t, *s;
+    int64_t n;
+  };
+  std::vector<Step> steps;
+  int32_t* ct = dev_alloc<int32_t>(nullptr, 1);
+  int32_t* cs = dev_alloc<int32_t>(nullptr, 1);
+  FMM_CUDA_TRY(cudaMemsetAsync(ct, 0, sizeof(int32_t), st));
+  FMM_CUDA_TRY(cudaMemsetAsync(cs, 0, sizeof(int32_t), st));
+  int64_t nc = 1;
+  int ls = 0, lt = 0;
+  int32_t *p2p_t = nullptr, *p2p_s = nullptr;
+  int64_t np = 0;
+  const bool tie_target = (t->prm.flags & FMM_TIE_TARGET) != 0;
+  for (;;) {
+    int64_t* fws = scratch_alloc<int64_t>(nc);
+    int64_t* fkeep = scratch_alloc<int64_t>(nc);
+    int64_t* pws = scratch_alloc<int64_t>(nc);
+    int64_t* pkeep = scratch_alloc<int64_t>(nc);
+    ws_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, level_offset(lt, s), level_offset(ls, s), t->center,
+                                                 t->radius, t->prm.theta, fws, fkeep);
+    FMM_LAUNCH_CHECK();
+    const int64_t nws = exclusive_scan(fws, pws, nc, st);
+    const int64_t nkeep = exclusive_scan(fkeep, pkeep, nc, st);
+    Step stp{dev_alloc<int32_t>(nullptr, nws), dev_alloc<int32_t>(nullptr, nws), nws};
+    int32_t* kt = dev_alloc<int32_t>(nullptr, nkeep);
+    int32_t* ks = dev_alloc<int32_t>(nullptr, nkeep);
+    emit_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, level_offset(lt, s), level_offset(ls, s), fws, pws,
+                                                   pkeep, stp.t, stp.s, kt, ks);
+    FMM_LAUNCH_CHECK();
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(fws), cudaFree(fkeep), cudaFree(pws), cudaFree(pkeep), cudaFree(ct), cudaFree(cs);
+    if (nws > 0) steps.push_back(stp);
+    else cudaFree(stp.t), cudaFree(stp.s);
+    if (nkeep == 0) {
+      cudaFree(kt), cudaFree(ks);
+      ct = cs = nullptr;
+      break;
+    }
+    const bool can_s = ls < L, can_t = lt < L;
+    if (!can_s && !can_t) {
+      p2p_t = kt;
+      p2p_s = ks;
+      np = nkeep;
+      ct = cs = nullptr;
+      break;
+    }
+    bool adv_src;
+    if (can_s && can_t) {
+      const double as = t->level_avg_host[ls], at = t->level_avg_host[lt];
+      adv_src = (as > at) || (as == at && !tie_target);
+    } else {
+      adv_src = can_s;
+    }
+    nc = nkeep * nch;
+    ct = dev_alloc<int32_t>(nullptr, nc);
+    cs = dev_alloc<int32_t>(nullptr, nc);
+    expand_kernel<<<grid_for(nkeep, 256), 256, 0, st>>>(kt, ks, nkeep, nch, adv_src ? 1 : 0, ct, cs);
+    FMM_LAUNCH_CHECK();
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(kt), cudaFree(ks);
+    if (adv_src) ls++;
+    else lt++;
+  }
+
+  // ---- M2L lists as CSR by target, sources ascending ----
+  int64_t nm = 0;
+  for (auto& x : steps) nm += x.n;
+  t->n_m2l = nm;
+  t->m2l_off = dev_alloc<int64_t>(t, NB + 1);
+  t->m2l_src = dev_alloc<int32_t>(t, nm);
+  t->m2l_trg = dev_alloc<int32_t>(t, nm);
+  {
+    int64_t* cnt = scratch_alloc<int64_t>(NB + 1);
+    int64_t* fill = scratch_alloc<int64_t>(NB + 1);
+    FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (NB + 1), st));
+    FMM_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int64_t) * (NB + 1), st));
+    for (auto& x : steps) {
+      count_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.n, cnt);
+      FMM_LAUNCH_CHECK();
+    }
+    exclusive_scan(cnt, t->m2l_off, NB + 1, st);
+    for (auto& x : steps) {
+      m2l_scatter_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.s, x.n, t->m2l_off, fill, t->m2l_trg, t->m2l_src);
+      FMM_LAUNCH_CHECK();
+      m2l_fill_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.n, fill);
+      FMM_LAUNCH_CHECK();
+    }
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(cnt), cudaFree(fill);
+    for (auto& x : steps) cudaFree(x.t), cudaFree(x.s);
+  }
+
+  // ---- near-field lists as CSR by target leaf ----
+  t->n_p2p = np;
+  t->p2p_off = dev_alloc<int64_t>(t, NL + 1);
+  t->p2p_src = dev_alloc<int32_t>(t, np);
+  t->p2p32 = dev_alloc<P2PEntry>(t, np);
+  int32_t* p2p_trg = dev_alloc<int32_t>(nullptr, np);
+  {
+    int64_t* cnt = scratch_alloc<int64_t>(NL + 1);
+    FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (NL + 1), st));
+    if (np > 0) {
+      count_kernel<<<grid_for(np, 256), 256, 0, st>>>(p2p_t, np, cnt);
+      FMM_LAUNCH_CHECK();
+      FMM_CUDA_TRY(cudaMemcpyAsync(t->p2p_src, p2p_s, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st));
+      FMM_CUDA_TRY(cudaMemcpyAsync(p2p_trg, p2p_t, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st));
+    }
+    exclusive_scan(cnt, t->p2p_off, NL + 1, st);
+    cudaFree(cnt);
+    if (p2p_t) cudaFree(p2p_t), cudaFree(p2p_s);
+  }
+
+  // ---- point records, rotation coefficients, near-field entries ----
+  const int p = t->prm.p;
+  t->pos_local = dev_alloc<float4>(t, n);
+  t->pos64 = dev_alloc<dvec4>(t, n);
+  point_records_kernel<<<grid_for(NL * 32, 256, 1 << 30), 256, 0, st>>>(Xa, n, t->box_start, t->box_count, leaf_off,
+                                                                        NL, t->center, t->pos_local, t->pos64);
+  FMM_LAUNCH_CHECK();
+  t->geo64 = dev_alloc<double>(t, (size_t)m2l_fields(p) * std::max<int64_t>(nm, 1));
+  t->geo32 = dev_alloc<float>(t, (size_t)m2l_fields(p) * std::max<int64_t>(nm, 1));
+  if (nm > 0) {
+    m2l_geo_kernel<<<grid_for(nm, 256), 256, 0, st>>>(t->m2l_trg, t->m2l_src, nm, t->center, t->radius, p, t->geo64,
+                                                      t->geo32);
+    FMM_LAUNCH_CHECK();
+  }
+  t->m2m64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
+  t->m2m32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
+  t->l2l64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
+  t->l2l32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
+  edge_geo_kernel<<<grid_for(NB, 128, 1 << 30), 128, 0, st>>>(NB, s, t->center, t->radius, p, t->m2m64, t->m2m32,
+                                                              t->l2l64, t->l2l32);
+  FMM_LAUNCH_CHECK();
+  {
+    unsigned long long* pairs = scratch_alloc<unsigned long long>(1);
+    FMM_CUDA_TRY(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), st));
+    if (np > 0) {
+      p2p_entry_kernel<<<grid_for(np, 256), 256, 0, st>>>(p2p_trg, t->p2p_src, np, leaf_off, t->center, blo, bhi,
+                                                          t->box_count, t->p2p32, pairs);
+      FMM_LAUNCH_CHECK();
+    }
+    unsigned long long hp = 0;
+    FMM_CUDA_TRY(cudaMemcpyAsync(&hp, pairs, sizeof(hp), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    t->n_p2p_pairs = (int64_t)hp;
+    cudaFree(pairs);
+  }
+
+  // ---- work orders: longest M2L lists and heaviest near fields first ----
+  {
+    std::vector<int64_t> off = to_host(t->m2l_off, NB + 1, st);
+    std::vector<int32_t> ord(NB);
+    for (int64_t g = 0; g < NB; g++) ord[g] = (int32_t)g;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    t->m2l_order = dev_alloc<int32_t>(t, NB);
+    FMM_CUDA_TRY(cudaMemcpyAsync(t->m2l_order, ord.data(), sizeof(int32_t) * NB, cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> poff = to_host(t->p2p_off, NL + 1, st);
+    std::vector<int32_t> psrc = to_host(t->p2p_src, np, st);
+    std::vector<int32_t> bcnt = to_host(t->box_count + leaf_off, NL, st);
+    std::vector<int64_t> work(NL, 0);
+    for (int64_t l = 0; l < NL; l++)
+      for (int64_t e = poff[l]; e < poff[l + 1]; e++) work[l] += bcnt[psrc[e]];
+    std::vector<int32_t> lord(NL);
+    for (int64_t l = 0; l < NL; l++) lord[l] = (int32_t)l;
+    std::stable_sort(lord.begin(), lord.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
+    t->leaf_order = dev_alloc<int32_t>(t, NL);
+    FMM_CUDA_TRY(cudaMemcpyAsync(t->leaf_order, lord.data(), sizeof(int32_t) * NL, cudaMemcpyHostToDevice, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+
+  // ---- evaluation workspace ----
+  const int NCP = ncoef_pad(p);
+  t->src32 = dev_alloc<float4>(t, n);
+  t->src64 = dev_alloc<dvec4>(t, n);
+  t->M32 = dev_alloc<float>(t, (size_t)NB * NCP);
+  t->Lam32 = dev_alloc<float>(t, (size_t)NB * NCP);
+  t->M64 = dev_alloc<double>(t, (size_t)NB * NCP);
+  t->Lam64 = dev_alloc<double>(t, (size_t)NB * NCP);
+  FMM_CUDA_TRY(cudaMemsetAsync(t->M32, 0, sizeof(float) * NB * NCP, st));
+  FMM_CUDA_TRY(cudaMemsetAsync(t->Lam32, 0, sizeof(float) * NB * NCP, st));
+  FMM_CUDA_TRY(cudaMemsetAsync(t->M64, 0, sizeof(double) * NB * NCP, st));
+  FMM_CUDA_TRY(cudaMemsetAsync(t->Lam64, 0, sizeof(double) * NB * NCP, st));
+  t->near_u = dev_alloc<double>(t, n);
+  t->near_f = dev_alloc<double>(t, 3 * (size_t)n);
+  t->q_stage = dev_alloc<double>(t, n);
+  t->u_stage = dev_alloc<double>(t, n);
+  t->f_stage = dev_alloc<double>(t, 3 * (size_t)n);
+  t->g_stage = dev_alloc<double>(t, 3 * (size_t)n);
+  t->counters = dev_alloc<int>(t, 8);
+  t->status = dev_alloc<int>(t, 1);
+  FMM_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), st));
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+
+  cudaFree(blo), cudaFree(bhi);
+  t->device_bytes -= sizeof(double) * 6 * NB;
+  cudaFree(p2p_trg);
+  cudaFree(starts);
+  cudaFree(Xa), cudaFree(Xb), cudaFree(Ia), cudaFree(Ib), cudaFree(flag);
+}
+
+}  // namespace fmm

@@ -1,0 +1,229 @@
+"""Python binding of the GB300 FMM library (C ABI in include/fmm.h).
+
+Argument marshalling only: every stage of the evaluation runs in the CUDA
+kernels of libfmm_gb300.so.  Tensors are torch CUDA tensors (float64,
+contiguous); work is enqueued on torch's current CUDA stream.  If the library
+has not been built, loading fails with an error (there is no other path).
+"""
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
+_lib = None
+
+FMM_OK, FMM_ERR_INVALID_ARG, FMM_ERR_CUDA, FMM_ERR_OOM, FMM_ERR_CAPACITY, FMM_ERR_TIMEOUT = range(6)
+FMM_FP64, FMM_FP32C = 0, 1
+FMM_TIE_TARGET = 1
+FMM_MAX_P = 10
+
+# exported entry points, in include/fmm.h order
+ENTRY_POINTS = ["fmm_last_error", "fmm_num_levels", "fmm_build_tree", "fmm_tree_free",
+                "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_export",
+                "fmm_eval_potential", "fmm_eval_field", "fmm_eval_potential_host", "fmm_backward"]
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("FMM error %d: %s" % (code, msg))
+        self.code = code
+
+
+class fmm_params(C.Structure):
+    _fields_ = [("p", C.c_int), ("leaf_size", C.c_int), ("splits", C.c_int), ("theta", C.c_double),
+                ("precision", C.c_int), ("flags", C.c_int)]
+
+
+class fmm_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("levels", C.c_int), ("p", C.c_int), ("splits", C.c_int),
+                ("leaf_size", C.c_int), ("precision", C.c_int), ("theta", C.c_double),
+                ("n_boxes", C.c_int64), ("n_leaves", C.c_int64), ("n_m2l", C.c_int64),
+                ("n_p2p", C.c_int64), ("n_p2p_pairs", C.c_int64), ("device_bytes", C.c_size_t),
+                ("build_ms", C.c_double)]
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def lib():
+    """Loads libfmm_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError("libfmm_gb300.so not found at %s; build it with "
+                              "paper_2511_15269_gb300.build.build()" % _LIB_PATH)
+        L = C.CDLL(_LIB_PATH)
+        vp, i64, i = C.c_void_p, C.c_int64, C.c_int
+        L.fmm_last_error.restype = C.c_char_p
+        L.fmm_num_levels.argtypes = [i64, i, i]
+        L.fmm_num_levels.restype = i
+        L.fmm_build_tree.argtypes = [vp, i64, C.POINTER(fmm_params), vp, C.POINTER(vp)]
+        L.fmm_tree_free.argtypes = [vp]
+        L.fmm_tree_free.restype = None
+        L.fmm_tree_set_precision.argtypes = [vp, i]
+        L.fmm_tree_stats.argtypes = [vp, C.POINTER(fmm_stats)]
+        L.fmm_tree_status.argtypes = [vp, vp]
+        L.fmm_tree_export.argtypes = [vp] * 11
+        L.fmm_eval_potential.argtypes = [vp, vp, vp, vp]
+        L.fmm_eval_field.argtypes = [vp, vp, vp, vp, vp]
+        L.fmm_eval_potential_host.argtypes = [vp, vp, vp, vp]
+        L.fmm_backward.argtypes = [vp, vp, vp, vp, vp, vp]
+        for f in ENTRY_POINTS:
+            if f not in ("fmm_last_error", "fmm_num_levels", "fmm_tree_free"):
+                getattr(L, f).restype = i
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != FMM_OK:
+        raise FmmError(rc, lib().fmm_last_error().decode(errors="replace"))
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, shape_last=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def fmm_last_error():
+    return lib().fmm_last_error().decode(errors="replace")
+
+
+def fmm_num_levels(n, leaf_size, splits=2):
+    return lib().fmm_num_levels(int(n), int(leaf_size), int(splits))
+
+
+class Tree:
+    """Owner of an fmm_tree* built by fmm_build_tree."""
+
+    def __init__(self, handle, n, params):
+        self._h = handle
+        self.n = n
+        self.params = params
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            lib().fmm_tree_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self):
+        return fmm_tree_stats(self)
+
+    def set_precision(self, precision):
+        fmm_tree_set_precision(self, precision)
+
+
+def fmm_build_tree(pos, p, leaf_size, splits=2, theta=0.5, precision=FMM_FP32C, flags=0):
+    """Builds the hierarchy of `pos` (N x 3 float64 CUDA tensor) on the device."""
+    pos = pos.contiguous()
+    n = pos.shape[0]
+    prm = fmm_params(int(p), int(leaf_size), int(splits), float(theta), int(precision), int(flags))
+    h = C.c_void_p()
+    _check(lib().fmm_build_tree(_dev(pos), n, C.byref(prm), _stream(), C.byref(h)))
+    return Tree(h, n, prm)
+
+
+def fmm_tree_free(tree):
+    tree.free()
+
+
+def fmm_tree_set_precision(tree, precision):
+    _check(lib().fmm_tree_set_precision(tree.handle, int(precision)))
+
+
+def fmm_tree_stats(tree):
+    s = fmm_stats()
+    _check(lib().fmm_tree_stats(tree.handle, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in fmm_stats._fields_}
+
+
+def fmm_tree_status(tree):
+    _check(lib().fmm_tree_status(tree.handle, _stream()))
+
+
+def fmm_tree_export(tree):
+    """Host copies of the hierarchy (numpy arrays)."""
+    import numpy as np
+    st = fmm_tree_stats(tree)
+    nb, L = st["n_boxes"], st["levels"]
+    out = dict(perm=np.zeros(st["n"], np.int32), box_start=np.zeros(nb, np.int64),
+               box_count=np.zeros(nb, np.int64), center=np.zeros((nb, 3)), radius=np.zeros(nb),
+               level_avg_radius=np.zeros(L + 1), m2l_trg=np.zeros(st["n_m2l"], np.int32),
+               m2l_src=np.zeros(st["n_m2l"], np.int32), p2p_trg=np.zeros(st["n_p2p"], np.int32),
+               p2p_src=np.zeros(st["n_p2p"], np.int32))
+    keys = ["perm", "box_start", "box_count", "center", "radius", "level_avg_radius", "m2l_trg",
+            "m2l_src", "p2p_trg", "p2p_src"]
+    _check(lib().fmm_tree_export(tree.handle, *[C.c_void_p(out[k].ctypes.data) for k in keys]))
+    return out
+
+
+def fmm_eval_potential(tree, q, out=None):
+    u = out if out is not None else torch.empty(tree.n, dtype=torch.float64, device=q.device)
+    _check(lib().fmm_eval_potential(tree.handle, _dev(q), _dev(u), _stream()))
+    return u
+
+
+def fmm_eval_field(tree, q, potential=True):
+    f = torch.empty((tree.n, 3), dtype=torch.float64, device=q.device)
+    u = torch.empty(tree.n, dtype=torch.float64, device=q.device) if potential else None
+    _check(lib().fmm_eval_field(tree.handle, _dev(q), _dev(u) if u is not None else None, _dev(f),
+                                _stream()))
+    return (u, f) if potential else f
+
+
+def fmm_eval_potential_host(tree, q_host, u_host=None):
+    """Host-buffer evaluation: q_host, u_host are float64 CPU tensors (pinned is fastest)."""
+    if u_host is None:
+        u_host = torch.empty(tree.n, dtype=torch.float64, pin_memory=True)
+    assert q_host.dtype == torch.float64 and not q_host.is_cuda and q_host.is_contiguous()
+    _check(lib().fmm_eval_potential_host(tree.handle, C.c_void_p(q_host.data_ptr()),
+                                         C.c_void_p(u_host.data_ptr()), _stream()))
+    return u_host
+
+
+def fmm_backward(tree, q, grad_u, need_q=True, need_pos=True):
+    gq = torch.empty(tree.n, dtype=torch.float64, device=q.device) if need_q else None
+    gp = torch.empty((tree.n, 3), dtype=torch.float64, device=q.device) if need_pos else None
+    _check(lib().fmm_backward(tree.handle, _dev(q), _dev(grad_u.contiguous()),
+                              _dev(gq) if gq is not None else None,
+                              _dev(gp) if gp is not None else None, _stream()))
+    return gq, gp
+
+
+class FMMPotential(torch.autograd.Function):
+    """u = FMM potential of charges q at the tree's points (Eq. 1-3).
+
+    Gradients: dL/dq = K dL/du (fmm_backward) and dL/dpos from the fields of q
+    and of dL/du, at the fixed hierarchy of the tree."""
+
+    @staticmethod
+    def forward(ctx, pos, q, tree):
+        ctx.tree = tree
+        ctx.save_for_backward(q)
+        return fmm_eval_potential(tree, q.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (q,) = ctx.saved_tensors
+        need_pos, need_q = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        gq, gp = fmm_backward(ctx.tree, q.contiguous(), grad_u.contiguous(), need_q=need_q,
+                              need_pos=need_pos)
+        return gp, gq, None

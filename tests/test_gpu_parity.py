@@ -1,0 +1,227 @@
+"""Parity of the CUDA path (called through the C ABI) with the CPU oracle.
+
+Tree, geometry and interaction lists must be bit-identical; FP64 potentials,
+fields and gradients must match the oracle FMM to 1e-12 relative L2 (1e-11
+for fields and position gradients, which carry an extra cancellation); the
+FP32-compensated path must match the FP64 oracle FMM to the FP32 budget
+derived in the tests below.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_15269_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# FP32 budget: unit roundoff 6e-8, about ten rounded operations deep per
+# translation chain plus FP32 position offsets; fields lose one more digit.
+TOL_FP64 = 1e-12
+TOL_FP64_FIELD = 1e-11
+TOL_FP32 = 3e-6
+TOL_FP32_FIELD = 3e-5
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_15269_gb300 import build, fmm
+    build.build()
+    fmm.lib()
+    return fmm
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def build_both(F, orc, pos, p, leaf, s=2, theta=0.5, prec=1, flags=0):
+    T = F.fmm_build_tree(cuda(pos), p, leaf, s, theta, prec, flags)
+    O = orc.Tree(pos, leaf, s, theta, tie_target=bool(flags & F.FMM_TIE_TARGET))
+    return T, O
+
+
+def assert_same_tree(F, T, O):
+    ex = F.fmm_tree_export(T)
+    st = F.fmm_tree_stats(T)
+    assert (st["levels"], st["n_boxes"], st["n_m2l"], st["n_p2p"]) == (O.L, O.n_boxes, O.n_m2l, O.n_p2p)
+    np.testing.assert_array_equal(ex["perm"], O.perm)
+    np.testing.assert_array_equal(ex["box_start"], O.box_start)
+    np.testing.assert_array_equal(ex["box_count"], O.box_count)
+    np.testing.assert_array_equal(ex["center"].view(np.uint64), O.center.view(np.uint64))
+    np.testing.assert_array_equal(ex["radius"].view(np.uint64), O.radius.view(np.uint64))
+    np.testing.assert_array_equal(ex["level_avg_radius"].view(np.uint64), O.level_avg_radius.view(np.uint64))
+    np.testing.assert_array_equal(ex["m2l_trg"], O.m2l_trg)
+    np.testing.assert_array_equal(ex["m2l_src"], O.m2l_src)
+    np.testing.assert_array_equal(ex["p2p_trg"], O.p2p_trg)
+    np.testing.assert_array_equal(ex["p2p_src"], O.p2p_src)
+    pairs = sum(int(O.box_count[O.level_offset(O.L) + t]) * int(O.box_count[O.level_offset(O.L) + s])
+                for t, s in zip(O.p2p_trg, O.p2p_src))
+    assert st["n_p2p_pairs"] == pairs
+
+
+def dup_grid(n, seed):
+    rng = np.random.default_rng(seed)
+    return np.round(rng.random((n, 3)) * 8) / 8  # many exact duplicates
+
+
+TREE_CASES = [
+    ("cube4k_cfg", lambda: workloads.uniform_cube(4096, 0)[0], 64, 2, 0.4, 0),
+    ("plummer30k", lambda: workloads.plummer_sphere(30000, 1)[0], 64, 2, 0.5, 0),
+    ("film40", lambda: workloads.thin_film(40, 2)[0], 32, 2, 0.5, 0),
+    ("clusters_s3", lambda: workloads.gaussian_clusters(10000, 3)[0], 16, 3, 0.6, 0),
+    ("cube_s1", lambda: workloads.uniform_cube(5000, 4)[0], 8, 1, 0.5, 0),
+    ("clusters_tie_target", lambda: workloads.gaussian_clusters(8000, 5)[0], 32, 2, 0.6, 1),
+    ("n1", lambda: np.array([[0.3, -0.2, 0.1]]), 64, 2, 0.5, 0),
+    ("n2", lambda: np.array([[0.3, -0.2, 0.1], [0.1, 0.1, 0.1]]), 4, 2, 0.5, 0),
+    ("n50_single_leaf", lambda: workloads.uniform_cube(50, 6)[0], 64, 2, 0.5, 0),
+    ("n2049", lambda: workloads.uniform_cube(2049, 7)[0], 16, 2, 0.5, 0),
+    ("n4097", lambda: workloads.uniform_cube(4097, 8)[0], 8, 2, 0.5, 0),
+    ("duplicates", lambda: dup_grid(3000, 9), 16, 2, 0.5, 0),
+    ("cube250k", lambda: workloads.uniform_cube(250000, 10)[0], 64, 2, 0.5, 0),
+]
+
+
+@pytest.mark.parametrize("name,mk,leaf,s,theta,flags", TREE_CASES, ids=[c[0] for c in TREE_CASES])
+def test_tree_and_lists_bit_exact(F, orc, name, mk, leaf, s, theta, flags):
+    pos = mk()
+    T, O = build_both(F, orc, pos, 4, leaf, s, theta, 1, flags)
+    assert_same_tree(F, T, O)
+    F.fmm_tree_status(T)
+
+
+POT_CASES = [
+    ("cube4k_p4", lambda: workloads.uniform_cube(4096, 0), 4, 64, 2, 0.4),
+    ("plummer20k_p8", lambda: workloads.plummer_sphere(20000, 1), 8, 64, 2, 0.5),
+    ("film30_p8", lambda: workloads.thin_film(30, 2), 8, 32, 2, 0.5),
+    ("cube12k_p10", lambda: workloads.uniform_cube(12000, 3), 10, 32, 2, 0.5),
+    ("clusters_s3_p6", lambda: workloads.gaussian_clusters(9000, 4), 6, 32, 3, 0.6),
+    ("cube6k_s1_p3", lambda: workloads.uniform_cube(6000, 5), 3, 16, 1, 0.5),
+    ("cube3k_p1", lambda: workloads.uniform_cube(3000, 6), 1, 32, 2, 0.5),
+    ("ragged_p5_leaf200", lambda: workloads.uniform_cube(7777, 7), 5, 200, 2, 0.5),
+]
+
+
+@pytest.mark.parametrize("name,mk,p,leaf,s,theta", POT_CASES, ids=[c[0] for c in POT_CASES])
+def test_potential_parity(F, orc, name, mk, p, leaf, s, theta):
+    pos, q = mk()
+    T, O = build_both(F, orc, pos, p, leaf, s, theta, F.FMM_FP64)
+    u_o = O.eval(q, p)
+    u64 = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    e64 = rel_l2(u64, u_o)
+    F.fmm_tree_set_precision(T, F.FMM_FP32C)
+    u32 = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    e32 = rel_l2(u32, u_o)
+    F.fmm_tree_status(T)
+    print("%s: fp64 vs oracle %.3e, fp32c vs oracle %.3e" % (name, e64, e32))
+    assert e64 <= TOL_FP64
+    assert e32 <= TOL_FP32
+
+
+@pytest.mark.parametrize("name,mk,p,leaf,s,theta", POT_CASES[:4], ids=[c[0] for c in POT_CASES[:4]])
+def test_field_parity(F, orc, name, mk, p, leaf, s, theta):
+    pos, q = mk()
+    T, O = build_both(F, orc, pos, p, leaf, s, theta, F.FMM_FP64)
+    u_o, f_o = O.eval(q, p, field=True)
+    u64, f64 = (x.cpu().numpy() for x in F.fmm_eval_field(T, cuda(q)))
+    F.fmm_tree_set_precision(T, F.FMM_FP32C)
+    u32, f32 = (x.cpu().numpy() for x in F.fmm_eval_field(T, cuda(q)))
+    print("%s field: fp64 %.3e fp32c %.3e" % (name, rel_l2(f64, f_o), rel_l2(f32, f_o)))
+    assert rel_l2(u64, u_o) <= TOL_FP64
+    assert rel_l2(f64, f_o) <= TOL_FP64_FIELD
+    assert rel_l2(u32, u_o) <= TOL_FP32
+    assert rel_l2(f32, f_o) <= TOL_FP32_FIELD
+
+
+def test_backward_matches_oracle(F, orc):
+    pos, q = workloads.thin_film(24, 1)
+    g = np.random.default_rng(2).normal(size=len(q))
+    p = 8
+    T, O = build_both(F, orc, pos, p, 32, 2, 0.5, F.FMM_FP64)
+    # oracle FMM vjp: dq = K g, dpos = g grad u + q grad v = -(g E_q + q E_g)
+    _, fq = O.eval(q, p, field=True)
+    v, fg = O.eval(g, p, field=True)
+    dq_o = v
+    dp_o = -(g[:, None] * fq + q[:, None] * fg)
+    gq, gp = F.fmm_backward(T, cuda(q), cuda(g))
+    assert rel_l2(gq.cpu().numpy(), dq_o) <= TOL_FP64
+    assert rel_l2(gp.cpu().numpy(), dp_o) <= TOL_FP64_FIELD
+    # and the exact direct-sum gradient within the FMM truncation
+    dq_d, dp_d = orc.direct_vjp(pos, q, g)
+    assert rel_l2(gq.cpu().numpy(), dq_d) < 1e-4
+    assert rel_l2(gp.cpu().numpy(), dp_d) < 1e-3
+
+
+def test_autograd_function(F, orc):
+    pos, q = workloads.uniform_cube(3000, 3)
+    T = F.fmm_build_tree(cuda(pos), 8, 32, 2, 0.5, F.FMM_FP64)
+    P = cuda(pos).requires_grad_(True)
+    Q = cuda(q).requires_grad_(True)
+    u = F.FMMPotential.apply(P, Q, T)
+    loss = 0.5 * (Q * u).sum()
+    loss.backward()
+    O = orc.Tree(pos, 32, 2, 0.5)
+    uo, fo = O.eval(q, 8, field=True)
+    # L = 1/2 q.u: dL/dq = u/2 + K(q/2) = u;  dL/dr = -(q/2 E_q + q E_{q/2}) = -q E_q
+    assert rel_l2(Q.grad.cpu().numpy(), uo) <= 1e-11
+    assert rel_l2(P.grad.cpu().numpy(), -q[:, None] * fo) <= TOL_FP64_FIELD
+
+
+def test_host_buffer_entry_point(F):
+    pos, q = workloads.uniform_cube(5000, 4)
+    T = F.fmm_build_tree(cuda(pos), 6, 64, 2, 0.5, F.FMM_FP32C)
+    u_dev = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    qh = torch.from_numpy(q).pin_memory()
+    u_host = F.fmm_eval_potential_host(T, qh).numpy()
+    np.testing.assert_array_equal(u_host, u_dev)
+
+
+def test_edge_cases(F, orc):
+    # one point: no other charge, potential 0
+    T = F.fmm_build_tree(cuda(np.array([[0.5, 0.5, 0.5]])), 4, 64, 2, 0.5, F.FMM_FP64)
+    assert F.fmm_eval_potential(T, cuda(np.array([3.0]))).item() == 0.0
+    # coincident points contribute nothing to each other
+    pos = np.array([[0.1, 0.2, 0.3]] * 3 + [[0.9, 0.8, 0.7]])
+    q = np.array([1.0, 2.0, 3.0, 4.0])
+    for prec in (F.FMM_FP64, F.FMM_FP32C):
+        T = F.fmm_build_tree(cuda(pos), 4, 4, 2, 0.5, prec)
+        u = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+        np.testing.assert_allclose(u, orc.direct(pos, q), rtol=1e-6)
+    # all points identical: zero radius everywhere
+    pos = np.zeros((40, 3)) + 0.25
+    T = F.fmm_build_tree(cuda(pos), 4, 4, 2, 0.5, F.FMM_FP32C)
+    assert np.all(F.fmm_eval_potential(T, cuda(np.ones(40))).cpu().numpy() == 0.0)
+    # non-finite positions are rejected
+    bad = workloads.uniform_cube(100, 0)[0]
+    bad[7, 1] = np.nan
+    with pytest.raises(F.FmmError) as ei:
+        F.fmm_build_tree(cuda(bad), 4, 16, 2, 0.5, F.FMM_FP64)
+    assert ei.value.code == F.FMM_ERR_INVALID_ARG
+
+
+def test_cube1m_p8_full_size(F, orc):
+    """Uniform cube N = 2^20, p = 8, leaf 128, theta 0.4: bit-exact hierarchy,
+    FP32C within 1e-6 relative L2 of the FP64 direct sum on sampled targets,
+    FP64 within 1e-12 of the oracle FMM there."""
+    c = workloads.CONFIGS["cube1m_p8"]
+    pos, q = workloads.uniform_cube(c["n"], 0)
+    T, O = build_both(F, orc, pos, c["p"], c["leaf_size"], c["s"], c["theta"], F.FMM_FP32C)
+    assert_same_tree(F, T, O)
+    tg = workloads.sample_targets(c["n"], 512, seed=1)
+    ud = orc.direct(pos, q, targets=tg)
+    u32 = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()[tg]
+    F.fmm_tree_set_precision(T, F.FMM_FP64)
+    u64 = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()[tg]
+    uo = O.eval(q, c["p"], targets=tg)
+    F.fmm_tree_status(T)
+    print("cube1m: fp32c vs direct %.3e, fp64 vs direct %.3e, fp64 vs oracle fmm %.3e"
+          % (rel_l2(u32, ud), rel_l2(u64, ud), rel_l2(u64, uo)))
+    assert rel_l2(u64, uo) <= TOL_FP64
+    assert rel_l2(u32, ud) <= 1e-6

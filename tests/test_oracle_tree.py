@@ -83,6 +83,8 @@ def test_ties_and_signed_zero(orc):
     pos2[pos2 == 0.0] = 0.0  # all +0.0
     T2 = orc.Tree(pos2, 4, 2, 0.5)
     np.testing.assert_array_equal(T.perm, T2.perm)
+    np.testing.assert_array_equal(T.center.view(np.uint64), T2.center.view(np.uint64))
+    assert not np.any(np.signbit(T.center) & (T.center == 0.0))
 
 
 def test_leaf_order_and_geometry(orc):
