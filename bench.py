@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of one FMM potential evaluation (Mpoints/s) on GB300.
+
+Workload: uniform cube N = 2^20 (seeded), charges U[-1,1], expansion order
+p = 8, leaf size 128, s = 2, theta = 0.4, FP32-compensated path.  A step is
+one evaluation with the hierarchy prebuilt (sort, P2M, M2M, M2L, L2L, L2P +
+P2P, inverse sort), charges resident in device memory; L2 is flushed (a
+256 MB write) before every timed step.  The JSON line also carries the FP64
+path, the errors against the FP64 direct sum on 4096 sampled targets, the
+backward/forward time ratio, per-stage times, the roofline of the dominant
+kernel and the CPU oracle timed on the host cores.
+
+--impl reference times the CPU oracle instead (the reference arm), on
+bounded target samples of the same workload.
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoints/s per FMM eval at 1M pts, FP32 vs FP64 at stated error; bwd/fwd ratio"
+WORKLOAD = "cube1m_p8"
+FP32_FLOPS_PER_PAIR = 10  # potential: 3 sub, 3 for r^2, 1 rsqrt-scale, 2 accumulate (+1 select)
+SMS = 152
+FP32_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64, backward, errors, CPU baseline")
+    ap.add_argument("--n", type=int, default=None,
+                    help="points of the uniform cube (default 2^20); smaller values are for profiling captures")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def oracle_sample_eval(O, q, p, leaves, n_leaves):
+    """Oracle FMM at every point of the given target leaves; returns (points, seconds)."""
+    off = O.level_offset(O.L)
+    tg = np.concatenate([O.perm[O.box_start[off + l]:O.box_start[off + l] + O.box_count[off + l]]
+                         for l in leaves]).astype(np.int64)
+    t0 = time.perf_counter()
+    O.eval(q, p, targets=tg)
+    return len(tg), time.perf_counter() - t0
+
+
+def run_reference(args, cfg):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2511_15269_gb300 import workloads
+    oracle.build()
+    pos, q = workloads.uniform_cube(cfg["n"], seed=0)
+    O = oracle.Tree(pos, cfg["leaf_size"], cfg["s"], cfg["theta"])
+    rng = np.random.default_rng(7)
+    # each step: the oracle FMM at all points of 32 random target leaves, so
+    # that warm-up + steps stay within a few minutes
+    per_step = []
+    pts = 0
+    for k in range(args.warmup + args.steps):
+        leaves = rng.choice(O.n_leaves, 32, replace=False)
+        m, dt = oracle_sample_eval(O, q, cfg["p"], leaves, O.n_leaves)
+        if k >= args.warmup:
+            per_step.append(dt)
+            pts += m
+    secs = sum(per_step)
+    value = pts / secs / 1e6
+    cores = oracle.num_threads()
+    sample = ("oracle FP64 FMM (rotation-based, OpenMP) at every point of 32 random target leaves "
+              "(~2048 points) per step, full P2M/M2M of the 2^20-point tree included; tree prebuilt")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(per_step),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(cfg, "FP64 CPU oracle"),
+        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(cfg, path):
+    return {"workload": "uniform cube N=%d (U[0,1)^3, q U[-1,1], seed 0), p=%d, leaf %d, s=%d, theta=%g, %s"
+            % (cfg["n"], cfg["p"], cfg["leaf_size"], cfg["s"], cfg["theta"], path),
+            "n_points": cfg["n"], "p": cfg["p"], "leaf_size": cfg["leaf_size"], "splits": cfg["s"],
+            "theta": cfg["theta"], "l2": "flushed before every timed step (256 MB write)",
+            "parallelism": "replicas"}
+
+
+def main():
+    args = parse()
+    from paper_2511_15269_gb300 import workloads
+    cfg = dict(workloads.CONFIGS[WORKLOAD])
+    if args.n:
+        cfg["n"] = int(args.n)
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+    rank, world, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2511_15269_gb300 import build, fmm
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    fmm.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = cfg["n"]
+    pos, q = workloads.uniform_cube(n, seed=rank)
+    pos_d = torch.from_numpy(pos).to(dev)
+    q_d = torch.from_numpy(q).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    T = fmm.fmm_build_tree(pos_d, cfg["p"], cfg["leaf_size"], cfg["s"], cfg["theta"], fmm.FMM_FP32C)
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    st = fmm.fmm_tree_stats(T)
+    u_d = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(max(args.warmup, 3)):
+        fmm.fmm_eval_potential(T, q_d, u_d)
+    torch.cuda.synchronize()
+
+    # ---- timed region ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fmm.fmm_tree_profile(T, True)
+    launches0 = fmm.fmm_tree_stats(T)["kernel_launches"]
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record()
+        fmm.fmm_eval_potential(T, q_d, u_d)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    fmm.fmm_tree_profile(T, False)
+    launches = fmm.fmm_tree_stats(T)["kernel_launches"] - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    stage, calls = fmm.fmm_tree_stage_times(T)
+    stage_ms = {k: v / max(calls, 1) for k, v in stage.items()}
+    fmm.fmm_tree_status(T)
+    value = world * n / (ms * 1e-3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (near field, P2P) ----
+    clk = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+    pairs = st["n_p2p_pairs"]
+    p2p_s = stage_ms["p2p"] * 1e-3
+    achieved = pairs * FP32_FLOPS_PER_PAIR / p2p_s / 1e12
+    roofline = {"bound": "alu", "kernel": "p2p_kernel (near field, FP32 + MUFU rsqrt)",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "traffic": None,
+                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
+                               % (SMS, FP32_LANES, clk),
+                "pairs_per_launch": pairs, "flops_per_pair": FP32_FLOPS_PER_PAIR,
+                "p2p_ms": stage_ms["p2p"],
+                "mufu_frac": pairs / p2p_s / (SMS * 16 * clk * 1e6)}
+
+    # ---- end to end through the host-buffer entry point ----
+    qh = torch.from_numpy(q).pin_memory()
+    uh = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        fmm.fmm_eval_potential_host(T, qh, uh)
+    e2e_steps = max(5, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fmm.fmm_eval_potential_host(T, qh, uh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": n / e2e_s / 1e6, "unit": "Mpoints/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+           "ms_per_step": 1e3 * e2e_s}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(cfg, "FP32-compensated path"),
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "wall_s_timed": wall, "tree_build_ms": build_ms,
+        "stage_ms": stage_ms,
+        "tree": {k: st[k] for k in ("levels", "n_boxes", "n_m2l", "n_p2p", "n_p2p_pairs", "device_bytes")},
+    }
+
+    if not args.no_extras and world == 1:
+        import oracle
+        oracle.build()
+        tg = workloads.sample_targets(n, 4096, seed=1)
+        ud = oracle.direct(pos, q, targets=tg)
+        u32 = u_d.cpu().numpy()[tg]
+        # FP64 path on the same tree
+        fmm.fmm_tree_set_precision(T, fmm.FMM_FP64)
+        u64_d = fmm.fmm_eval_potential(T, q_d)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(2):
+            fmm.fmm_eval_potential(T, q_d, u64_d)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / 2
+        u64 = u64_d.cpu().numpy()[tg]
+        fmm.fmm_tree_set_precision(T, fmm.FMM_FP32C)
+        # backward (charges and positions) and field, FP32C
+        g_d = torch.from_numpy(np.random.default_rng(3).normal(size=n)).to(dev)
+        fmm.fmm_backward(T, q_d, g_d)
+        fmm.fmm_eval_field(T, q_d)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            fmm.fmm_backward(T, q_d, g_d)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_bwd = e0.elapsed_time(e1) / 3
+        e0.record()
+        for _ in range(3):
+            fmm.fmm_eval_field(T, q_d)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_field = e0.elapsed_time(e1) / 3
+        line["fp64"] = {"value": n / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
+                        "fp32c_speedup": ms64 / ms}
+        line["errors_vs_direct_4096_targets"] = {
+            "fp32c_rel_l2": rel_l2(u32, ud), "fp32c_rel_linf": rel_linf(u32, ud),
+            "fp64_rel_l2": rel_l2(u64, ud), "fp64_rel_linf": rel_linf(u64, ud),
+            "fp32c_vs_fp64_rel_l2": rel_l2(u32, u64)}
+        line["backward"] = {"ms": ms_bwd, "bwd_fwd_ratio": ms_bwd / ms,
+                            "what": "dL/dq and dL/dpos (two field evaluations + combine), FP32C"}
+        line["field"] = {"value": n / (ms_field * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms_field}
+        # CPU oracle baseline on bounded samples (rank 0, one GPU)
+        O = oracle.Tree(pos, cfg["leaf_size"], cfg["s"], cfg["theta"])
+        rng = np.random.default_rng(11)
+        pts, secs = 0, 0.0
+        for _ in range(3):
+            m, dt = oracle_sample_eval(O, q, cfg["p"], rng.choice(O.n_leaves, 32, replace=False), O.n_leaves)
+            pts += m
+            secs += dt
+        line["cpu_baseline"] = {
+            "value": pts / secs / 1e6, "unit": "Mpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "oracle FP64 FMM at every point of 3 x 32 random target leaves (%d points), "
+                      "full P2M/M2M of the 2^20-point tree included each time; %.1f s" % (pts, secs)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

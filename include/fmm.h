@@ -91,7 +91,23 @@ typedef struct {
   int64_t n_p2p_pairs;   /* near-field point pairs: sum over leaf pairs |S||T|  */
   size_t device_bytes;   /* device memory owned by the tree                     */
   double build_ms;       /* wall time of fmm_build_tree                         */
+  int64_t kernel_launches; /* kernels this library launched for evaluations of
+                              this tree so far                                  */
 } fmm_stats;
+
+/* Evaluation stages in launch order, named after the stages of Sec. III.A:
+ * sort (charges into tree order), evdir (P2P), mpls (P2M), M2M, M2L, L2L,
+ * evloc (L2P, near + far combination and inverse sort). */
+enum {
+  FMM_STAGE_SORT = 0,
+  FMM_STAGE_P2P = 1,
+  FMM_STAGE_P2M = 2,
+  FMM_STAGE_M2M = 3,
+  FMM_STAGE_M2L = 4,
+  FMM_STAGE_L2L = 5,
+  FMM_STAGE_L2P = 6,
+  FMM_NUM_STAGES = 7
+};
 
 /* Thread-local description of the last failure on this thread. */
 const char* fmm_last_error(void);
@@ -141,6 +157,15 @@ int fmm_tree_export(const fmm_tree* tree, int32_t* perm, int64_t* box_start,
                     int64_t* box_count, double* center, double* radius,
                     double* level_avg_radius, int32_t* m2l_trg, int32_t* m2l_src,
                     int32_t* p2p_trg, int32_t* p2p_src);
+
+/* Per-stage device timing.  enable = 1 clears the record and starts
+ * recording CUDA events around every stage of the next evaluation calls of
+ * this tree (on the stream they run on, up to 512 calls); enable = 0 stops.
+ * fmm_tree_stage_times synchronises the recorded events and writes the summed
+ * milliseconds per stage (FMM_NUM_STAGES doubles, host) and the number of
+ * recorded calls. */
+int fmm_tree_profile(fmm_tree* tree, int enable);
+int fmm_tree_stage_times(const fmm_tree* tree, double* ms, int64_t* calls);
 
 /* Potential u (n doubles) of charges q (n doubles) at the tree's points:
  * sort into tree order, P2M, M2M, M2L, L2L, L2P + P2P, inverse sort

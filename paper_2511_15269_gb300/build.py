@@ -26,7 +26,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "fmm.h")]
+    return (_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+            [GEN, os.path.join(ROOT, "include", "fmm.h")])
 
 
 def _compile(src, verbose):
@@ -38,8 +39,18 @@ def _compile(src, verbose):
     return obj, r.stderr
 
 
+GEN = os.path.join(CSRC, "gen_tables.py")
+GEN_OUT = os.path.join(CSRC, "tables_gen.h")
+
+
+def _generate():
+    if not os.path.exists(GEN_OUT) or os.path.getmtime(GEN_OUT) < os.path.getmtime(GEN):
+        subprocess.run([sys.executable, GEN, GEN_OUT], check=True)
+
+
 def build(force=False, verbose=False, jobs=None):
     """Compile every CUDA source for sm_103a and link libfmm_gb300.so."""
+    _generate()
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(p) for p in _deps())
         if os.path.getmtime(LIB) >= newest:

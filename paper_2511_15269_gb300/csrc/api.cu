@@ -39,10 +39,14 @@ void free_tree(fmm_tree* t) {
                   t->m2l_trg,  t->m2l_order, t->p2p_off,   t->p2p_src,  t->p2p32,    t->leaf_order, t->pos_local,
                   t->pos64,    t->inv_rho32, t->inv_rho64, t->geo32,    t->geo64,    t->m2m32,    t->m2m64,
                   t->l2l32,    t->l2l64,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
-                  t->Lam64,    t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
+                  t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
                   t->counters, t->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (t->prof_ev) {
+    for (int i = 0; i < fmm_tree::kProfCalls * (FMM_NUM_STAGES + 1); i++) cudaEventDestroy(t->prof_ev[i]);
+    delete[] t->prof_ev;
+  }
   delete[] t->level_avg_host;
   delete t;
 }
@@ -153,6 +157,38 @@ int fmm_tree_stats(const fmm_tree* t, fmm_stats* s) {
     s->n_p2p_pairs = t->n_p2p_pairs;
     s->device_bytes = t->device_bytes;
     s->build_ms = t->build_ms;
+    s->kernel_launches = t->launches;
+  });
+}
+
+int fmm_tree_profile(fmm_tree* t, int enable) {
+  return guarded([&] {
+    require(t != nullptr, "tree is NULL");
+    if (enable && !t->prof_ev) {
+      const int ne = fmm_tree::kProfCalls * (FMM_NUM_STAGES + 1);
+      t->prof_ev = new cudaEvent_t[ne];
+      for (int i = 0; i < ne; i++) FMM_CUDA_TRY(cudaEventCreate(&t->prof_ev[i]));
+    }
+    t->prof_on = enable ? 1 : 0;
+    if (enable) t->prof_used = 0;
+  });
+}
+
+int fmm_tree_stage_times(const fmm_tree* t, double* ms, int64_t* calls) {
+  return guarded([&] {
+    require(t != nullptr && ms != nullptr, "NULL argument");
+    for (int s = 0; s < FMM_NUM_STAGES; s++) ms[s] = 0.0;
+    if (calls) *calls = t->prof_ev ? t->prof_used : 0;
+    if (!t->prof_ev) return;
+    for (int c = 0; c < t->prof_used; c++) {
+      cudaEvent_t* ev = t->prof_ev + c * (FMM_NUM_STAGES + 1);
+      FMM_CUDA_TRY(cudaEventSynchronize(ev[FMM_NUM_STAGES]));
+      for (int s = 0; s < FMM_NUM_STAGES; s++) {
+        float x = 0.f;
+        FMM_CUDA_TRY(cudaEventElapsedTime(&x, ev[s], ev[s + 1]));
+        ms[s] += x;
+      }
+    }
   });
 }
 

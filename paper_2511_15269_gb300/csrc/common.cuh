@@ -63,9 +63,10 @@ __host__ __device__ constexpr int ncoef_pad(int p) { return (ncoef(p) + 3) & ~3;
 __host__ __device__ constexpr int m2l_fields(int p) { return 3 + 4 * p; }
 __host__ __device__ constexpr int edge_fields(int p) { return 2 + 4 * p; }
 
-// Near-field entry for the FP32 path: source leaf (bit 31 set when the two
-// leaves' bounding boxes touch, so coincident points are possible) and the
-// centre offset c_T - c_S rounded to FP32.
+// Near-field entry for the FP32 path: source leaf (bit 31 set when the tree
+// holds coincident points and the two leaves' bounding boxes touch, so that
+// zero distances are possible outside the self pair) and the centre offset
+// c_T - c_S rounded to FP32.
 struct __align__(16) P2PEntry {
   int src;
   float dx, dy, dz;
@@ -75,6 +76,12 @@ struct __align__(16) P2PEntry {
 // bulk copies.
 struct __align__(32) dvec4 {
   double x, y, z, w;
+};
+
+// FP32 near-field source record with every component duplicated
+// (x, x, y, y, z, z, q, q): 128-bit loads give packed f32x2 operands.
+struct __align__(32) DupRec {
+  float x0, x1, y0, y1, z0, z1, q0, q1;
 };
 
 }  // namespace fmm
@@ -87,6 +94,7 @@ struct fmm_tree {
   int64_t n_boxes = 0, n_leaves = 0;
   int64_t n_m2l = 0, n_p2p = 0, n_p2p_pairs = 0;
   int max_leaf = 0;          // largest leaf point count
+  int has_duplicates = 0;    // two distinct points share a position
   double build_ms = 0;
   size_t device_bytes = 0;
   double* level_avg_host = nullptr;  // L + 1
@@ -122,6 +130,7 @@ struct fmm_tree {
 
   // evaluation workspace
   float4* src32 = nullptr;       // n: (x_local, q) in tree order
+  fmm::DupRec* src_dup = nullptr;  // n: duplicated FP32 near-field records
   fmm::dvec4* src64 = nullptr;   // n: (x, q) in tree order
   float* M32 = nullptr;          // n_boxes x ncoef_pad(p)
   float* Lam32 = nullptr;
@@ -135,9 +144,26 @@ struct fmm_tree {
   double* g_stage = nullptr;     // 3 n (backward)
   int* counters = nullptr;       // work counters, reset before each launch
   int* status = nullptr;         // latched kernel status bits
+
+  // per-stage timing (fmm_tree_profile) and launch accounting
+  static constexpr int kProfCalls = 512;
+  cudaEvent_t* prof_ev = nullptr;      // kProfCalls x (FMM_NUM_STAGES + 1)
+  mutable int prof_on = 0;
+  mutable int prof_used = 0;
+  mutable int prof_cur = -1;           // slot of the call being recorded
+  mutable int64_t launches = 0;
 };
 
 namespace fmm {
+
+// Stage boundary i (0..FMM_NUM_STAGES) of the current evaluation call.
+inline void stage_mark(const fmm_tree* t, int i, cudaStream_t st) {
+  if (!t->prof_on) return;
+  if (i == 0) {
+    t->prof_cur = (t->prof_used < fmm_tree::kProfCalls) ? t->prof_used++ : -1;
+  }
+  if (t->prof_cur >= 0) cudaEventRecord(t->prof_ev[t->prof_cur * (FMM_NUM_STAGES + 1) + i], st);
+}
 
 // tree_build.cu
 void build_tree(fmm_tree* t, const double* pos, cudaStream_t st);
@@ -150,19 +176,7 @@ void eval_fp64(const fmm_tree* t, const double* q, double* u, double* field, cud
 void init_tables_fp32();
 void init_tables_fp64();
 
-// tables.cu: host-side FP64 constant tables (see there for the formulas).
-struct HostTables {
-  // dense per degree n: (2n+1)^2 entries at offset b_off(n)
-  double B[1771], Binv[1771];
-  double ax_m2l[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];  // [n][k][|m|]
-  double ax_m2m[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];
-  double ax_l2l[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];
-  double r_diag[kMaxP + 1];                 // regular-basis recursion constants
-  double r_sub[kMaxP + 1];
-  double r_a[(kMaxP + 1) * (kMaxP + 1)];    // [n][|m|]
-  double r_b[(kMaxP + 1) * (kMaxP + 1)];
-};
-const HostTables& host_tables();
+// Offset of degree n in the dense per-degree rotation tables.
 __host__ __device__ constexpr int b_off(int n) {
   // sum_{j<n} (2j+1)^2 = n (4n^2 - 1) / 3
   return n * (4 * n * n - 1) / 3;

@@ -53,12 +53,16 @@ __device__ __forceinline__ void load_coef(const real* src, real (&v)[ncoef(P)]) 
 // ---- E0: sort charges into tree order ----------------------------------------
 __global__ void gather_kernel(int64_t n, const int32_t* __restrict__ perm,
                               const double* __restrict__ q, const vec4* __restrict__ pos,
-                              vec4* __restrict__ src) {
+                              vec4* __restrict__ src, DupRec* __restrict__ dup) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     vec4 p = pos[i];
     p.w = (real)q[perm[i]];
     src[i] = p;
+    if (dup) {
+      const float x = (float)p.x, y = (float)p.y, z = (float)p.z, w = (float)p.w;
+      dup[i] = DupRec{x, x, y, y, z, z, w, w};
+    }
   }
 }
 
@@ -308,6 +312,79 @@ __device__ __forceinline__ void p2p_tile(const vec4* sb, int scount, const real 
   }
 }
 
+// Packed FP32 pairs (f32x2 arithmetic of sm_100-family GPUs): a 64-bit
+// register holds two FP32 lanes, one instruction updates both.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2pack(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(f2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 f2add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// MUFU reciprocal square root (denormal inputs flush to zero)
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// FP32 near-field tile: sources staged as (x, x, y, y, z, z, q, q) so that
+// each 128-bit shared load yields two packed operands; every lane updates its
+// NP packed target pairs.
+template <bool MASK, bool FIELD, int NP>
+__device__ __forceinline__ void p2p_tile_f32(const DupRec* sb, int scount, const f2 (&tx)[NP], const f2 (&ty)[NP],
+                                             const f2 (&tz)[NP], f2 (&pu)[NP], f2 (&fx)[NP], f2 (&fy)[NP],
+                                             f2 (&fz)[NP]) {
+  const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
+#pragma unroll 4
+  for (int j = 0; j < scount; j++) {
+    const ulonglong2 a = s2[2 * j];
+    const ulonglong2 b = s2[2 * j + 1];
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+      const f2 dx = f2sub(tx[k], a.x), dy = f2sub(ty[k], a.y), dz = f2sub(tz[k], b.x);
+      const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+      float r0, r1;
+      f2unpack(r2, r0, r1);
+      float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
+      if (MASK) {
+        i0 = (r0 > 0.f) ? i0 : 0.f;
+        i1 = (r1 > 0.f) ? i1 : 0.f;
+      }
+      const f2 ri = f2pack(i0, i1);
+      pu[k] = f2fma(b.y, ri, pu[k]);
+      if (FIELD) {
+        const f2 w = f2mul(f2mul(f2mul(ri, ri), ri), b.y);
+        fx[k] = f2fma(w, dx, fx[k]);
+        fy[k] = f2fma(w, dy, fy[k]);
+        fz[k] = f2fma(w, dz, fz[k]);
+      }
+    }
+  }
+}
+
 struct P2PArgs {
   int64_t n_leaves, leaf_off;
   const int32_t* order;
@@ -316,7 +393,9 @@ struct P2PArgs {
   const int32_t* ent_src;
   const int64_t* box_start;
   const int32_t* box_count;
-  const vec4* src;
+  const vec4* src;       // targets: (x_local, q) FP32 or (x, q) FP64
+  const void* tile;      // sources staged by the bulk copies, 32 bytes per point:
+                         // DupRec (FP32) or dvec4 (FP64)
   real* near_u;   // 2 per point (FP32: hi, lo) or 1 (FP64)
   real* near_f;   // 3 per point (FIELD)
   int* counter;
@@ -327,8 +406,11 @@ template <int TPL, bool FIELD>
 __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
   constexpr int CAP = TPL * 32;
   constexpr int WARPS = 4;
+  constexpr int NP = TPL >= 2 ? TPL / 2 : 1;  // packed target pairs per lane (FP32)
+  using rec = typename std::conditional<kF32, DupRec, dvec4>::type;
   extern __shared__ __align__(128) unsigned char p2p_smem[];
-  vec4 (*sbuf)[2][CAP] = reinterpret_cast<vec4 (*)[2][CAP]>(p2p_smem);  // [WARPS][2][CAP]
+  rec (*sbuf)[2][CAP] = reinterpret_cast<rec (*)[2][CAP]>(p2p_smem);  // [WARPS][2][CAP]
+  const rec* tile = reinterpret_cast<const rec*>(a.tile);
   __shared__ __align__(8) uint64_t bars[WARPS][2];
   const int lane = lane_id();
   const int warp = threadIdx.x >> 5;
@@ -374,7 +456,7 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
       const int64_t gs = a.leaf_off + src_leaf(e);
       if (lane == 0) {
         fence_proxy_async();
-        tma_load_1d(sbuf[warp][buf], a.src + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(vec4)),
+        tma_load_1d(sbuf[warp][buf], tile + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(rec)),
                     &bar[buf]);
       }
     };
@@ -394,38 +476,52 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
       phase ^= 1u << buf;
       const int ls = src_leaf(e);
       const int scount = a.box_count[a.leaf_off + ls];
-      real tx[TPL], ty[TPL], tz[TPL];
-      bool mask;
-      if (kF32) {
+      if constexpr (kF32) {
         const P2PEntry en = a.ent32[e];
-        mask = (en.src < 0) || (ls == (int)leaf);
+        const bool mask = (en.src < 0) || (ls == (int)leaf);
+        const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
+        f2 tx[NP], ty[NP], tz[NP], pu[NP], px[NP], py[NP], pz[NP];
 #pragma unroll
-        for (int k = 0; k < TPL; k++) {
-          tx[k] = tx0[k] + (real)en.dx;
-          ty[k] = ty0[k] + (real)en.dy;
-          tz[k] = tz0[k] + (real)en.dz;
+        for (int k = 0; k < NP; k++) {
+          const int k1 = (2 * k + 1 < TPL) ? 2 * k + 1 : 2 * k;
+          tx[k] = f2add(f2pack(tx0[2 * k], tx0[k1]), ddx);
+          ty[k] = f2add(f2pack(ty0[2 * k], ty0[k1]), ddy);
+          tz[k] = f2add(f2pack(tz0[2 * k], tz0[k1]), ddz);
+          pu[k] = px[k] = py[k] = pz[k] = 0ull;
+        }
+        if (mask) p2p_tile_f32<true, FIELD, NP>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz);
+        else p2p_tile_f32<false, FIELD, NP>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz);
+#pragma unroll
+        for (int k = 0; k < NP; k++) {
+          float u0, u1, x0, x1, y0, y1, z0, z1;
+          f2unpack(pu[k], u0, u1);
+          f2unpack(px[k], x0, x1);
+          f2unpack(py[k], y0, y1);
+          f2unpack(pz[k], z0, z1);
+          two_sum(hi[2 * k], lo[2 * k], (real)u0);
+          fx[2 * k] += (real)x0;
+          fy[2 * k] += (real)y0;
+          fz[2 * k] += (real)z0;
+          if (2 * k + 1 < TPL) {
+            two_sum(hi[2 * k + 1], lo[2 * k + 1], (real)u1);
+            fx[2 * k + 1] += (real)x1;
+            fy[2 * k + 1] += (real)y1;
+            fz[2 * k + 1] += (real)z1;
+          }
         }
       } else {
-        mask = true;
+        real pu[TPL], px[TPL], py[TPL], pz[TPL];
+#pragma unroll
+        for (int k = 0; k < TPL; k++) pu[k] = px[k] = py[k] = pz[k] = real(0);
+        p2p_tile<true, FIELD, TPL>(reinterpret_cast<const vec4*>(sbuf[warp][buf]), scount, tx0, ty0, tz0, pu, px,
+                                   py, pz);
 #pragma unroll
         for (int k = 0; k < TPL; k++) {
-          tx[k] = tx0[k];
-          ty[k] = ty0[k];
-          tz[k] = tz0[k];
+          hi[k] += pu[k];
+          fx[k] += px[k];
+          fy[k] += py[k];
+          fz[k] += pz[k];
         }
-      }
-      real pu[TPL], px[TPL], py[TPL], pz[TPL];
-#pragma unroll
-      for (int k = 0; k < TPL; k++) pu[k] = px[k] = py[k] = pz[k] = real(0);
-      if (mask) p2p_tile<true, FIELD, TPL>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz);
-      else p2p_tile<false, FIELD, TPL>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz);
-#pragma unroll
-      for (int k = 0; k < TPL; k++) {
-        if (kF32) two_sum(hi[k], lo[k], pu[k]);
-        else hi[k] += pu[k];
-        fx[k] += px[k];
-        fy[k] += py[k];
-        fz[k] += pz[k];
       }
       __syncwarp();
     }
@@ -580,6 +676,8 @@ void run_far(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   p2m_kernel<P><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
       t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, pp.src, pp.inv_rho, pp.M);
   FMM_LAUNCH_CHECK();
+  t->launches += 1 + 2 * L + 1;
+  stage_mark(t, FMM_STAGE_M2M, st);
   for (int l = L - 1; l >= 0; l--) {
     const int64_t nchild = (int64_t)1 << (s * (l + 1));
     m2m_kernel<P><<<grid_for(nchild, 128, 1 << 30), 128, 0, st>>>(nchild, loff(l + 1), loff(l), nch,
@@ -592,6 +690,7 @@ void run_far(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set = true;
   }
+  stage_mark(t, FMM_STAGE_M2L, st);
   FMM_CUDA_TRY(cudaMemsetAsync(t->counters, 0, sizeof(int), st));
   int dev = 0, nsm = 0, occ = 0;
   FMM_CUDA_TRY(cudaGetDevice(&dev));
@@ -604,6 +703,7 @@ void run_far(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   m2l_kernel<P><<<(int)blocks, 128, smem, st>>>(t->n_boxes, t->m2l_order, t->m2l_off, t->m2l_src,
                                                 pp.geo, t->n_m2l, pp.M, pp.Lam, t->counters);
   FMM_LAUNCH_CHECK();
+  stage_mark(t, FMM_STAGE_L2L, st);
   for (int l = 1; l <= L; l++) {
     const int64_t nb = (int64_t)1 << (s * l);
     l2l_kernel<P><<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(nb, loff(l), loff(l - 1), s, pp.l2l,
@@ -617,6 +717,7 @@ void run_l2p(const fmm_tree* t, const Ptrs& pp, const real* near_u, const real* 
              double* field, cudaStream_t st) {
   int64_t leaf_off = 0;
   for (int i = 0; i < t->L; i++) leaf_off += (int64_t)1 << (t->s * i);
+  t->launches += 1;
   if (field)
     l2p_kernel<P, true><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
         t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
@@ -642,12 +743,13 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
   a.box_start = t->box_start;
   a.box_count = t->box_count;
   a.src = pp.src;
+  a.tile = kF32 ? (const void*)t->src_dup : (const void*)pp.src;
   a.near_u = near_u;
   a.near_f = near_f;
   a.counter = t->counters + 1;
   a.status = t->status;
   FMM_CUDA_TRY(cudaMemsetAsync(t->counters + 1, 0, sizeof(int), st));
-  const size_t smem = (size_t)4 * 2 * TPL * 32 * sizeof(vec4);
+  const size_t smem = (size_t)4 * 2 * TPL * 32 * 32;  // 32-byte records
   static bool attr_set = false;
   if (!attr_set) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -663,6 +765,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
   int64_t blocks = (int64_t)nsm * occ;
   const int64_t need = (t->n_leaves + 3) / 4;
   if (blocks > need) blocks = need;
+  t->launches += 1;
   if (field) p2p_kernel<TPL, true><<<(int)blocks, 128, smem, st>>>(a);
   else p2p_kernel<TPL, false><<<(int)blocks, 128, smem, st>>>(a);
   FMM_LAUNCH_CHECK();
@@ -694,17 +797,24 @@ void dispatch_p(int p, F&& f) {
 
 void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
   Ptrs pp = ptrs(t);
-  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->perm, q, pp.pos, pp.src);
+  stage_mark(t, FMM_STAGE_SORT, st);
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->perm, q, pp.pos, pp.src,
+                                                     kF32 ? t->src_dup : nullptr);
   FMM_LAUNCH_CHECK();
+  t->launches += 1;
   // near field first (largest kernel), then the far-field chain
   real* near_u = reinterpret_cast<real*>(t->near_u);
   real* near_f = reinterpret_cast<real*>(t->near_f);
+  stage_mark(t, FMM_STAGE_P2P, st);
   run_p2p(t, pp, near_u, near_f, field != nullptr, st);
+  stage_mark(t, FMM_STAGE_P2M, st);
   dispatch_p(t->prm.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
     run_far<P>(t, pp, st);
+    stage_mark(t, FMM_STAGE_L2P, st);
     run_l2p<P>(t, pp, near_u, near_f, u, field, st);
   });
+  stage_mark(t, FMM_NUM_STAGES, st);
 }
 
 }  // namespace

@@ -1,37 +1,50 @@
 // Device-side expansion algebra, compiled once per precision: the including
 // translation unit defines `real` (float or double) before including this
-// header, and uploads the constant tables with upload_tables().
+// header.  Table entries come from tables_gen.h (written by gen_tables.py).
 //
-// Expansions live in the normalised, radius-scaled real basis described in
-// tables.cu.  Coefficient (n, m) of an order-P expansion is v[n*n + n + m].
-// All loops run over compile-time bounds and are fully unrolled, so the
-// coefficient vector stays in registers and every table entry is a constant
-// bank operand.
+// Coefficient (n, m) of an order-P expansion is v[n*n + n + m].  All loops
+// run over compile-time indices, so the coefficient vector stays in registers
+// and every table entry is an instruction immediate (no constant-bank
+// traffic).
 #pragma once
+//
+// The kernels keep expansions in a normalised, radius-scaled real basis:
+//   multipole  M^m_n = C^m_n K_n^m / rho^n,
+//   local      L^m_n = +-D^m_n rho^n / K_n^m   (minus sign for m < 0),
+// with C, D the real coefficients of Sec. II.C, K_n^m = sqrt((n-|m|)!(n+|m|)!)
+// and rho the box's scaling radius.  In this basis the azimuthal rotation of
+// App. B.1 has the same form for multipoles and locals, and the polar
+// rotation of App. B.2 is W^m_{n,k}(beta) for both (the N^m_{n,k} factors
+// cancel).  A polar rotation is evaluated as Y(beta) = B^-1 Z(beta) B with the
+// fixed per-degree matrices
+//   B = Y(-pi/2) Z(-pi/2),   B^-1 = Z(pi/2) Y(pi/2),
+// which follow from turning about y = (quarter turn taking y to z) o (turn
+// about z) o (its inverse).  Y(+-pi/2) uses Wigner elements at a right angle,
+//   d^n_{m,k}(pi/2) = 2^-n sqrt((n+m)!(n-m)!/((n+k)!(n-k)!))
+//                     * sum_t (-1)^(m-k+t) C(n+k, t) C(n-k, n-m-t),
+// whose sum is an exact integer.  About a quarter of B's entries vanish by
+// parity, which the kernels skip at compile time.
+//
+// Diagonal (axial) transforms of App. B.3 in the scaled basis, for a shift of
+// length r along +z, with u_S = rho_S/r, u_T = rho_T/r, a = r/rho_P,
+// b = rho_C/rho_P:
+//   M2L  L^m_n = sum_k (-1)^(k+m) (n+k)!/(K_n^m K_k^m) u_T^n u_S^k / r  M^m_k
+//   M2M  M'^m_n = sum_{k<=n} sqrt(C(n-|m|,k-|m|) C(n+|m|,k+|m|)) a^(n-k) b^k M^m_k
+//   L2L  L'^m_n = sum_{k>=n} (-1)^(k-n) sqrt(C(k-|m|,n-|m|) C(k+|m|,n+|m|)) a^(k-n) b^n L^m_k
+// Normalised regular basis Rt^m_n = K_n^m R^m_n (App. A.1 times K):
+//   Rt^0_0 = 1, Rt^1_1 = x/sqrt2, Rt^-1_1 = -y/sqrt2,
+//   Rt^+-n_n = sqrt((2n-1)/(2n)) (x Rt.. +- y Rt..)          (diagonal)
+//   Rt^+-n_{n+1} = sqrt(2n+1) z Rt^+-n_n                      (sub-diagonal)
+//   Rt^m_n = (2n-1)/sqrt((n-m)(n+m)) z Rt^m_{n-1}
+//            - sqrt((n-m-1)(n+m-1)/((n-m)(n+m))) r^2 Rt^m_{n-2}
 
 #include <type_traits>
 
 #include "common.cuh"
+#include "tables_gen.h"
 
 namespace fmm {
 namespace {
-
-__constant__ real c_B[1771];
-__constant__ real c_Bi[1771];
-__constant__ real c_ax_m2l[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];
-__constant__ real c_ax_m2m[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];
-__constant__ real c_ax_l2l[(kMaxP + 1) * (kMaxP + 1) * (kMaxP + 1)];
-__constant__ real c_rdiag[kMaxP + 1];
-__constant__ real c_rsub[kMaxP + 1];
-__constant__ real c_ra[(kMaxP + 1) * (kMaxP + 1)];
-__constant__ real c_rb[(kMaxP + 1) * (kMaxP + 1)];
-
-template <class Dst>
-void upload(const Dst& sym, const double* src, size_t count) {
-  real tmp[1771];
-  for (size_t i = 0; i < count; i++) tmp[i] = (real)src[i];
-  FMM_CUDA_TRY(cudaMemcpyToSymbol(sym, tmp, sizeof(real) * count));
-}
 
 // Parity pattern of the quarter-turn polar rotation in the internal basis:
 // entry (row order m, source order l) of Y(+-pi/2) can be nonzero only if
@@ -47,28 +60,17 @@ __host__ __device__ constexpr int qmap(int m) { return ((m < 0 ? -m : m) % 2 == 
 __host__ __device__ constexpr bool b_nz(int n, int i, int j) { return ymask(n, i - n, qmap(j - n)); }
 __host__ __device__ constexpr bool bi_nz(int n, int i, int j) { return ymask(n, qmap(i - n), j - n); }
 
+// Every structurally skipped entry of B and B^-1 must be zero.
 void upload_tables() {
-  const HostTables& T = host_tables();
-  // every entry the kernels skip must be zero
   for (int n = 0; n <= kMaxP; n++)
     for (int i = 0; i <= 2 * n; i++)
       for (int j = 0; j <= 2 * n; j++) {
-        int id = b_off(n) + i * (2 * n + 1) + j;
-        if ((!b_nz(n, i, j) && T.B[id] != 0.0 && std::fabs(T.B[id]) > 1e-13) ||
-            (!bi_nz(n, i, j) && T.Binv[id] != 0.0 && std::fabs(T.Binv[id]) > 1e-13)) {
+        const int id = b_off(n) + i * (2 * n + 1) + j;
+        if ((!b_nz(n, i, j) && gen::kB[id] != 0.0) || (!bi_nz(n, i, j) && gen::kBi[id] != 0.0)) {
           set_error("rotation table sparsity check failed at degree %d (%d, %d)", n, i, j);
           throw Fail{FMM_ERR_CUDA};
         }
       }
-  upload(c_B, T.B, 1771);
-  upload(c_Bi, T.Binv, 1771);
-  upload(c_ax_m2l, T.ax_m2l, 1331);
-  upload(c_ax_m2m, T.ax_m2m, 1331);
-  upload(c_ax_l2l, T.ax_l2l, 1331);
-  upload(c_rdiag, T.r_diag, kMaxP + 1);
-  upload(c_rsub, T.r_sub, kMaxP + 1);
-  upload(c_ra, T.r_a, 121);
-  upload(c_rb, T.r_b, 121);
 }
 
 template <int B, int E, class F>
@@ -120,8 +122,10 @@ __device__ __forceinline__ void apply_b(real (&v)[ncoef(P)]) {
       sfor<0, w>([&](auto jj) {
         constexpr int j = decltype(jj)::value;
         constexpr bool nz = INV ? bi_nz(n, i, j) : b_nz(n, i, j);
-        if constexpr (nz) acc = fmar(INV ? c_Bi[b_off(n) + i * w + j] : c_B[b_off(n) + i * w + j],
-                                     v[n * n + j], acc);
+        if constexpr (nz) {
+          constexpr double c = INV ? gen::kBi[b_off(n) + i * w + j] : gen::kB[b_off(n) + i * w + j];
+          if constexpr (c != 0.0) acc = fmar(real(c), v[n * n + j], acc);
+        }
       });
       out[i] = acc;
     });
@@ -164,20 +168,23 @@ __device__ __forceinline__ void axial_m2l(real (&v)[ncoef(P)], real uS, real uT,
     pS[k] = pS[k - 1] * uS;
     pT[k] = pT[k - 1] * uT;
   }
-#pragma unroll
-  for (int m = -P; m <= P; m++) {
-    const int am = m < 0 ? -m : m;
+  sfor<0, 2 * P + 1>([&](auto mm) {
+    constexpr int m = decltype(mm)::value - P;
+    constexpr int am = m < 0 ? -m : m;
     real in[P + 1];
 #pragma unroll
     for (int k = am; k <= P; k++) in[k] = v[ix(k, m)] * pS[k];
-#pragma unroll
-    for (int n = am; n <= P; n++) {
+    sfor<am, P + 1>([&](auto nn) {
+      constexpr int n = decltype(nn)::value;
       real acc = real(0);
-#pragma unroll
-      for (int k = am; k <= P; k++) acc = fmar(c_ax_m2l[ax_id(n, k, am)], in[k], acc);
+      sfor<am, P + 1>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr double c = gen::kAxM2L[ax_id(n, k, am)];
+        acc = fmar(real(c), in[k], acc);
+      });
       v[ix(n, m)] = acc * pT[n];
-    }
-  }
+    });
+  });
 }
 
 // Axial M2M (App. B.3), a = r/rho_parent, b = rho_child/rho_parent.
@@ -191,20 +198,23 @@ __device__ __forceinline__ void axial_m2m(real (&v)[ncoef(P)], real a, real b) {
     pA[k] = pA[k - 1] * a;
     pB[k] = pB[k - 1] * b;
   }
-#pragma unroll
-  for (int m = -P; m <= P; m++) {
-    const int am = m < 0 ? -m : m;
+  sfor<0, 2 * P + 1>([&](auto mm) {
+    constexpr int m = decltype(mm)::value - P;
+    constexpr int am = m < 0 ? -m : m;
     real in[P + 1];
 #pragma unroll
     for (int k = am; k <= P; k++) in[k] = v[ix(k, m)] * pB[k];
-#pragma unroll
-    for (int n = P; n >= am; n--) {
+    sfor<am, P + 1>([&](auto nn) {
+      constexpr int n = decltype(nn)::value;
       real acc = real(0);
-#pragma unroll
-      for (int k = am; k <= n; k++) acc = fmar(c_ax_m2m[ax_id(n, k, am)] * pA[n - k], in[k], acc);
+      sfor<am, n + 1>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr double c = gen::kAxM2M[ax_id(n, k, am)];
+        acc = fmar(real(c) * pA[n - k], in[k], acc);
+      });
       v[ix(n, m)] = acc;
-    }
-  }
+    });
+  });
 }
 
 // Axial L2L (App. B.3), a = r/rho_parent, b = rho_child/rho_parent.
@@ -218,20 +228,23 @@ __device__ __forceinline__ void axial_l2l(real (&v)[ncoef(P)], real a, real b) {
     pA[k] = pA[k - 1] * a;
     pB[k] = pB[k - 1] * b;
   }
-#pragma unroll
-  for (int m = -P; m <= P; m++) {
-    const int am = m < 0 ? -m : m;
+  sfor<0, 2 * P + 1>([&](auto mm) {
+    constexpr int m = decltype(mm)::value - P;
+    constexpr int am = m < 0 ? -m : m;
     real in[P + 1];
 #pragma unroll
     for (int k = am; k <= P; k++) in[k] = v[ix(k, m)];
-#pragma unroll
-    for (int n = am; n <= P; n++) {
+    sfor<am, P + 1>([&](auto nn) {
+      constexpr int n = decltype(nn)::value;
       real acc = real(0);
-#pragma unroll
-      for (int k = n; k <= P; k++) acc = fmar(c_ax_l2l[ax_id(n, k, am)] * pA[k - n], in[k], acc);
+      sfor<n, P + 1>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr double c = gen::kAxL2L[ax_id(n, k, am)];
+        acc = fmar(real(c) * pA[k - n], in[k], acc);
+      });
       v[ix(n, m)] = acc * pB[n];
-    }
-  }
+    });
+  });
 }
 
 // Normalised regular basis Rt(y) up to degree P (recursions in tables.cu),
@@ -251,18 +264,21 @@ __device__ __forceinline__ void regular_basis(real x, real y, real z, real (&R)[
   }
   sfor<2, P + 1>([&](auto nn) {
     constexpr int n = decltype(nn)::value;
-    const real cd = c_rdiag[n];
+    constexpr double cdd = gen::kRDiag[n];
+    const real cd = real(cdd);
     R[ix(n, n)] = cd * fmar(x, R[ix(n - 1, n - 1)], y * R[ix(n - 1, 1 - n)]);
     R[ix(n, -n)] = cd * fmar(x, R[ix(n - 1, 1 - n)], -y * R[ix(n - 1, n - 1)]);
-    const real zs = c_rsub[n - 1] * z;
+    constexpr double csub = gen::kRSub[n - 1];
+    const real zs = real(csub) * z;
     R[ix(n, n - 1)] = zs * R[ix(n - 1, n - 1)];
     R[ix(n, 1 - n)] = zs * R[ix(n - 1, 1 - n)];
-#pragma unroll
-    for (int m = 2 - n; m <= n - 2; m++) {
-      const int am = m < 0 ? -m : m;
-      R[ix(n, m)] = fmar(c_ra[n * (kMaxP + 1) + am] * z, R[ix(n - 1, m)],
-                         -(c_rb[n * (kMaxP + 1) + am] * r2) * R[ix(n - 2, m)]);
-    }
+    sfor<0, 2 * n - 3>([&](auto mm) {
+      constexpr int m = decltype(mm)::value + 2 - n;
+      constexpr int am = m < 0 ? -m : m;
+      constexpr double ca = gen::kRA[n * (kMaxP + 1) + am];
+      constexpr double cb = gen::kRB[n * (kMaxP + 1) + am];
+      R[ix(n, m)] = fmar(real(ca) * z, R[ix(n - 1, m)], -(real(cb) * r2) * R[ix(n - 2, m)]);
+    });
     consume(nn);
   });
 }

@@ -748,23 +748,59 @@ __global__ void edge_geo_kernel(int64_t nbox, int s, const double* __restrict__ 
   m32[nbox + g] = l32[nbox + g] = (float)bb;
 }
 
-// near-field entries: source leaf, FP32 centre offset, touching-box flag
+// Are two distinct points at exactly the same position?  Open-addressing
+// hash table over the coordinate bits (splitmix64 finaliser), load factor
+// <= 1/2, probing bounded by the table size.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__global__ void duplicate_kernel(const double* __restrict__ X, int64_t n, int* __restrict__ tab, int64_t mask,
+                                 int* __restrict__ found) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = X[i], y = X[n + i], z = X[2 * n + i];
+    unsigned long long h = mix64((unsigned long long)__double_as_longlong(x));
+    h = mix64(h ^ (unsigned long long)__double_as_longlong(y));
+    h = mix64(h ^ (unsigned long long)__double_as_longlong(z));
+    int64_t slot = (int64_t)(h & (unsigned long long)mask);
+    for (int64_t probe = 0; probe <= mask; probe++) {
+      const int prev = atomicCAS(&tab[slot], -1, (int)i);
+      if (prev == -1) break;
+      if (X[prev] == x && X[n + prev] == y && X[2 * n + prev] == z) {
+        atomicOr(found, 1);
+        break;
+      }
+      slot = (slot + 1) & mask;
+    }
+  }
+}
+
+// near-field entries: source leaf, FP32 centre offset, and the flag that
+// zero distances are possible (coincident points exist and the leaves'
+// bounding boxes touch)
 __global__ void p2p_entry_kernel(const int32_t* __restrict__ pt, const int32_t* __restrict__ ps, int64_t np,
                                  int64_t leaf_off, const double* __restrict__ center,
                                  const double* __restrict__ lo, const double* __restrict__ hi,
-                                 const int32_t* __restrict__ bc, P2PEntry* __restrict__ ent,
+                                 const int32_t* __restrict__ bc, int has_dup, P2PEntry* __restrict__ ent,
                                  unsigned long long* __restrict__ pairs) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t gt = leaf_off + pt[e], gs = leaf_off + ps[e];
-    bool touch = true;
-    for (int a = 0; a < 3; a++) touch = touch && lo[3 * gt + a] <= hi[3 * gs + a] && lo[3 * gs + a] <= hi[3 * gt + a];
-    P2PEntry en;
-    en.src = ps[e] | (touch ? (int)0x80000000 : 0);
-    en.dx = (float)(center[3 * gt] - center[3 * gs]);
-    en.dy = (float)(center[3 * gt + 1] - center[3 * gs + 1]);
-    en.dz = (float)(center[3 * gt + 2] - center[3 * gs + 2]);
-    ent[e] = en;
-    atomicAdd(pairs, (unsigned long long)bc[gt] * (unsigned long long)bc[gs]);
+  for (int64_t e0 = (blockIdx.x * (int64_t)blockDim.x) & ~31ll; e0 < np; e0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = e0 + (threadIdx.x & 31) + (threadIdx.x & ~31);
+    unsigned long long w = 0;
+    if (e < np) {
+      const int64_t gt = leaf_off + pt[e], gs = leaf_off + ps[e];
+      bool touch = has_dup != 0;
+      for (int a = 0; a < 3; a++) touch = touch && lo[3 * gt + a] <= hi[3 * gs + a] && lo[3 * gs + a] <= hi[3 * gt + a];
+      P2PEntry en;
+      en.src = ps[e] | (touch ? (int)0x80000000 : 0);
+      en.dx = (float)(center[3 * gt] - center[3 * gs]);
+      en.dy = (float)(center[3 * gt + 1] - center[3 * gs + 1]);
+      en.dz = (float)(center[3 * gt + 2] - center[3 * gs + 2]);
+      ent[e] = en;
+      w = (unsigned long long)bc[gt] * (unsigned long long)bc[gs];
+    }
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(pairs, w);
   }
 }
 
@@ -833,6 +869,20 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     cudaFree(Xa), cudaFree(Xb), cudaFree(Ia), cudaFree(Ib), cudaFree(flag);
     require(false, "positions must be finite");
   }
+  int has_dup = 0;
+  {
+    int64_t tsize = 1;
+    while (tsize < 2 * n) tsize <<= 1;
+    int* tab = scratch_alloc<int>(tsize);
+    FMM_CUDA_TRY(cudaMemsetAsync(tab, 0xff, sizeof(int) * tsize, st));
+    FMM_CUDA_TRY(cudaMemsetAsync(flag + 1, 0, sizeof(int), st));
+    duplicate_kernel<<<grid_for(n, 256), 256, 0, st>>>(Xa, n, tab, tsize - 1, flag + 1);
+    FMM_LAUNCH_CHECK();
+    FMM_CUDA_TRY(cudaMemcpyAsync(&has_dup, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(tab);
+  }
+  t->has_duplicates = has_dup;
 
   // ---- segment boundaries of every round (closed form) ----
   std::vector<int64_t> round_off(R + 2);
@@ -936,9 +986,11 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   // ---- average radius per level ----
   t->level_avg_host = new double[L + 1];
   {
-    double* pa = scratch_alloc<double>(std::max<int64_t>(NL, 1));
-    double* pb = scratch_alloc<double>(std::max<int64_t>(NL / 2, 1));
+    double* buf0 = scratch_alloc<double>(std::max<int64_t>(NL, 1));
+    double* buf1 = scratch_alloc<double>(std::max<int64_t>(NL, 1));
     for (int l = 0; l <= L; l++) {
+      double* pa = buf0;
+      double* pb = buf1;
       int64_t m = (int64_t)1 << (s * l);
       FMM_CUDA_TRY(cudaMemcpyAsync(pa, t->radius + level_offset(l, s), sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
       while (m > 1) {
@@ -952,7 +1004,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
       FMM_CUDA_TRY(cudaStreamSynchronize(st));
       t->level_avg_host[l] = sum / (double)((int64_t)1 << (s * l));
     }
-    cudaFree(pa), cudaFree(pb);
+    cudaFree(buf0), cudaFree(buf1);
   }
 
   // ---- level march ----
@@ -1095,7 +1147,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     FMM_CUDA_TRY(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), st));
     if (np > 0) {
       p2p_entry_kernel<<<grid_for(np, 256), 256, 0, st>>>(p2p_trg, t->p2p_src, np, leaf_off, t->center, blo, bhi,
-                                                          t->box_count, t->p2p32, pairs);
+                                                          t->box_count, has_dup, t->p2p32, pairs);
       FMM_LAUNCH_CHECK();
     }
     unsigned long long hp = 0;
@@ -1131,6 +1183,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   // ---- evaluation workspace ----
   const int NCP = ncoef_pad(p);
   t->src32 = dev_alloc<float4>(t, n);
+  t->src_dup = dev_alloc<DupRec>(t, n);
   t->src64 = dev_alloc<dvec4>(t, n);
   t->M32 = dev_alloc<float>(t, (size_t)NB * NCP);
   t->Lam32 = dev_alloc<float>(t, (size_t)NB * NCP);

@@ -22,7 +22,9 @@ FMM_MAX_P = 10
 # exported entry points, in include/fmm.h order
 ENTRY_POINTS = ["fmm_last_error", "fmm_num_levels", "fmm_build_tree", "fmm_tree_free",
                 "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_export",
-                "fmm_eval_potential", "fmm_eval_field", "fmm_eval_potential_host", "fmm_backward"]
+                "fmm_tree_profile", "fmm_tree_stage_times", "fmm_eval_potential", "fmm_eval_field",
+                "fmm_eval_potential_host", "fmm_backward"]
+STAGES = ["sort", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p"]
 
 
 class FmmError(RuntimeError):
@@ -41,7 +43,7 @@ class fmm_stats(C.Structure):
                 ("leaf_size", C.c_int), ("precision", C.c_int), ("theta", C.c_double),
                 ("n_boxes", C.c_int64), ("n_leaves", C.c_int64), ("n_m2l", C.c_int64),
                 ("n_p2p", C.c_int64), ("n_p2p_pairs", C.c_int64), ("device_bytes", C.c_size_t),
-                ("build_ms", C.c_double)]
+                ("build_ms", C.c_double), ("kernel_launches", C.c_int64)]
 
 
 def library_path():
@@ -67,6 +69,8 @@ def lib():
         L.fmm_tree_stats.argtypes = [vp, C.POINTER(fmm_stats)]
         L.fmm_tree_status.argtypes = [vp, vp]
         L.fmm_tree_export.argtypes = [vp] * 11
+        L.fmm_tree_profile.argtypes = [vp, i]
+        L.fmm_tree_stage_times.argtypes = [vp, vp, vp]
         L.fmm_eval_potential.argtypes = [vp, vp, vp, vp]
         L.fmm_eval_field.argtypes = [vp, vp, vp, vp, vp]
         L.fmm_eval_potential_host.argtypes = [vp, vp, vp, vp]
@@ -173,6 +177,19 @@ def fmm_tree_export(tree):
             "m2l_src", "p2p_trg", "p2p_src"]
     _check(lib().fmm_tree_export(tree.handle, *[C.c_void_p(out[k].ctypes.data) for k in keys]))
     return out
+
+
+def fmm_tree_profile(tree, enable=True):
+    _check(lib().fmm_tree_profile(tree.handle, int(bool(enable))))
+
+
+def fmm_tree_stage_times(tree):
+    """(dict stage -> summed ms, number of recorded calls)."""
+    import numpy as np
+    ms = np.zeros(len(STAGES))
+    calls = C.c_int64()
+    _check(lib().fmm_tree_stage_times(tree.handle, C.c_void_p(ms.ctypes.data), C.byref(calls)))
+    return dict(zip(STAGES, ms.tolist())), calls.value
 
 
 def fmm_eval_potential(tree, q, out=None):

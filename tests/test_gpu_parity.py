@@ -106,6 +106,7 @@ POT_CASES = [
     ("cube6k_s1_p3", lambda: workloads.uniform_cube(6000, 5), 3, 16, 1, 0.5),
     ("cube3k_p1", lambda: workloads.uniform_cube(3000, 6), 1, 32, 2, 0.5),
     ("ragged_p5_leaf200", lambda: workloads.uniform_cube(7777, 7), 5, 200, 2, 0.5),
+    ("duplicates_p6", lambda: (dup_grid(5000, 8), np.random.default_rng(8).uniform(-1, 1, 5000)), 6, 16, 2, 0.5),
 ]
 
 
