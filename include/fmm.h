@@ -183,6 +183,28 @@ int fmm_eval_field(const fmm_tree* tree, const double* q, double* u, double* fie
 int fmm_eval_potential_host(const fmm_tree* tree, const double* q_host, double* u_host,
                             void* stream);
 
+/* Allocation-free variant of fmm_eval_potential (the paper has no
+ * counterpart; it serves callers that may not allocate device memory at
+ * evaluation time: code whose device memory budget belongs to another
+ * allocator, latency-critical loops that cannot absorb cudaMalloc's implicit
+ * synchronisation, plug-ins allowed to allocate only at start-up).
+ * Same inputs, outputs and results as fmm_eval_potential, but the per-call
+ * scratch (point records, near-field sums, expansions, work counters) lives
+ * in one file-scope device array of FMM_STATIC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.  It calls no
+ * cudaMalloc/cudaFree and no allocating library routine.
+ *   Limits: tree->n <= FMM_STATIC_MAX_POINTS and n_boxes <=
+ *   FMM_STATIC_MAX_BOXES, else FMM_ERR_CAPACITY with a message.
+ *   The first call on a device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents (the
+ *   work counters are cleared by each call before use): calls that overlap
+ *   on the GPU, on any streams or trees, race and must be ordered. */
+#define FMM_STATIC_MAX_POINTS 65536
+#define FMM_STATIC_MAX_BOXES 5461
+#define FMM_STATIC_SCRATCH_BYTES 16602368
+int fmm_eval_potential_static(const fmm_tree* tree, const double* q, double* u, void* stream);
+
 /* Vector-Jacobian product of u = K q at the tree's fixed geometry, for a loss
  * L(u) with grad_u = dL/du (n doubles):
  *     grad_q   = K grad_u                               (K is symmetric)

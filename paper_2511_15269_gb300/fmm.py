@@ -23,7 +23,7 @@ FMM_MAX_P = 10
 ENTRY_POINTS = ["fmm_last_error", "fmm_num_levels", "fmm_build_tree", "fmm_tree_free",
                 "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_export",
                 "fmm_tree_profile", "fmm_tree_stage_times", "fmm_eval_potential", "fmm_eval_field",
-                "fmm_eval_potential_host", "fmm_backward"]
+                "fmm_eval_potential_host", "fmm_eval_potential_static", "fmm_backward"]
 STAGES = ["sort", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p"]
 
 
@@ -74,6 +74,7 @@ def lib():
         L.fmm_eval_potential.argtypes = [vp, vp, vp, vp]
         L.fmm_eval_field.argtypes = [vp, vp, vp, vp, vp]
         L.fmm_eval_potential_host.argtypes = [vp, vp, vp, vp]
+        L.fmm_eval_potential_static.argtypes = [vp, vp, vp, vp]
         L.fmm_backward.argtypes = [vp, vp, vp, vp, vp, vp]
         for f in ENTRY_POINTS:
             if f not in ("fmm_last_error", "fmm_num_levels", "fmm_tree_free"):
@@ -214,6 +215,15 @@ def fmm_eval_potential_host(tree, q_host, u_host=None):
     _check(lib().fmm_eval_potential_host(tree.handle, C.c_void_p(q_host.data_ptr()),
                                          C.c_void_p(u_host.data_ptr()), _stream()))
     return u_host
+
+
+def fmm_eval_potential_static(tree, q, out=None):
+    """fmm_eval_potential without device allocation in the library: the
+    per-call scratch is the library's static device array (see fmm.h).
+    `out` lets the caller pass a preallocated output."""
+    u = out if out is not None else torch.empty(tree.n, dtype=torch.float64, device=q.device)
+    _check(lib().fmm_eval_potential_static(tree.handle, _dev(q), _dev(u), _stream()))
+    return u
 
 
 def fmm_backward(tree, q, grad_u, need_q=True, need_pos=True):
