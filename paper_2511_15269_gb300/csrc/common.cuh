@@ -145,9 +145,14 @@ struct fmm_tree {
   int* counters = nullptr;       // work counters, reset before each launch
   int* status = nullptr;         // latched kernel status bits
 
+  // far-field stages run on a second, higher-priority stream forked from
+  // and joined back into the caller's stream
+  cudaStream_t far_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
   // per-stage timing (fmm_tree_profile) and launch accounting
   static constexpr int kProfCalls = 512;
-  cudaEvent_t* prof_ev = nullptr;      // kProfCalls x (FMM_NUM_STAGES + 1)
+  cudaEvent_t* prof_ev = nullptr;      // kProfCalls x FMM_NUM_STAGES x {begin, end}
   mutable int prof_on = 0;
   mutable int prof_used = 0;
   mutable int prof_cur = -1;           // slot of the call being recorded
@@ -156,13 +161,14 @@ struct fmm_tree {
 
 namespace fmm {
 
-// Stage boundary i (0..FMM_NUM_STAGES) of the current evaluation call.
-inline void stage_mark(const fmm_tree* t, int i, cudaStream_t st) {
+// Begin (end = false) or end of stage s of the current evaluation call,
+// recorded on the stream the stage runs on.
+inline void stage_event(const fmm_tree* t, int s, bool end, cudaStream_t st) {
   if (!t->prof_on) return;
-  if (i == 0) {
+  if (s == FMM_STAGE_SORT && !end) {
     t->prof_cur = (t->prof_used < fmm_tree::kProfCalls) ? t->prof_used++ : -1;
   }
-  if (t->prof_cur >= 0) cudaEventRecord(t->prof_ev[t->prof_cur * (FMM_NUM_STAGES + 1) + i], st);
+  if (t->prof_cur >= 0) cudaEventRecord(t->prof_ev[(t->prof_cur * FMM_NUM_STAGES + s) * 2 + (end ? 1 : 0)], st);
 }
 
 // tree_build.cu

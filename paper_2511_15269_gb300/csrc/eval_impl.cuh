@@ -44,10 +44,29 @@ __device__ __forceinline__ void load_trig(const real* geo, int64_t stride, int64
   }
 }
 
+// One expansion row (16-byte aligned, padded to ncoef_pad) in vector loads.
 template <int P>
 __device__ __forceinline__ void load_coef(const real* src, real (&v)[ncoef(P)]) {
+  constexpr int NC = ncoef(P);
+  if constexpr (kF32) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
-  for (int c = 0; c < ncoef(P); c++) v[c] = src[c];
+    for (int c = 0; c < (NC + 3) / 4; c++) {
+      const float4 x = __ldg(s4 + c);
+      v[4 * c] = x.x;
+      if (4 * c + 1 < NC) v[4 * c + 1] = x.y;
+      if (4 * c + 2 < NC) v[4 * c + 2] = x.z;
+      if (4 * c + 3 < NC) v[4 * c + 3] = x.w;
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int c = 0; c < (NC + 1) / 2; c++) {
+      const double2 x = __ldg(s2 + c);
+      v[2 * c] = x.x;
+      if (2 * c + 1 < NC) v[2 * c + 1] = x.y;
+    }
+  }
 }
 
 // ---- E0: sort charges into tree order ----------------------------------------
@@ -135,9 +154,7 @@ __global__ void __launch_bounds__(128) m2m_kernel(int64_t n_child, int64_t child
     const real a = edge[0 * edge_stride + g], b = edge[1 * edge_stride + g];
     real cp[P], sp[P], ct[P], st[P];
     load_trig<P>(edge, edge_stride, g, 2, cp, sp, ct, st);
-    rotate_to_z<P>(v, cp, sp, ct, st);
-    axial_m2m<P>(v, a, b);
-    rotate_from_z<P>(v, cp, sp, ct, st);
+    translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_m2m<P>(w, a, b); });
   } else {
 #pragma unroll
     for (int c = 0; c < NC; c++) v[c] = real(0);
@@ -188,9 +205,7 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
       const real rinv = geo[i], uS = geo[n_m2l + i], uT = geo[2 * n_m2l + i];
       real cp[P], sp[P], ct[P], st[P];
       load_trig<P>(geo, n_m2l, i, 3, cp, sp, ct, st);
-      rotate_to_z<P>(v, cp, sp, ct, st);
-      axial_m2l<P>(v, uS, uT, rinv);
-      rotate_from_z<P>(v, cp, sp, ct, st);
+      translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_m2l<P>(w, uS, uT, rinv); });
 #pragma unroll
       for (int c = 0; c < NC; c++) acc[c * 32 + lane] += v[c];
     }
@@ -228,9 +243,7 @@ __global__ void __launch_bounds__(128) l2l_kernel(int64_t n_box, int64_t off, in
   const real a = edge[0 * edge_stride + g], b = edge[1 * edge_stride + g];
   real cp[P], sp[P], ct[P], st[P];
   load_trig<P>(edge, edge_stride, g, 2, cp, sp, ct, st);
-  rotate_to_z<P>(v, cp, sp, ct, st);
-  axial_l2l<P>(v, a, b);
-  rotate_from_z<P>(v, cp, sp, ct, st);
+  translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_l2l<P>(w, a, b); });
   real* out = Lam + g * NCP;
 #pragma unroll
   for (int c = 0; c < NC; c++) out[c] = out[c] + v[c];
@@ -364,6 +377,41 @@ __device__ __forceinline__ void p2p_tile_f32(const DupRec* sb, int scount, const
     const ulonglong2 b = s2[2 * j + 1];
 #pragma unroll
     for (int k = 0; k < NP; k++) {
+      const f2 dx = f2sub(tx[k], a.x), dy = f2sub(ty[k], a.y), dz = f2sub(tz[k], b.x);
+      const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+      float r0, r1;
+      f2unpack(r2, r0, r1);
+      float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
+      if (MASK) {
+        i0 = (r0 > 0.f) ? i0 : 0.f;
+        i1 = (r1 > 0.f) ? i1 : 0.f;
+      }
+      const f2 ri = f2pack(i0, i1);
+      pu[k] = f2fma(b.y, ri, pu[k]);
+      if (FIELD) {
+        const f2 w = f2mul(f2mul(f2mul(ri, ri), ri), b.y);
+        fx[k] = f2fma(w, dx, fx[k]);
+        fy[k] = f2fma(w, dy, fy[k]);
+        fz[k] = f2fma(w, dz, fz[k]);
+      }
+    }
+  }
+}
+
+// FP32 near-field tile, half-warp split: lanes 0-15 take the even and lanes
+// 16-31 the odd sources of the staged tile, each lane updating NPH packed
+// target pairs (two independent accumulation chains per source for NPH = 2).
+template <bool MASK, bool FIELD, int NPH>
+__device__ __forceinline__ void p2p_tile_f32h(const DupRec* sb, int scount, int half, const f2 (&tx)[NPH],
+                                              const f2 (&ty)[NPH], const f2 (&tz)[NPH], f2 (&pu)[NPH],
+                                              f2 (&fx)[NPH], f2 (&fy)[NPH], f2 (&fz)[NPH]) {
+  const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
+#pragma unroll 2
+  for (int j = half; j < scount; j += 2) {
+    const ulonglong2 a = s2[2 * j];
+    const ulonglong2 b = s2[2 * j + 1];
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
       const f2 dx = f2sub(tx[k], a.x), dy = f2sub(ty[k], a.y), dz = f2sub(tz[k], b.x);
       const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
       float r0, r1;
@@ -547,6 +595,139 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
   }
 }
 
+
+// ---- E6 (FP32): near field, one warp per target leaf, one block of four
+// leaves; each lane holds 2*TPL targets i = (lane & 15) + 16 k as TPL packed
+// pairs and sums over half of every source tile; the halves are combined by
+// a two-sum at the end.  Source leaves arrive by double-buffered 1D TMA bulk
+// copies completing on per-warp mbarriers.
+template <int TPL, bool FIELD>
+__global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_f32h(P2PArgs a) {
+  constexpr int CAP = TPL * 32;
+  constexpr int WARPS = 4;
+  constexpr int NT = 2 * TPL;
+  constexpr int NPH = TPL;
+  extern __shared__ __align__(128) unsigned char p2p_smem[];
+  DupRec (*sbuf)[2][CAP] = reinterpret_cast<DupRec (*)[2][CAP]>(p2p_smem);
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const DupRec* tile = reinterpret_cast<const DupRec*>(a.tile);
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int half = lane >> 4, l16 = lane & 15;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+  if (t >= a.n_leaves) return;
+  const int64_t leaf = a.order[t];
+  const int64_t g = a.leaf_off + leaf;
+  const int64_t tstart = a.box_start[g];
+  const int tcnt = a.box_count[g];
+  float tx0[NT], ty0[NT], tz0[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const int i = l16 + 16 * k;
+    if (i < tcnt) {
+      const float4 p = reinterpret_cast<const float4*>(a.src)[tstart + i];
+      tx0[k] = p.x;
+      ty0[k] = p.y;
+      tz0[k] = p.z;
+    } else {
+      tx0[k] = ty0[k] = tz0[k] = 0.f;
+    }
+  }
+  float hi[NT], lo[NT], fx[NT], fy[NT], fz[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) hi[k] = lo[k] = fx[k] = fy[k] = fz[k] = 0.f;
+  const int64_t eb = a.off[leaf], ee = a.off[leaf + 1];
+  auto issue = [&](int64_t e, int buf) {
+    const int64_t gs = a.leaf_off + (a.ent32[e].src & 0x7fffffff);
+    if (lane == 0) {
+      fence_proxy_async();
+      tma_load_1d(sbuf[warp][buf], tile + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(DupRec)), &bar[buf]);
+    }
+  };
+  uint32_t phase = 0;
+  if (eb < ee) issue(eb, 0);
+  for (int64_t e = eb; e < ee; e++) {
+    const int buf = (int)((e - eb) & 1);
+    if (e + 1 < ee) issue(e + 1, buf ^ 1);
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      // copies still in flight into this warp's buffers must land first
+      mbar_wait(&bar[buf], (phase >> buf) & 1u);
+      if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      return;
+    }
+    phase ^= 1u << buf;
+    const P2PEntry en = a.ent32[e];
+    const int ls = en.src & 0x7fffffff;
+    const int scount = a.box_count[a.leaf_off + ls];
+    const bool mask = (en.src < 0) || (ls == (int)leaf);
+    const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
+    f2 tx[NPH], ty[NPH], tz[NPH], pu[NPH], px[NPH], py[NPH], pz[NPH];
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      tx[k] = f2add(f2pack(tx0[2 * k], tx0[2 * k + 1]), ddx);
+      ty[k] = f2add(f2pack(ty0[2 * k], ty0[2 * k + 1]), ddy);
+      tz[k] = f2add(f2pack(tz0[2 * k], tz0[2 * k + 1]), ddz);
+      pu[k] = px[k] = py[k] = pz[k] = 0ull;
+    }
+    if (mask) p2p_tile_f32h<true, FIELD, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz);
+    else p2p_tile_f32h<false, FIELD, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz);
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      float u0, u1, x0, x1, y0, y1, z0, z1;
+      f2unpack(pu[k], u0, u1);
+      f2unpack(px[k], x0, x1);
+      f2unpack(py[k], y0, y1);
+      f2unpack(pz[k], z0, z1);
+      two_sum(hi[2 * k], lo[2 * k], u0);
+      two_sum(hi[2 * k + 1], lo[2 * k + 1], u1);
+      fx[2 * k] += x0;
+      fx[2 * k + 1] += x1;
+      fy[2 * k] += y0;
+      fy[2 * k + 1] += y1;
+      fz[2 * k] += z0;
+      fz[2 * k + 1] += z1;
+    }
+    __syncwarp();
+  }
+  // combine the two halves
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi[k], 16);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo[k], 16);
+    two_sum(hi[k], lo[k], oh);
+    lo[k] += ol;
+    if (FIELD) {
+      fx[k] += __shfl_xor_sync(0xffffffffu, fx[k], 16);
+      fy[k] += __shfl_xor_sync(0xffffffffu, fy[k], 16);
+      fz[k] += __shfl_xor_sync(0xffffffffu, fz[k], 16);
+    }
+  }
+  if (half == 0) {
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+      const int i = l16 + 16 * k;
+      if (i < tcnt) {
+        const int64_t pidx = tstart + i;
+        a.near_u[2 * pidx] = hi[k];
+        a.near_u[2 * pidx + 1] = lo[k];
+        if (FIELD) {
+          a.near_f[3 * pidx] = fx[k];
+          a.near_f[3 * pidx + 1] = fy[k];
+          a.near_f[3 * pidx + 2] = fz[k];
+        }
+      }
+    }
+  }
+}
+
 // ---- E5 + E7: L2P, near + far combination and inverse sort --------------------
 // u = -1/(4 pi) (far + near);  E = -grad u = 1/(4 pi) (grad far - sum q d / r^3).
 template <int P, bool FIELD>
@@ -663,8 +844,9 @@ struct Ptrs {
 
 Ptrs ptrs(const fmm_tree* t);
 
+// Upward pass: P2M on the leaves, then M2M level by level.
 template <int P>
-void run_far(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   const int s = t->s, L = t->L;
   const int nch = 1 << s;
   auto loff = [&](int l) {
@@ -673,43 +855,65 @@ void run_far(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
     return o;
   };
   const int64_t leaf_off = loff(L);
+  stage_event(t, FMM_STAGE_P2M, false, st);
   p2m_kernel<P><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
       t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, pp.src, pp.inv_rho, pp.M);
   FMM_LAUNCH_CHECK();
-  t->launches += 1 + 2 * L + 1;
-  stage_mark(t, FMM_STAGE_M2M, st);
+  t->launches += 1 + L;
+  stage_event(t, FMM_STAGE_P2M, true, st);
+  stage_event(t, FMM_STAGE_M2M, false, st);
   for (int l = L - 1; l >= 0; l--) {
     const int64_t nchild = (int64_t)1 << (s * (l + 1));
     m2m_kernel<P><<<grid_for(nchild, 128, 1 << 30), 128, 0, st>>>(nchild, loff(l + 1), loff(l), nch,
                                                                  pp.m2m, t->n_boxes, pp.M);
     FMM_LAUNCH_CHECK();
   }
+  stage_event(t, FMM_STAGE_M2M, true, st);
+}
+
+// M2L blocks per SM while the near field runs beside it: one M2L block
+// (4 warps, ~30K registers) leaves room for four near-field blocks.
+constexpr int kM2LBlocksPerSM = 1;
+
+// Downward pass: M2L over the whole list, then L2L level by level.
+template <int P>
+void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+  const int s = t->s, L = t->L;
+  auto loff = [&](int l) {
+    int64_t o = 0;
+    for (int i = 0; i < l; i++) o += (int64_t)1 << (s * i);
+    return o;
+  };
   const size_t smem = (size_t)4 * ncoef(P) * 32 * sizeof(real);
   static bool attr_set = false;
   if (!attr_set) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set = true;
   }
-  stage_mark(t, FMM_STAGE_M2L, st);
+  stage_event(t, FMM_STAGE_M2L, false, st);
   FMM_CUDA_TRY(cudaMemsetAsync(t->counters, 0, sizeof(int), st));
   int dev = 0, nsm = 0, occ = 0;
   FMM_CUDA_TRY(cudaGetDevice(&dev));
   FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, m2l_kernel<P>, 128, smem));
   if (occ < 1) occ = 1;
+  if (occ > kM2LBlocksPerSM) occ = kM2LBlocksPerSM;
   int64_t blocks = (int64_t)nsm * occ;
   const int64_t need = (t->n_boxes + 3) / 4;
   if (blocks > need) blocks = need;
   m2l_kernel<P><<<(int)blocks, 128, smem, st>>>(t->n_boxes, t->m2l_order, t->m2l_off, t->m2l_src,
                                                 pp.geo, t->n_m2l, pp.M, pp.Lam, t->counters);
   FMM_LAUNCH_CHECK();
-  stage_mark(t, FMM_STAGE_L2L, st);
+  t->launches += 1 + L;
+  stage_event(t, FMM_STAGE_M2L, true, st);
+  stage_event(t, FMM_STAGE_L2L, false, st);
   for (int l = 1; l <= L; l++) {
     const int64_t nb = (int64_t)1 << (s * l);
     l2l_kernel<P><<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(nb, loff(l), loff(l - 1), s, pp.l2l,
                                                              t->n_boxes, pp.Lam);
     FMM_LAUNCH_CHECK();
   }
+  stage_event(t, FMM_STAGE_L2L, true, st);
 }
 
 template <int P>
@@ -748,8 +952,26 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
   a.near_f = near_f;
   a.counter = t->counters + 1;
   a.status = t->status;
-  FMM_CUDA_TRY(cudaMemsetAsync(t->counters + 1, 0, sizeof(int), st));
   const size_t smem = (size_t)4 * 2 * TPL * 32 * 32;  // 32-byte records
+  t->launches += 1;
+  if constexpr (kF32) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32h<TPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32h<TPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32h<TPL, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+      FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32h<TPL, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared));
+      attr_set = true;
+    }
+    const int64_t blocks = (t->n_leaves + 3) / 4;
+    if (field) p2p_kernel_f32h<TPL, true><<<(unsigned)blocks, 128, smem, st>>>(a);
+    else p2p_kernel_f32h<TPL, false><<<(unsigned)blocks, 128, smem, st>>>(a);
+    FMM_LAUNCH_CHECK();
+    return;
+  }
+  FMM_CUDA_TRY(cudaMemsetAsync(t->counters + 1, 0, sizeof(int), st));
   static bool attr_set = false;
   if (!attr_set) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -765,7 +987,6 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
   int64_t blocks = (int64_t)nsm * occ;
   const int64_t need = (t->n_leaves + 3) / 4;
   if (blocks > need) blocks = need;
-  t->launches += 1;
   if (field) p2p_kernel<TPL, true><<<(int)blocks, 128, smem, st>>>(a);
   else p2p_kernel<TPL, false><<<(int)blocks, 128, smem, st>>>(a);
   FMM_LAUNCH_CHECK();
@@ -797,24 +1018,38 @@ void dispatch_p(int p, F&& f) {
 
 void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
   Ptrs pp = ptrs(t);
-  stage_mark(t, FMM_STAGE_SORT, st);
+  stage_event(t, FMM_STAGE_SORT, false, st);
   gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->perm, q, pp.pos, pp.src,
                                                      kF32 ? t->src_dup : nullptr);
   FMM_LAUNCH_CHECK();
   t->launches += 1;
-  // near field first (largest kernel), then the far-field chain
+  stage_event(t, FMM_STAGE_SORT, true, st);
   real* near_u = reinterpret_cast<real*>(t->near_u);
   real* near_f = reinterpret_cast<real*>(t->near_f);
-  stage_mark(t, FMM_STAGE_P2P, st);
-  run_p2p(t, pp, near_u, near_f, field != nullptr, st);
-  stage_mark(t, FMM_STAGE_P2M, st);
+  // upward pass on the caller's stream, then fork: M2L and L2L on the
+  // tree's higher-priority stream beside the near field on the caller's
+  // stream; join before the local evaluation
   dispatch_p(t->prm.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
-    run_far<P>(t, pp, st);
-    stage_mark(t, FMM_STAGE_L2P, st);
+    run_upward<P>(t, pp, st);
+  });
+  FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+  FMM_CUDA_TRY(cudaStreamWaitEvent(t->far_stream, t->ev_fork, 0));
+  dispatch_p(t->prm.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    run_downward<P>(t, pp, t->far_stream);
+  });
+  FMM_CUDA_TRY(cudaEventRecord(t->ev_join, t->far_stream));
+  stage_event(t, FMM_STAGE_P2P, false, st);
+  run_p2p(t, pp, near_u, near_f, field != nullptr, st);
+  stage_event(t, FMM_STAGE_P2P, true, st);
+  FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+  stage_event(t, FMM_STAGE_L2P, false, st);
+  dispatch_p(t->prm.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
     run_l2p<P>(t, pp, near_u, near_f, u, field, st);
   });
-  stage_mark(t, FMM_NUM_STAGES, st);
+  stage_event(t, FMM_STAGE_L2P, true, st);
 }
 
 }  // namespace

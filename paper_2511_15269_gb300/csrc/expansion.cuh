@@ -134,26 +134,26 @@ __device__ __forceinline__ void apply_b(real (&v)[ncoef(P)]) {
   });
 }
 
-// Polar rotation by the angle whose multiples' cosines/sines are (ct, st):
-// Y = B^-1 Z B.
-template <int P, bool INV>
-__device__ __forceinline__ void rot_y(real (&v)[ncoef(P)], const real (&ct)[P], const real (&st)[P]) {
-  apply_b<P, false>(v);
-  rot_z<P, INV>(v, ct, st);
-  apply_b<P, true>(v);
-}
-
-// Rotation bringing the translation vector onto +z (forward) and back.
-template <int P>
-__device__ __forceinline__ void rotate_to_z(real (&v)[ncoef(P)], const real (&cp)[P], const real (&sp)[P],
-                                            const real (&ct)[P], const real (&st)[P]) {
+// Rotate so that the translation vector lies on +z, apply the axial
+// transform `axial`, rotate back.  Both polar rotations run through one copy
+// of the quarter-turn products (a two-pass loop, the second pass with the
+// opposite angle), which halves the instruction footprint of the kernels.
+template <int P, class Axial>
+__device__ __forceinline__ void translate_rotated(real (&v)[ncoef(P)], const real (&cp)[P], const real (&sp)[P],
+                                                  const real (&ct)[P], const real (&st)[P], Axial&& axial) {
+  real s[P];
+#pragma unroll
+  for (int m = 0; m < P; m++) s[m] = st[m];
   rot_z<P, false>(v, cp, sp);
-  rot_y<P, false>(v, ct, st);
-}
-template <int P>
-__device__ __forceinline__ void rotate_from_z(real (&v)[ncoef(P)], const real (&cp)[P], const real (&sp)[P],
-                                              const real (&ct)[P], const real (&st)[P]) {
-  rot_y<P, true>(v, ct, st);
+#pragma unroll 1
+  for (int pass = 0; pass < 2; pass++) {
+    if (pass == 1) axial(v);
+    apply_b<P, false>(v);
+    rot_z<P, false>(v, ct, s);
+    apply_b<P, true>(v);
+#pragma unroll
+    for (int m = 0; m < P; m++) s[m] = -s[m];
+  }
   rot_z<P, true>(v, cp, sp);
 }
 

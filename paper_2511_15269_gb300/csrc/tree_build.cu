@@ -1199,6 +1199,13 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   t->u_stage = dev_alloc<double>(t, n);
   t->f_stage = dev_alloc<double>(t, 3 * (size_t)n);
   t->g_stage = dev_alloc<double>(t, 3 * (size_t)n);
+  {
+    int lo_prio = 0, hi_prio = 0;
+    FMM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    FMM_CUDA_TRY(cudaStreamCreateWithPriority(&t->far_stream, cudaStreamNonBlocking, hi_prio));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming));
+    FMM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming));
+  }
   t->counters = dev_alloc<int>(t, 8);
   t->status = dev_alloc<int>(t, 1);
   FMM_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), st));
