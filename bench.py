@@ -154,6 +154,108 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+def event_ms(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def bench_plummer(fmm, workloads, oracle, dev):
+    """Highly non-uniform workload: 70% Plummer sphere + 30% unit-sphere
+    surface, N = 2^22, p = 10, leaf 64; tree build and evaluation timed
+    separately, FP32C and FP64 against the direct sum on 4096 targets."""
+    import torch
+    c = workloads.CONFIGS["plummer4m_p10"]
+    pos, q = workloads.plummer_sphere(c["n"], seed=0)
+    pos_d, q_d = torch.from_numpy(pos).to(dev), torch.from_numpy(q).to(dev)
+    builds = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T = fmm.fmm_build_tree(pos_d, c["p"], c["leaf_size"], c["s"], c["theta"], fmm.FMM_FP32C)
+        torch.cuda.synchronize()
+        builds.append(1e3 * (time.perf_counter() - t0))
+        if len(builds) < 3:
+            T.free()
+    u = torch.empty_like(q_d)
+    ms32 = event_ms(lambda: fmm.fmm_eval_potential(T, q_d, u), 5)
+    u32 = u.cpu().numpy()
+    fmm.fmm_tree_set_precision(T, fmm.FMM_FP64)
+    ms64 = event_ms(lambda: fmm.fmm_eval_potential(T, q_d, u), 1)
+    u64 = u.cpu().numpy()
+    st = fmm.fmm_tree_stats(T)
+    T.free()
+    tg = workloads.sample_targets(c["n"], 4096, seed=1)
+    ud = oracle.direct(pos, q, targets=tg)
+    return {"workload": "70%% Plummer (a=0.05) + 30%% unit-sphere surface, N=%d, q=+-1, p=%d, leaf %d, theta %g"
+                        % (c["n"], c["p"], c["leaf_size"], c["theta"]),
+            "tree_build_ms": min(builds), "levels": st["levels"], "n_m2l": st["n_m2l"],
+            "n_p2p_pairs": st["n_p2p_pairs"],
+            "fp32c": {"ms": ms32, "Mpoints/s": c["n"] / ms32 / 1e3, "rel_l2": rel_l2(u32[tg], ud),
+                      "rel_linf": rel_linf(u32[tg], ud)},
+            "fp64": {"ms": ms64, "Mpoints/s": c["n"] / ms64 / 1e3, "rel_l2": rel_l2(u64[tg], ud),
+                     "rel_linf": rel_linf(u64[tg], ud)}}
+
+
+def bench_batched(fmm, workloads, oracle, dev):
+    """64 independent charge sets of log-uniform size in [1e4, 5e5], uniform
+    cube or Gaussian clusters, p = 6, FP32C: leaf size autotuned, the sets
+    merged into one batch, one evaluation captured as a CUDA graph and
+    replayed."""
+    import torch
+    from paper_2511_15269_gb300 import autotune
+    c = workloads.CONFIGS["batched64_p6"]
+    sets = workloads.batched_sets(64, seed=0)
+    pos_list = [pos for pos, q in sets]
+    q_all = np.concatenate([q for pos, q in sets])
+    best, tried = autotune.tune_leaf_size(pos_list, q_all, c["p"], c["s"], c["theta"], fmm.FMM_FP32C)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = autotune.build_batch(pos_list, c["p"], best, c["s"], c["theta"], fmm.FMM_FP32C)
+    torch.cuda.synchronize()
+    build_ms = 1e3 * (time.perf_counter() - t0)
+    q_d = torch.from_numpy(q_all).to(dev)
+    u = torch.empty_like(q_d)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            fmm.fmm_eval_potential(B, q_d, u)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        fmm.fmm_eval_potential(B, q_d, u)
+    ms = event_ms(graph.replay, 10)
+    ms_eager = event_ms(lambda: fmm.fmm_eval_potential(B, q_d, u), 5)
+    graph.replay()
+    torch.cuda.synchronize()
+    uu = u.cpu().numpy()
+    off = fmm.fmm_tree_point_offsets(B)
+    st = fmm.fmm_tree_stats(B)
+    B.free()
+    errs_num, errs_den = 0.0, 0.0
+    rng = np.random.default_rng(3)
+    for k, (pos, q) in enumerate(sets):
+        tg = np.sort(rng.choice(len(q), 64, replace=False)).astype(np.int64)
+        ud = oracle.direct(pos, q, targets=tg)
+        errs_num += float(np.sum((uu[off[k] + tg] - ud) ** 2))
+        errs_den += float(np.sum(ud ** 2))
+    n = int(off[-1])
+    return {"workload": "64 sets, N log-uniform in [1e4, 5e5] (total %d), cube / 8 Gaussian clusters sigma 0.02, "
+                        "p=%d, theta %g, FP32C" % (n, c["p"], c["theta"]),
+            "leaf_size": best, "autotune_ms": tried, "batch_build_ms": build_ms,
+            "graph_ms": ms, "eager_ms": ms_eager, "Mpoints/s": n / ms / 1e3,
+            "kernel_launches_per_eval": None, "trees": st["n_trees"],
+            "rel_l2_vs_direct_64_targets_per_set": float(np.sqrt(errs_num / errs_den))}
+
+
 def config_dict(cfg, path):
     return {"workload": "uniform cube N=%d (U[0,1)^3, q U[-1,1], seed 0), p=%d, leaf %d, s=%d, theta=%g, %s"
             % (cfg["n"], cfg["p"], cfg["leaf_size"], cfg["s"], cfg["theta"], path),
@@ -336,6 +438,8 @@ def main():
             m, dt = oracle_sample_eval(O, q, cfg["p"], rng.choice(O.n_leaves, 32, replace=False), O.n_leaves)
             pts += m
             secs += dt
+        line["plummer4m_p10"] = bench_plummer(fmm, workloads, oracle, dev)
+        line["batched64_p6"] = bench_batched(fmm, workloads, oracle, dev)
         line["cpu_baseline"] = {
             "value": pts / secs / 1e6, "unit": "Mpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "oracle FP64 FMM at every point of 3 x 32 random target leaves (%d points), "

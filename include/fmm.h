@@ -97,6 +97,7 @@ typedef struct {
   double build_ms;       /* wall time of fmm_build_tree                         */
   int64_t kernel_launches; /* kernels this library launched for evaluations of
                               this tree so far                                  */
+  int n_trees;           /* 1, or the number of trees of a merged batch          */
 } fmm_stats;
 
 /* Evaluation stages in launch order, named after the stages of Sec. III.A:
@@ -140,6 +141,22 @@ int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void*
 /* Releases a tree and its device memory (synchronises the device first).
  * NULL is accepted. */
 void fmm_tree_free(fmm_tree* tree);
+
+/* Batch of independent charge sets (many trees, uneven sizes) evaluated
+ * together: builds one tree-shaped object holding copies of n_trees trees
+ * (same p and splits; leaf sizes may differ), whose points are the
+ * concatenation of the trees' points in the given order.  Every evaluation
+ * entry point accepts it, with q, u, field, gradients of the concatenated
+ * length; each stage then runs as one launch over the whole batch (a whole
+ * evaluation can be captured as one CUDA graph).  The input trees stay valid
+ * and independent; free the batch with fmm_tree_free.  Synchronous.
+ * Errors: FMM_ERR_INVALID_ARG (mismatched trees, nested batches), FMM_ERR_OOM,
+ * FMM_ERR_CUDA. */
+int fmm_tree_merge(fmm_tree* const* trees, int n_trees, void* stream, fmm_tree** out);
+
+/* Point offsets of the trees of a batch: n_trees + 1 int64 (host); a plain
+ * tree gives {0, n}. */
+int fmm_tree_point_offsets(const fmm_tree* tree, int64_t* offsets);
 
 /* Selects the precision of later evaluation calls (FMM_FP64 or FMM_FP32C). */
 int fmm_tree_set_precision(fmm_tree* tree, int precision);

@@ -40,7 +40,7 @@ void free_tree(fmm_tree* t) {
                   t->pos64,    t->inv_rho32, t->inv_rho64, t->geo32,    t->geo64,    t->m2m32,    t->m2m64,
                   t->l2l32,    t->l2l64,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
                   t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
-                  t->counters, t->status};
+                  t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->down_ids};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->prof_ev) {
@@ -51,6 +51,9 @@ void free_tree(fmm_tree* t) {
   if (t->ev_join) cudaEventDestroy(t->ev_join);
   if (t->far_stream) cudaStreamDestroy(t->far_stream);
   delete[] t->level_avg_host;
+  delete[] t->up_off_h;
+  delete[] t->down_off_h;
+  delete[] t->tree_point_off_h;
   delete t;
 }
 
@@ -134,6 +137,37 @@ int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void*
 
 void fmm_tree_free(fmm_tree* tree) { free_tree(tree); }
 
+int fmm_tree_merge(fmm_tree* const* trees, int n_trees, void* stream, fmm_tree** out) {
+  if (out) *out = nullptr;
+  fmm_tree* m = nullptr;
+  int rc = guarded([&] {
+    require(out != nullptr && trees != nullptr, "NULL argument");
+    require(n_trees >= 1, "n_trees must be >= 1");
+    auto t0 = std::chrono::steady_clock::now();
+    m = new fmm_tree();
+    merge_trees(trees, n_trees, (cudaStream_t)stream, m);
+    m->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  });
+  if (rc != FMM_OK) {
+    free_tree(m);
+    return rc;
+  }
+  *out = m;
+  return FMM_OK;
+}
+
+int fmm_tree_point_offsets(const fmm_tree* t, int64_t* offsets) {
+  return guarded([&] {
+    require(t != nullptr && offsets != nullptr, "NULL argument");
+    if (t->tree_point_off_h) {
+      for (int k = 0; k <= t->n_trees; k++) offsets[k] = t->tree_point_off_h[k];
+    } else {
+      offsets[0] = 0;
+      offsets[1] = t->n;
+    }
+  });
+}
+
 int fmm_tree_set_precision(fmm_tree* tree, int precision) {
   return guarded([&] {
     require(tree != nullptr, "tree is NULL");
@@ -161,6 +195,7 @@ int fmm_tree_stats(const fmm_tree* t, fmm_stats* s) {
     s->device_bytes = t->device_bytes;
     s->build_ms = t->build_ms;
     s->kernel_launches = t->launches;
+    s->n_trees = t->n_trees;
   });
 }
 

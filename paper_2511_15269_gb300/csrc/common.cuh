@@ -113,6 +113,17 @@ struct fmm_tree {
   int32_t* p2p_src = nullptr;    // n_p2p
   fmm::P2PEntry* p2p32 = nullptr;  // n_p2p
   int32_t* leaf_order = nullptr;   // n_leaves: target leaves, most work first
+  int32_t* leaf_box = nullptr;     // n_leaves: global box id of each leaf
+  int32_t* box_parent = nullptr;   // n_boxes: parent box id (-1 for a root)
+  // M2M rounds (bottom-up) and L2L rounds (top-down): device lists of box
+  // ids with host offsets; the children of a parent are consecutive
+  int n_up = 0, n_down = 0;
+  int64_t* up_off_h = nullptr;     // n_up + 1
+  int64_t* down_off_h = nullptr;   // n_down + 1
+  int32_t* up_ids = nullptr;
+  int32_t* down_ids = nullptr;
+  int n_trees = 1;                 // > 1 for a merged batch of trees
+  int64_t* tree_point_off_h = nullptr;  // n_trees + 1 (merged batches)
 
   // per-point and per-box constants
   float4* pos_local = nullptr;   // n: tree order, x - c_leaf (FP32), w = 0
@@ -173,6 +184,8 @@ inline void stage_event(const fmm_tree* t, int s, bool end, cudaStream_t st) {
 
 // tree_build.cu
 void build_tree(fmm_tree* t, const double* pos, cudaStream_t st);
+// merge.cu: a batch of trees as one tree-shaped object
+void merge_trees(fmm_tree* const* in, int n, cudaStream_t st, fmm_tree* out);
 
 // eval_f32.cu / eval_f64.cu: the evaluation pipelines.
 //   q: device, original order; u / field: device outputs (nullable)

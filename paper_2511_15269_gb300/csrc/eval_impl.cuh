@@ -88,7 +88,7 @@ __global__ void gather_kernel(int64_t n, const int32_t* __restrict__ perm,
 // ---- E1: P2M, one warp per leaf ----------------------------------------------
 // M^m_n = sum_i q_i Rt^m_n((x_i - c) / rho)   (Sec. II.C in the scaled basis)
 template <int P>
-__global__ void __launch_bounds__(128) p2m_kernel(int64_t n_leaves, int64_t leaf_off,
+__global__ void __launch_bounds__(128) p2m_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
                                                   const int64_t* __restrict__ box_start,
                                                   const int32_t* __restrict__ box_count,
                                                   const double* __restrict__ center,
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(128) p2m_kernel(int64_t n_leaves, int64_t leaf
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves;
        leaf += warps) {
-    const int64_t g = leaf_off + leaf;
+    const int64_t g = leaf_box[leaf];
     const int64_t start = box_start[g];
     const int cnt = box_count[g];
     const real ir = inv_rho[g];
@@ -140,16 +140,17 @@ __global__ void __launch_bounds__(128) p2m_kernel(int64_t n_leaves, int64_t leaf
 
 // ---- E2: M2M, one thread per child box of level l+1 -------------------------
 template <int P>
-__global__ void __launch_bounds__(128) m2m_kernel(int64_t n_child, int64_t child_off,
-                                                  int64_t par_off, int nch,
+__global__ void __launch_bounds__(128) m2m_kernel(int64_t n_child, const int32_t* __restrict__ child,
+                                                  const int32_t* __restrict__ parent, int nch,
                                                   const real* __restrict__ edge,
                                                   int64_t edge_stride, real* __restrict__ M) {
   constexpr int NC = ncoef(P);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const bool active = t < n_child;
   real v[NC];
+  int64_t g = 0;
   if (active) {
-    const int64_t g = child_off + t;
+    g = child[t];
     load_coef<P>(M + g * ncoef_pad(P), v);
     const real a = edge[0 * edge_stride + g], b = edge[1 * edge_stride + g];
     real cp[P], sp[P], ct[P], st[P];
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(128) m2m_kernel(int64_t n_child, int64_t child
     v[c] = x;
   }
   if (active && (t % nch) == 0) {
-    real* out = M + (par_off + t / nch) * ncoef_pad(P);
+    real* out = M + (int64_t)parent[g] * ncoef_pad(P);
 #pragma unroll
     for (int c = 0; c < NC; c++) out[c] = v[c];
   }
@@ -229,15 +230,16 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
 
 // ---- E4: L2L, one thread per box of level l; adds into its own M2L local ----
 template <int P>
-__global__ void __launch_bounds__(128) l2l_kernel(int64_t n_box, int64_t off, int64_t par_off,
-                                                  int s, const real* __restrict__ edge,
+__global__ void __launch_bounds__(128) l2l_kernel(int64_t n_box, const int32_t* __restrict__ box,
+                                                  const int32_t* __restrict__ parent,
+                                                  const real* __restrict__ edge,
                                                   int64_t edge_stride, real* __restrict__ Lam) {
   constexpr int NC = ncoef(P);
   constexpr int NCP = ncoef_pad(P);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n_box) return;
-  const int64_t g = off + t;
-  const int64_t gp = par_off + (t >> s);
+  const int64_t g = box[t];
+  const int64_t gp = parent[g];
   real v[NC];
   load_coef<P>(Lam + gp * NCP, v);
   const real a = edge[0 * edge_stride + g], b = edge[1 * edge_stride + g];
@@ -434,7 +436,8 @@ __device__ __forceinline__ void p2p_tile_f32h(const DupRec* sb, int scount, int 
 }
 
 struct P2PArgs {
-  int64_t n_leaves, leaf_off;
+  int64_t n_leaves;
+  const int32_t* leaf_box;  // global box id of each leaf
   const int32_t* order;
   const int64_t* off;
   const P2PEntry* ent32;
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= a.n_leaves || !ok) break;
     const int64_t leaf = a.order[t];
-    const int64_t g = a.leaf_off + leaf;
+    const int64_t g = a.leaf_box[leaf];
     const int64_t tstart = a.box_start[g];
     const int tcnt = a.box_count[g];
     real tx0[TPL], ty0[TPL], tz0[TPL];
@@ -501,7 +504,7 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
       return kF32 ? (a.ent32[e].src & 0x7fffffff) : a.ent_src[e];
     };
     auto issue = [&](int64_t e, int buf) {
-      const int64_t gs = a.leaf_off + src_leaf(e);
+      const int64_t gs = a.leaf_box[src_leaf(e)];
       if (lane == 0) {
         fence_proxy_async();
         tma_load_1d(sbuf[warp][buf], tile + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(rec)),
@@ -523,7 +526,7 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
       }
       phase ^= 1u << buf;
       const int ls = src_leaf(e);
-      const int scount = a.box_count[a.leaf_off + ls];
+      const int scount = a.box_count[a.leaf_box[ls]];
       if constexpr (kF32) {
         const P2PEntry en = a.ent32[e];
         const bool mask = (en.src < 0) || (ls == (int)leaf);
@@ -624,7 +627,7 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_
   const int64_t t = (int64_t)blockIdx.x * WARPS + warp;
   if (t >= a.n_leaves) return;
   const int64_t leaf = a.order[t];
-  const int64_t g = a.leaf_off + leaf;
+  const int64_t g = a.leaf_box[leaf];
   const int64_t tstart = a.box_start[g];
   const int tcnt = a.box_count[g];
   float tx0[NT], ty0[NT], tz0[NT];
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_
   for (int k = 0; k < NT; k++) hi[k] = lo[k] = fx[k] = fy[k] = fz[k] = 0.f;
   const int64_t eb = a.off[leaf], ee = a.off[leaf + 1];
   auto issue = [&](int64_t e, int buf) {
-    const int64_t gs = a.leaf_off + (a.ent32[e].src & 0x7fffffff);
+    const int64_t gs = a.leaf_box[a.ent32[e].src & 0x7fffffff];
     if (lane == 0) {
       fence_proxy_async();
       tma_load_1d(sbuf[warp][buf], tile + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(DupRec)), &bar[buf]);
@@ -666,7 +669,7 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_
     phase ^= 1u << buf;
     const P2PEntry en = a.ent32[e];
     const int ls = en.src & 0x7fffffff;
-    const int scount = a.box_count[a.leaf_off + ls];
+    const int scount = a.box_count[a.leaf_box[ls]];
     const bool mask = (en.src < 0) || (ls == (int)leaf);
     const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
     f2 tx[NPH], ty[NPH], tz[NPH], pu[NPH], px[NPH], py[NPH], pz[NPH];
@@ -731,7 +734,7 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_
 // ---- E5 + E7: L2P, near + far combination and inverse sort --------------------
 // u = -1/(4 pi) (far + near);  E = -grad u = 1/(4 pi) (grad far - sum q d / r^3).
 template <int P, bool FIELD>
-__global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, int64_t leaf_off,
+__global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
                                                   const int64_t* __restrict__ box_start,
                                                   const int32_t* __restrict__ box_count,
                                                   const double* __restrict__ center,
@@ -752,7 +755,7 @@ __global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, int64_t leaf
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
   for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves;
        leaf += warps) {
-    const int64_t g = leaf_off + leaf;
+    const int64_t g = leaf_box[leaf];
     const real* L = Lam + g * ncoef_pad(P);
     for (int c = lane; c < NC; c += 32) sL[warp][c] = L[c];
     __syncwarp();
@@ -844,28 +847,22 @@ struct Ptrs {
 
 Ptrs ptrs(const fmm_tree* t);
 
-// Upward pass: P2M on the leaves, then M2M level by level.
+// Upward pass: P2M on the leaves, then M2M round by round (round r holds
+// the child boxes r levels above the leaves of every tree in the batch).
 template <int P>
 void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
-  const int s = t->s, L = t->L;
-  const int nch = 1 << s;
-  auto loff = [&](int l) {
-    int64_t o = 0;
-    for (int i = 0; i < l; i++) o += (int64_t)1 << (s * i);
-    return o;
-  };
-  const int64_t leaf_off = loff(L);
+  const int nch = 1 << t->s;
   stage_event(t, FMM_STAGE_P2M, false, st);
   p2m_kernel<P><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-      t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, pp.src, pp.inv_rho, pp.M);
+      t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->center, pp.src, pp.inv_rho, pp.M);
   FMM_LAUNCH_CHECK();
-  t->launches += 1 + L;
+  t->launches += 1 + t->n_up;
   stage_event(t, FMM_STAGE_P2M, true, st);
   stage_event(t, FMM_STAGE_M2M, false, st);
-  for (int l = L - 1; l >= 0; l--) {
-    const int64_t nchild = (int64_t)1 << (s * (l + 1));
-    m2m_kernel<P><<<grid_for(nchild, 128, 1 << 30), 128, 0, st>>>(nchild, loff(l + 1), loff(l), nch,
-                                                                 pp.m2m, t->n_boxes, pp.M);
+  for (int r = 0; r < t->n_up; r++) {
+    const int64_t nchild = t->up_off_h[r + 1] - t->up_off_h[r];
+    m2m_kernel<P><<<grid_for(nchild, 128, 1 << 30), 128, 0, st>>>(nchild, t->up_ids + t->up_off_h[r], t->box_parent,
+                                                                 nch, pp.m2m, t->n_boxes, pp.M);
     FMM_LAUNCH_CHECK();
   }
   stage_event(t, FMM_STAGE_M2M, true, st);
@@ -875,15 +872,10 @@ void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 // (4 warps, ~30K registers) leaves room for four near-field blocks.
 constexpr int kM2LBlocksPerSM = 1;
 
-// Downward pass: M2L over the whole list, then L2L level by level.
+// Downward pass: M2L over the whole list, then L2L round by round (round r
+// holds the boxes at depth r + 1 of every tree in the batch).
 template <int P>
 void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
-  const int s = t->s, L = t->L;
-  auto loff = [&](int l) {
-    int64_t o = 0;
-    for (int i = 0; i < l; i++) o += (int64_t)1 << (s * i);
-    return o;
-  };
   const size_t smem = (size_t)4 * ncoef(P) * 32 * sizeof(real);
   static bool attr_set = false;
   if (!attr_set) {
@@ -904,13 +896,13 @@ void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   m2l_kernel<P><<<(int)blocks, 128, smem, st>>>(t->n_boxes, t->m2l_order, t->m2l_off, t->m2l_src,
                                                 pp.geo, t->n_m2l, pp.M, pp.Lam, t->counters);
   FMM_LAUNCH_CHECK();
-  t->launches += 1 + L;
+  t->launches += 1 + t->n_down;
   stage_event(t, FMM_STAGE_M2L, true, st);
   stage_event(t, FMM_STAGE_L2L, false, st);
-  for (int l = 1; l <= L; l++) {
-    const int64_t nb = (int64_t)1 << (s * l);
-    l2l_kernel<P><<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(nb, loff(l), loff(l - 1), s, pp.l2l,
-                                                             t->n_boxes, pp.Lam);
+  for (int r = 0; r < t->n_down; r++) {
+    const int64_t nb = t->down_off_h[r + 1] - t->down_off_h[r];
+    l2l_kernel<P><<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(nb, t->down_ids + t->down_off_h[r], t->box_parent,
+                                                             pp.l2l, t->n_boxes, pp.Lam);
     FMM_LAUNCH_CHECK();
   }
   stage_event(t, FMM_STAGE_L2L, true, st);
@@ -919,16 +911,14 @@ void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 template <int P>
 void run_l2p(const fmm_tree* t, const Ptrs& pp, const real* near_u, const real* near_f, double* u,
              double* field, cudaStream_t st) {
-  int64_t leaf_off = 0;
-  for (int i = 0; i < t->L; i++) leaf_off += (int64_t)1 << (t->s * i);
   t->launches += 1;
   if (field)
     l2p_kernel<P, true><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-        t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
+        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
         pp.Lam, near_u, near_f, u, field);
   else
     l2p_kernel<P, false><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-        t->n_leaves, leaf_off, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
+        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
         pp.Lam, near_u, near_f, u, field);
   FMM_LAUNCH_CHECK();
 }
@@ -938,8 +928,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
                  cudaStream_t st) {
   P2PArgs a;
   a.n_leaves = t->n_leaves;
-  a.leaf_off = 0;
-  for (int i = 0; i < t->L; i++) a.leaf_off += (int64_t)1 << (t->s * i);
+  a.leaf_box = t->leaf_box;
   a.order = t->leaf_order;
   a.off = t->p2p_off;
   a.ent32 = t->p2p32;

@@ -560,6 +560,19 @@ __global__ void box_range_kernel(const int64_t* __restrict__ st, int64_t nb, int
   bc[off + b] = (int32_t)(st[b + 1] - st[b]);
 }
 
+// leaf box ids, parents and per-level box ids of one tree
+__global__ void index_lists_kernel(int64_t nbox, int s, int L, int32_t* __restrict__ leaf_box,
+                                   int32_t* __restrict__ parent, int32_t* __restrict__ ids) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= nbox) return;
+  int l = 0;
+  while (level_offset(l + 1, s) <= g) l++;
+  const int64_t b = g - level_offset(l, s);
+  parent[g] = (l == 0) ? -1 : (int32_t)(level_offset(l - 1, s) + (b >> s));
+  ids[g] = (int32_t)g;
+  if (l == L) leaf_box[b] = (int32_t)g;
+}
+
 // adjacent-pair sums, one stage
 __global__ void pair_sum_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t m) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -982,6 +995,31 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   centre_radius_kernel<<<grid_for(NB, 256, 1 << 30), 256, 0, st>>>(NB, blo, bhi, t->center, t->radius, t->inv_rho32,
                                                                    t->inv_rho64);
   FMM_LAUNCH_CHECK();
+  // index lists: a single tree's M2M round r holds level L - r, its L2L
+  // round r level r + 1 (children of a parent consecutive)
+  t->leaf_box = dev_alloc<int32_t>(t, NL);
+  t->box_parent = dev_alloc<int32_t>(t, NB);
+  t->down_ids = dev_alloc<int32_t>(t, NB);
+  t->up_ids = dev_alloc<int32_t>(t, NB);
+  index_lists_kernel<<<grid_for(NB, 256, 1 << 30), 256, 0, st>>>(NB, s, L, t->leaf_box, t->box_parent, t->down_ids);
+  FMM_LAUNCH_CHECK();
+  t->n_up = t->n_down = L;
+  t->up_off_h = new int64_t[L + 1];
+  t->down_off_h = new int64_t[L + 1];
+  {
+    std::vector<int32_t> up;
+    up.reserve((size_t)NB);
+    for (int r = 0; r < L; r++) {
+      t->up_off_h[r] = (int64_t)up.size();
+      for (int64_t g = level_offset(L - r, s); g < level_offset(L - r + 1, s); g++) up.push_back((int32_t)g);
+      t->down_off_h[r] = level_offset(r + 1, s);
+    }
+    t->up_off_h[L] = (int64_t)up.size();
+    t->down_off_h[L] = level_offset(L + 1, s);
+    if (!up.empty())
+      FMM_CUDA_TRY(cudaMemcpyAsync(t->up_ids, up.data(), sizeof(int32_t) * up.size(), cudaMemcpyHostToDevice, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
 
   // ---- average radius per level ----
   t->level_avg_host = new double[L + 1];

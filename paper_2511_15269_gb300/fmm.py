@@ -20,7 +20,8 @@ FMM_TIE_TARGET = 1
 FMM_MAX_P = 10
 
 # exported entry points, in include/fmm.h order
-ENTRY_POINTS = ["fmm_last_error", "fmm_num_levels", "fmm_build_tree", "fmm_tree_free",
+ENTRY_POINTS = ["fmm_last_error", "fmm_num_levels", "fmm_build_tree", "fmm_tree_free", "fmm_tree_merge",
+                "fmm_tree_point_offsets",
                 "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_export",
                 "fmm_tree_profile", "fmm_tree_stage_times", "fmm_eval_potential", "fmm_eval_field",
                 "fmm_eval_potential_host", "fmm_eval_potential_static", "fmm_backward"]
@@ -43,7 +44,7 @@ class fmm_stats(C.Structure):
                 ("leaf_size", C.c_int), ("precision", C.c_int), ("theta", C.c_double),
                 ("n_boxes", C.c_int64), ("n_leaves", C.c_int64), ("n_m2l", C.c_int64),
                 ("n_p2p", C.c_int64), ("n_p2p_pairs", C.c_int64), ("device_bytes", C.c_size_t),
-                ("build_ms", C.c_double), ("kernel_launches", C.c_int64)]
+                ("build_ms", C.c_double), ("kernel_launches", C.c_int64), ("n_trees", C.c_int)]
 
 
 def library_path():
@@ -64,6 +65,8 @@ def lib():
         L.fmm_num_levels.restype = i
         L.fmm_build_tree.argtypes = [vp, i64, C.POINTER(fmm_params), vp, C.POINTER(vp)]
         L.fmm_tree_free.argtypes = [vp]
+        L.fmm_tree_merge.argtypes = [vp, i, vp, C.POINTER(vp)]
+        L.fmm_tree_point_offsets.argtypes = [vp, vp]
         L.fmm_tree_free.restype = None
         L.fmm_tree_set_precision.argtypes = [vp, i]
         L.fmm_tree_stats.argtypes = [vp, C.POINTER(fmm_stats)]
@@ -148,6 +151,24 @@ def fmm_build_tree(pos, p, leaf_size, splits=2, theta=0.5, precision=FMM_FP32C, 
 
 def fmm_tree_free(tree):
     tree.free()
+
+
+def fmm_tree_merge(trees):
+    """Batch of independent trees evaluated together (points concatenated in
+    the given order); the inputs stay valid."""
+    arr = (C.c_void_p * len(trees))(*[t.handle for t in trees])
+    h = C.c_void_p()
+    _check(lib().fmm_tree_merge(arr, len(trees), _stream(), C.byref(h)))
+    n = sum(t.n for t in trees)
+    return Tree(h, n, trees[0].params)
+
+
+def fmm_tree_point_offsets(tree):
+    import numpy as np
+    st = fmm_tree_stats(tree)
+    out = np.zeros(st["n_trees"] + 1, dtype=np.int64)
+    _check(lib().fmm_tree_point_offsets(tree.handle, C.c_void_p(out.ctypes.data)))
+    return out
 
 
 def fmm_tree_set_precision(tree, precision):
