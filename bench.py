@@ -186,6 +186,11 @@ def bench_plummer(fmm, workloads, oracle, dev):
             T.free()
     u = torch.empty_like(q_d)
     ms32 = event_ms(lambda: fmm.fmm_eval_potential(T, q_d, u), 5)
+    fmm.fmm_tree_profile(T, True)
+    fmm.fmm_eval_potential(T, q_d, u)
+    torch.cuda.synchronize()
+    fmm.fmm_tree_profile(T, False)
+    stages, calls = fmm.fmm_tree_stage_times(T)
     u32 = u.cpu().numpy()
     fmm.fmm_tree_set_precision(T, fmm.FMM_FP64)
     ms64 = event_ms(lambda: fmm.fmm_eval_potential(T, q_d, u), 1)
@@ -199,7 +204,8 @@ def bench_plummer(fmm, workloads, oracle, dev):
             "tree_build_ms": min(builds), "levels": st["levels"], "n_m2l": st["n_m2l"],
             "n_p2p_pairs": st["n_p2p_pairs"],
             "fp32c": {"ms": ms32, "Mpoints/s": c["n"] / ms32 / 1e3, "rel_l2": rel_l2(u32[tg], ud),
-                      "rel_linf": rel_linf(u32[tg], ud)},
+                      "rel_linf": rel_linf(u32[tg], ud),
+                      "stage_ms": {k: v / max(calls, 1) for k, v in stages.items()}},
             "fp64": {"ms": ms64, "Mpoints/s": c["n"] / ms64 / 1e3, "rel_l2": rel_l2(u64[tg], ud),
                      "rel_linf": rel_linf(u64[tg], ud)}}
 

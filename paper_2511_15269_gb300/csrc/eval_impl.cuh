@@ -404,33 +404,66 @@ __device__ __forceinline__ void p2p_tile_f32(const DupRec* sb, int scount, const
 // 16-31 the odd sources of the staged tile, each lane updating NPH packed
 // target pairs (two independent accumulation chains per source for NPH = 2).
 template <bool MASK, bool FIELD, int NPH>
+__device__ __forceinline__ void p2p_pair_f32(const ulonglong2 a, const ulonglong2 b, const f2 (&tx)[NPH],
+                                             const f2 (&ty)[NPH], const f2 (&tz)[NPH], f2 (&pu)[NPH],
+                                             f2 (&fx)[NPH], f2 (&fy)[NPH], f2 (&fz)[NPH]) {
+#pragma unroll
+  for (int k = 0; k < NPH; k++) {
+    const f2 dx = f2sub(tx[k], a.x), dy = f2sub(ty[k], a.y), dz = f2sub(tz[k], b.x);
+    const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+    float r0, r1;
+    f2unpack(r2, r0, r1);
+    float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
+    if (MASK) {
+      i0 = (r0 > 0.f) ? i0 : 0.f;
+      i1 = (r1 > 0.f) ? i1 : 0.f;
+    }
+    const f2 ri = f2pack(i0, i1);
+    pu[k] = f2fma(b.y, ri, pu[k]);
+    if (FIELD) {
+      const f2 w = f2mul(f2mul(f2mul(ri, ri), ri), b.y);
+      fx[k] = f2fma(w, dx, fx[k]);
+      fy[k] = f2fma(w, dy, fy[k]);
+      fz[k] = f2fma(w, dz, fz[k]);
+    }
+  }
+}
+
+// FP32 near-field tile, half-warp split: lanes 0-15 take the even and lanes
+// 16-31 the odd sources of the staged tile, each lane updating NPH packed
+// target pairs.  For the potential with up to two packed pairs, two
+// accumulator sets (alternate sources) keep independent chains in flight.
+template <bool MASK, bool FIELD, int NPH>
 __device__ __forceinline__ void p2p_tile_f32h(const DupRec* sb, int scount, int half, const f2 (&tx)[NPH],
                                               const f2 (&ty)[NPH], const f2 (&tz)[NPH], f2 (&pu)[NPH],
                                               f2 (&fx)[NPH], f2 (&fy)[NPH], f2 (&fz)[NPH]) {
   const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
+  if constexpr (FIELD || NPH > 2) {
+    // one accumulator set (register budget of the field and large tiles)
 #pragma unroll 2
-  for (int j = half; j < scount; j += 2) {
-    const ulonglong2 a = s2[2 * j];
-    const ulonglong2 b = s2[2 * j + 1];
+    for (int j = half; j < scount; j += 2)
+      p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz);
+    return;
+  }
+  f2 pu2[NPH], fx2[NPH], fy2[NPH], fz2[NPH];
 #pragma unroll
-    for (int k = 0; k < NPH; k++) {
-      const f2 dx = f2sub(tx[k], a.x), dy = f2sub(ty[k], a.y), dz = f2sub(tz[k], b.x);
-      const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
-      float r0, r1;
-      f2unpack(r2, r0, r1);
-      float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
-      if (MASK) {
-        i0 = (r0 > 0.f) ? i0 : 0.f;
-        i1 = (r1 > 0.f) ? i1 : 0.f;
-      }
-      const f2 ri = f2pack(i0, i1);
-      pu[k] = f2fma(b.y, ri, pu[k]);
-      if (FIELD) {
-        const f2 w = f2mul(f2mul(f2mul(ri, ri), ri), b.y);
-        fx[k] = f2fma(w, dx, fx[k]);
-        fy[k] = f2fma(w, dy, fy[k]);
-        fz[k] = f2fma(w, dz, fz[k]);
-      }
+  for (int k = 0; k < NPH; k++) pu2[k] = fx2[k] = fy2[k] = fz2[k] = 0ull;
+  int j = half;
+#pragma unroll 2
+  for (; j + 2 < scount; j += 4) {
+    const ulonglong2 a0 = s2[2 * j], b0 = s2[2 * j + 1];
+    const ulonglong2 a1 = s2[2 * j + 4], b1 = s2[2 * j + 5];
+    p2p_pair_f32<MASK, FIELD, NPH>(a0, b0, tx, ty, tz, pu, fx, fy, fz);
+    p2p_pair_f32<MASK, FIELD, NPH>(a1, b1, tx, ty, tz, pu2, fx2, fy2, fz2);
+  }
+  if (j < scount) p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz);
+#pragma unroll
+  for (int k = 0; k < NPH; k++) {
+    pu[k] = f2add(pu[k], pu2[k]);
+    if (FIELD) {
+      fx[k] = f2add(fx[k], fx2[k]);
+      fy[k] = f2add(fy[k], fy2[k]);
+      fz[k] = f2add(fz[k], fz2[k]);
     }
   }
 }
