@@ -202,12 +202,12 @@ def num_levels(n, leaf_size, s=2):
 class Tree:
     """Oracle hierarchy: median-split tree, geometry and interaction lists."""
 
-    def __init__(self, pos, leaf_size, s=2, theta=0.5, tie_target=False):
+    def __init__(self, pos, leaf_size, s=2, theta=0.5, tie_target=False, same_level=False):
         self.pos = _f64(pos).reshape(-1, 3)
         self.n = len(self.pos)
         self.leaf_size, self.s, self.theta = leaf_size, s, theta
-        h = lib().orc_tree_build(_p(self.pos), self.n, int(leaf_size), int(s),
-                                 float(theta), int(bool(tie_target)))
+        flags = (1 if tie_target else 0) | (2 if same_level else 0)
+        h = lib().orc_tree_build(_p(self.pos), self.n, int(leaf_size), int(s), float(theta), flags)
         if not h:
             raise ValueError("oracle tree build rejected its arguments")
         self._h = h

@@ -51,10 +51,11 @@ double orc_m2p(int p, const double* C, const double c[3], const double x[3]);
 /* ---- hierarchy (Sec. II.A, II.B) ---- */
 int orc_num_levels(int64_t n, int leaf_size, int s);
 typedef struct orc_tree orc_tree;
-/* tie_target = 0: equal average radii advance the source level (text of
- * Sec. II.B); 1: they advance the target level. */
+/* flags bit 0 (tie target): equal average radii advance the target level
+ * instead of the source level (text of Sec. II.B); bit 1 (same level): the
+ * same-level lists of Sec. II.B steps 1-3 instead of level marching. */
 orc_tree* orc_tree_build(const double* pos, int64_t n, int leaf_size, int s,
-                         double theta, int tie_target);
+                         double theta, int flags);
 void orc_tree_free(orc_tree* t);
 /* info[0]=L, [1]=n_boxes, [2]=n_m2l, [3]=n_p2p, [4]=n_leaves */
 void orc_tree_info(const orc_tree* t, int64_t* info);

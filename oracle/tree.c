@@ -23,7 +23,9 @@
  *    (the text) unless tie_target is set (the reading of the same-vs-cross
  *    table, whose rows advance the target).  The march ends when no candidate
  *    is left or both sides are at the leaf level; the remaining leaf pairs,
- *    self pairs included, form the near field.
+ *    self pairs included, form the near field.  With same_level set, the
+ *    lists are the same-level lists of Sec. II.B steps 1-3: both sides
+ *    descend together and only boxes of one level are compared.
  *  - Canonical list order: M2L sorted by (target global box, source global
  *    box), near-field pairs by (target leaf, source leaf).  The global id of
  *    box b on level l is (2^(s l) - 1) / (2^s - 1) + b.
@@ -38,6 +40,7 @@ struct orc_tree {
   int L, s;
   double theta;
   int tie_target;
+  int same_level;
   int64_t n_boxes, n_leaves;
   int32_t* perm;        /* tree position -> original index          */
   double* pos_tree;     /* positions in tree order, 3 per point     */
@@ -168,6 +171,17 @@ static void build_lists(orc_tree* t) {
       }
       break;
     }
+    n_cand = 0;
+    if (t->same_level) {
+      /* same-level lists (Sec. II.B steps 1-3): both sides descend together */
+      for (int64_t i = 0; i < n_keep; i++)
+        for (int64_t ct = 0; ct < nch; ct++)
+          for (int64_t cs = 0; cs < nch; cs++)
+            push(&cand, &n_cand, &cap_cand, (int32_t)(nch * keep[i].t + ct), (int32_t)(nch * keep[i].s + cs));
+      ls++;
+      lt++;
+      continue;
+    }
     int adv_src;
     if (can_s && can_t) {
       double as = t->level_avg[ls], at = t->level_avg[lt];
@@ -177,7 +191,6 @@ static void build_lists(orc_tree* t) {
     } else {
       adv_src = can_s;
     }
-    n_cand = 0;
     for (int64_t i = 0; i < n_keep; i++)
       for (int64_t c = 0; c < nch; c++) {
         if (adv_src) push(&cand, &n_cand, &cap_cand, keep[i].t, (int32_t)(nch * keep[i].s + c));
@@ -204,7 +217,7 @@ static void build_lists(orc_tree* t) {
 }
 
 orc_tree* orc_tree_build(const double* pos, int64_t n, int leaf_size, int s, double theta,
-                         int tie_target) {
+                         int flags) {
   if (n < 1 || s < 1 || leaf_size < (1 << s)) return NULL;
   orc_tree* t = (orc_tree*)calloc(1, sizeof(orc_tree));
   /* -0.0 is treated as +0.0 (x + 0.0 rounds -0.0 to +0.0) */
@@ -214,7 +227,8 @@ orc_tree* orc_tree_build(const double* pos, int64_t n, int leaf_size, int s, dou
   t->n = n;
   t->s = s;
   t->theta = theta;
-  t->tie_target = tie_target;
+  t->tie_target = (flags & 1) != 0;
+  t->same_level = (flags & 2) != 0;
   t->L = orc_num_levels(n, leaf_size, s);
   int L = t->L;
   t->n_boxes = level_offset(L + 1, s);

@@ -73,6 +73,22 @@ def batched_sets(n_sets=64, seed=0, n_min=10_000, n_max=500_000):
     return out
 
 
+def double_helix(n, seed=0, turns=4.0, radius=1.0, pitch=0.5, tube=0.05):
+    """Two interleaved helical strands (phase offset pi) of the given radius,
+    pitch and number of turns; points are scattered isotropically (Gaussian,
+    standard deviation `tube`) around the strand centre lines; charges
+    U[-1,1].  A project-made stand-in for the paper's double-helix example,
+    whose parameters are not given."""
+    rng = np.random.default_rng(seed)
+    s = rng.random(n) * turns * 2.0 * np.pi
+    strand = rng.integers(0, 2, n)
+    phase = s + np.pi * strand
+    pos = np.stack([radius * np.cos(phase), radius * np.sin(phase), pitch * s / (2.0 * np.pi)], axis=1)
+    pos += tube * rng.normal(size=(n, 3))
+    q = rng.uniform(-1.0, 1.0, n)
+    return pos, q
+
+
 def thin_film(cells=256, seed=0):
     """Film [0,1]^2 x [0,h], h = 1/cells, one random unit magnetisation m per
     cell.  Surface charges of div m sit at the top face centres (z = h,

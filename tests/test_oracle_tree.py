@@ -179,3 +179,60 @@ def test_average_radius_per_level(orc):
         off, nb = T.level_offset(l), 1 << (2 * l)
         assert T.level_avg_radius[l] == pytest.approx(T.radius[off:off + nb].mean(), rel=1e-14)
     assert np.all(np.diff(T.level_avg_radius) < 0)
+
+
+@pytest.mark.parametrize("s", [2, 3])
+def test_same_level_lists_brute_force(orc, s):
+    """Same-level lists (Sec. II.B steps 1-3) against their definition: a pair
+    of boxes on one level is weakly coupled when it is well separated and no
+    pair of their ancestors on a coarser level is; the leaf pairs with no
+    well-separated ancestor pair at any level are strongly coupled."""
+    pos, _ = workloads.double_helix(700, seed=4, turns=3.0, pitch=2.0)
+    theta = 0.6
+    T = orc.Tree(pos, 10, s, theta, same_level=True)
+    nl = 1 << (s * T.L)
+    m2l_ref, p2p_ref = set(), set()
+    for t in range(nl):
+        for s_ in range(nl):
+            hit = None
+            for l in range(T.L + 1):
+                gt, gs = _ancestor(T, t, l), _ancestor(T, s_, l)
+                if _ws(T, gs, gt, theta):
+                    hit = (gt, gs)
+                    break
+            if hit is None:
+                p2p_ref.add((t, s_))
+            else:
+                m2l_ref.add(hit)
+    assert set(zip(T.m2l_trg.tolist(), T.m2l_src.tolist())) == m2l_ref
+    assert set(zip(T.p2p_trg.tolist(), T.p2p_src.tolist())) == p2p_ref
+    assert T.n_m2l == len(m2l_ref) and T.n_p2p == len(p2p_ref)
+    key = T.m2l_trg.astype(np.int64) * T.n_boxes + T.m2l_src
+    assert np.all(np.diff(key) > 0)
+
+
+def test_same_vs_cross_level_on_helix(orc):
+    """The comparison of Sec. II.B on a double helix with s = 3: the level
+    march needs fewer weakly coupled pairs than same-level lists, by moving
+    pairs to coarser target or source levels; the leaves covered are the
+    same, and the root-level interactions agree."""
+    pos, q = workloads.double_helix(6000, seed=0, turns=5.0, pitch=3.4, tube=0.1)
+    A = orc.Tree(pos, 12, 3, 0.77, same_level=True)
+    B = orc.Tree(pos, 12, 3, 0.77)
+    assert B.n_m2l < A.n_m2l
+    lv = lambda T, g: _level_of(T, g)
+    la = {(lv(A, t), lv(A, s_)) for t, s_ in zip(A.m2l_trg, A.m2l_src)}
+    assert all(a == b for a, b in la)
+    lb = {(lv(B, t), lv(B, s_)) for t, s_ in zip(B.m2l_trg, B.m2l_src)}
+    assert any(a != b for a, b in lb)
+    first = min(l for l, _ in la)
+    na = sum(1 for t in A.m2l_trg if lv(A, t) == first)
+    nb = sum(1 for t, s_ in zip(B.m2l_trg, B.m2l_src) if lv(B, t) == first and lv(B, s_) == first)
+    assert na == nb
+    # both are complete, so the FMM results agree to the expansion error
+    sub = workloads.sample_targets(len(q), 200)
+    ua = A.eval(q, 6, targets=sub)
+    ub = B.eval(q, 6, targets=sub)
+    ud = orc.direct(pos, q, targets=sub)
+    for u in (ua, ub):
+        assert np.linalg.norm(u - ud) / np.linalg.norm(ud) < 1e-3
