@@ -63,9 +63,15 @@ enum {
 };
 
 enum {
-  FMM_TIE_TARGET = 1 /* equal average radii advance the target level (the
-                        same-vs-cross table of Sec. II.B) instead of the source
-                        level (the text of Sec. II.B, the default)            */
+  FMM_TIE_TARGET = 1, /* equal average radii advance the target level (the
+                         same-vs-cross table of Sec. II.B) instead of the source
+                         level (the text of Sec. II.B, the default)            */
+  FMM_SAME_LEVEL = 2  /* same-level lists (Sec. II.B, steps 1-3): source and
+                         target descend together and only boxes of one level
+                         are compared; no cross-level M2L pairs.  Overrides
+                         FMM_TIE_TARGET.  More M2L work than the default
+                         level march (the same-vs-cross table of Sec. II.B);
+                         kept for comparison                                   */
 };
 
 #define FMM_MAX_P 10 /* largest supported expansion order */
@@ -78,7 +84,7 @@ typedef struct {
   int splits;     /* s: bisections per level, 2^s children per box, 1..3        */
   double theta;   /* well-separation parameter of Eq. 4, 0 < theta < 1          */
   int precision;  /* FMM_FP64 or FMM_FP32C, used by the evaluation calls        */
-  int flags;      /* 0 or FMM_TIE_TARGET                                        */
+  int flags;      /* 0 or a combination of FMM_TIE_TARGET, FMM_SAME_LEVEL      */
 } fmm_params;
 
 typedef struct fmm_tree fmm_tree;

@@ -117,7 +117,7 @@ int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void*
     require(p.leaf_size >= (1 << p.splits) && p.leaf_size <= kMaxLeaf, "leaf_size must be in [2^splits, 256]");
     require(p.theta > 0.0 && p.theta < 1.0, "theta must be in (0, 1)");
     require(p.precision == FMM_FP64 || p.precision == FMM_FP32C, "precision must be FMM_FP64 or FMM_FP32C");
-    require((p.flags & ~FMM_TIE_TARGET) == 0, "unknown flags");
+    require((p.flags & ~(FMM_TIE_TARGET | FMM_SAME_LEVEL)) == 0, "unknown flags");
     auto t0 = std::chrono::steady_clock::now();
     ensure_tables();
     t = new fmm_tree();

@@ -24,7 +24,9 @@
 // the children of the side whose level has the larger average radius (ties:
 // source, or target with FMM_TIE_TARGET); pairs left when both sides reach
 // the leaf level form the near field.  Average radii are adjacent-pair sums
-// repeated down to one value, divided by the box count.
+// repeated down to one value, divided by the box count.  FMM_SAME_LEVEL
+// replaces the march by the same-level lists of Sec. II.B steps 1-3: both
+// sides descend together, so only boxes of one level are compared.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -633,12 +635,23 @@ __device__ __forceinline__ int64_t lower_bound32(const int32_t* a, int64_t n, in
   return lo;
 }
 
-// children of the advanced side; the result stays sorted by (target, source)
+// children of the advanced side (adv: 1 source, 0 target, 2 both); the result
+// stays sorted by (target, source)
 __global__ void expand_kernel(const int32_t* __restrict__ kt, const int32_t* __restrict__ ks, int64_t nk,
-                              int nch, int adv_src, int32_t* __restrict__ ct, int32_t* __restrict__ cs) {
+                              int nch, int adv, int32_t* __restrict__ ct, int32_t* __restrict__ cs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nk; e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t t = kt[e], s = ks[e];
-    if (adv_src) {
+    if (adv == 2) {
+      const int64_t first = lower_bound32(kt, nk, t);
+      const int64_t last = lower_bound32(kt, nk, t + 1);
+      const int64_t k = last - first;
+      for (int c = 0; c < nch; c++)
+        for (int d = 0; d < nch; d++) {
+          const int64_t o = (int64_t)nch * nch * first + (int64_t)c * nch * k + (e - first) * nch + d;
+          ct[o] = nch * t + c;
+          cs[o] = nch * s + d;
+        }
+    } else if (adv == 1) {
       for (int c = 0; c < nch; c++) {
         ct[nch * e + c] = t;
         cs[nch * e + c] = nch * s + c;
@@ -1060,6 +1073,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   int32_t *p2p_t = nullptr, *p2p_s = nullptr;
   int64_t np = 0;
   const bool tie_target = (t->prm.flags & FMM_TIE_TARGET) != 0;
+  const bool same_level = (t->prm.flags & FMM_SAME_LEVEL) != 0;
   for (;;) {
     int64_t* fws = scratch_alloc<int64_t>(nc);
     int64_t* fkeep = scratch_alloc<int64_t>(nc);
@@ -1093,22 +1107,24 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
       ct = cs = nullptr;
       break;
     }
-    bool adv_src;
-    if (can_s && can_t) {
+    int adv;  // 1 source, 0 target, 2 both (same-level lists)
+    if (same_level) {
+      adv = 2;
+    } else if (can_s && can_t) {
       const double as = t->level_avg_host[ls], at = t->level_avg_host[lt];
-      adv_src = (as > at) || (as == at && !tie_target);
+      adv = (as > at) || (as == at && !tie_target) ? 1 : 0;
     } else {
-      adv_src = can_s;
+      adv = can_s ? 1 : 0;
     }
-    nc = nkeep * nch;
+    nc = nkeep * (adv == 2 ? nch * nch : nch);
     ct = dev_alloc<int32_t>(nullptr, nc);
     cs = dev_alloc<int32_t>(nullptr, nc);
-    expand_kernel<<<grid_for(nkeep, 256), 256, 0, st>>>(kt, ks, nkeep, nch, adv_src ? 1 : 0, ct, cs);
+    expand_kernel<<<grid_for(nkeep, 256), 256, 0, st>>>(kt, ks, nkeep, nch, adv, ct, cs);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(kt), cudaFree(ks);
-    if (adv_src) ls++;
-    else lt++;
+    if (adv != 0) ls++;
+    if (adv != 1) lt++;
   }
 
   // ---- M2L lists as CSR by target, sources ascending ----

@@ -44,7 +44,8 @@ def cuda(x):
 
 def build_both(F, orc, pos, p, leaf, s=2, theta=0.5, prec=1, flags=0):
     T = F.fmm_build_tree(cuda(pos), p, leaf, s, theta, prec, flags)
-    O = orc.Tree(pos, leaf, s, theta, tie_target=bool(flags & F.FMM_TIE_TARGET))
+    O = orc.Tree(pos, leaf, s, theta, tie_target=bool(flags & F.FMM_TIE_TARGET),
+                 same_level=bool(flags & F.FMM_SAME_LEVEL))
     return T, O
 
 
@@ -86,6 +87,10 @@ TREE_CASES = [
     ("n4097", lambda: workloads.uniform_cube(4097, 8)[0], 8, 2, 0.5, 0),
     ("duplicates", lambda: dup_grid(3000, 9), 16, 2, 0.5, 0),
     ("cube250k", lambda: workloads.uniform_cube(250000, 10)[0], 64, 2, 0.5, 0),
+    ("helix_same_level_s3", lambda: workloads.double_helix(6000, 0, 5.0, 1.0, 3.4, 0.1)[0], 12, 3, 0.77, 2),
+    ("helix_cross_s3", lambda: workloads.double_helix(6000, 0, 5.0, 1.0, 3.4, 0.1)[0], 12, 3, 0.77, 0),
+    ("cube_same_level", lambda: workloads.uniform_cube(20000, 11)[0], 32, 2, 0.5, 2),
+    ("clusters_same_level_tie", lambda: workloads.gaussian_clusters(7000, 12)[0], 16, 2, 0.6, 3),
 ]
 
 
@@ -124,6 +129,16 @@ def test_potential_parity(F, orc, name, mk, p, leaf, s, theta):
     print("%s: fp64 vs oracle %.3e, fp32c vs oracle %.3e" % (name, e64, e32))
     assert e64 <= TOL_FP64
     assert e32 <= TOL_FP32
+
+
+def test_same_level_potential_parity(F, orc):
+    pos, q = workloads.double_helix(30000, 1, 5.0, 1.0, 3.4, 0.1)
+    T, O = build_both(F, orc, pos, 8, 24, 3, 0.6, F.FMM_FP64, F.FMM_SAME_LEVEL)
+    u_o = O.eval(q, 8)
+    assert rel_l2(F.fmm_eval_potential(T, cuda(q)).cpu().numpy(), u_o) <= TOL_FP64
+    F.fmm_tree_set_precision(T, F.FMM_FP32C)
+    assert rel_l2(F.fmm_eval_potential(T, cuda(q)).cpu().numpy(), u_o) <= TOL_FP32
+    F.fmm_tree_status(T)
 
 
 @pytest.mark.parametrize("name,mk,p,leaf,s,theta", POT_CASES[:4], ids=[c[0] for c in POT_CASES[:4]])
