@@ -73,6 +73,17 @@ def lib():
         L.orc_fmm_eval.argtypes = [vp, i, vp, vp, i64, vp, vp]
         L.orc_direct.argtypes = [vp, vp, i64, vp, i64, vp, vp]
         L.orc_direct_vjp.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.orc_tree2_build.argtypes = [vp, i64, vp, i64, i, i, d, i]
+        L.orc_tree2_build.restype = vp
+        L.orc_tree2_free.argtypes = [vp]
+        L.orc_tree2_source.argtypes = [vp]
+        L.orc_tree2_source.restype = vp
+        L.orc_tree2_target.argtypes = [vp]
+        L.orc_tree2_target.restype = vp
+        L.orc_tree2_info.argtypes = [vp, vp]
+        L.orc_tree2_export_lists.argtypes = [vp] * 5
+        L.orc_fmm2_eval.argtypes = [vp, i, vp, vp, vp]
+        L.orc_direct2.argtypes = [vp, vp, i64, vp, i64, vp, vp]
         L.orc_num_threads.restype = i
         _lib = L
     return _lib
@@ -248,6 +259,82 @@ class Tree:
         lib().orc_fmm_eval(self._h, int(p), _p(q), _p(tg), 0 if tg is None else m,
                            _p(u), _p(f))
         return (u, f) if field else u
+
+
+class _Hierarchy:
+    """Read-only view of one of the two hierarchies of a Tree2."""
+
+    def __init__(self, h, n, s):
+        info = np.zeros(5, dtype=np.int64)
+        lib().orc_tree_info(h, _p(info))
+        self.L, self.n_boxes, _, _, self.n_leaves = (int(v) for v in info)
+        self.n, self.s = n, s
+        self.perm = np.zeros(n, dtype=np.int32)
+        self.box_start = np.zeros(self.n_boxes, dtype=np.int64)
+        self.box_count = np.zeros(self.n_boxes, dtype=np.int64)
+        self.center = np.zeros((self.n_boxes, 3))
+        self.radius = np.zeros(self.n_boxes)
+        self.level_avg_radius = np.zeros(self.L + 1)
+        lib().orc_tree_export(h, _p(self.perm), _p(self.box_start), _p(self.box_count),
+                              _p(self.center), _p(self.radius), _p(self.level_avg_radius))
+
+    def level_offset(self, l):
+        return sum(1 << (self.s * i) for i in range(l))
+
+
+class Tree2:
+    """Separate source and target hierarchies (Sec. II.B, final part) and the
+    level-march lists between them.  M2L pairs use combined box ids (source
+    boxes first, target box g at src.n_boxes + g); near-field pairs are
+    (target leaf, source leaf)."""
+
+    def __init__(self, src_pos, trg_pos, leaf_size, s=2, theta=0.5, tie_target=False):
+        sp = _f64(src_pos).reshape(-1, 3)
+        tp = _f64(trg_pos).reshape(-1, 3)
+        self.src_pos, self.trg_pos = sp, tp
+        self.leaf_size, self.s, self.theta = leaf_size, s, theta
+        h = lib().orc_tree2_build(_p(sp), len(sp), _p(tp), len(tp), int(leaf_size), int(s),
+                                  float(theta), 1 if tie_target else 0)
+        if not h:
+            raise ValueError("oracle tree build rejected its arguments")
+        self._h = h
+        self.src = _Hierarchy(lib().orc_tree2_source(h), len(sp), s)
+        self.trg = _Hierarchy(lib().orc_tree2_target(h), len(tp), s)
+        info = np.zeros(2, dtype=np.int64)
+        lib().orc_tree2_info(h, _p(info))
+        self.n_m2l, self.n_p2p = (int(v) for v in info)
+        self.m2l_trg = np.zeros(self.n_m2l, dtype=np.int32)
+        self.m2l_src = np.zeros(self.n_m2l, dtype=np.int32)
+        self.p2p_trg = np.zeros(self.n_p2p, dtype=np.int32)
+        self.p2p_src = np.zeros(self.n_p2p, dtype=np.int32)
+        lib().orc_tree2_export_lists(h, _p(self.m2l_trg), _p(self.m2l_src),
+                                     _p(self.p2p_trg), _p(self.p2p_src))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_tree2_free(h)
+            self._h = None
+
+    def eval(self, q, p, field=False):
+        """FMM potential (and field) of charges q (source order) at the
+        targets (target order)."""
+        q = _f64(q)
+        m = len(self.trg_pos)
+        u = np.zeros(m)
+        f = np.zeros((m, 3)) if field else None
+        lib().orc_fmm2_eval(self._h, int(p), _p(q), _p(u), _p(f))
+        return (u, f) if field else u
+
+
+def direct2(src_pos, q, trg_pos, field=False):
+    """Direct sum of Eq. 1-3 of charges q at src_pos, evaluated at trg_pos;
+    zero distances contribute nothing."""
+    sp, q, tp = _f64(src_pos).reshape(-1, 3), _f64(q), _f64(trg_pos).reshape(-1, 3)
+    u = np.zeros(len(tp))
+    f = np.zeros((len(tp), 3)) if field else None
+    lib().orc_direct2(_p(sp), _p(q), len(q), _p(tp), len(tp), _p(u), _p(f))
+    return (u, f) if field else u
 
 
 def direct(pos, q, targets=None, field=False):

@@ -34,6 +34,12 @@ const int32_t* orc__m2l_src(const orc_tree* t);
 int64_t orc__n_p2p(const orc_tree* t);
 const int32_t* orc__p2p_trg(const orc_tree* t);
 const int32_t* orc__p2p_src(const orc_tree* t);
+int64_t orc2__n_m2l(const orc_tree2* t2);
+const int32_t* orc2__m2l_trg(const orc_tree2* t2);
+const int32_t* orc2__m2l_src(const orc_tree2* t2);
+int64_t orc2__n_p2p(const orc_tree2* t2);
+const int32_t* orc2__p2p_trg(const orc_tree2* t2);
+const int32_t* orc2__p2p_src(const orc_tree2* t2);
 
 static const double FOUR_PI = 12.566370614359172953850573533118;
 
@@ -214,6 +220,133 @@ void orc_direct(const double* pos, const double* q, int64_t n, const int64_t* ta
     }
     u[k] = -acc / FOUR_PI;
     /* grad(1/r) = -(r_i - r_j)/r^3, so field = -grad u = -(1/4pi) sum q (r_i - r_j)/r^3 */
+    if (field) {
+      field[3 * k] = -g0 / FOUR_PI;
+      field[3 * k + 1] = -g1 / FOUR_PI;
+      field[3 * k + 2] = -g2 / FOUR_PI;
+    }
+  }
+}
+
+/* Separate source and target trees (Sec. II.B, final part): multipoles on the
+ * source tree (mpls, M2M), M2L from source boxes into target boxes, locals on
+ * the target tree (L2L), evloc and evdir at every target point. */
+void orc_fmm2_eval(const orc_tree2* t2, int p, const double* q, double* u, double* field) {
+  const orc_tree* S = orc_tree2_source(t2);
+  const orc_tree* T = orc_tree2_target(t2);
+  const int s = orc__splits(S);
+  const int64_t nch = (int64_t)1 << s;
+  const int P = (p + 1) * (p + 1);
+  const int Ls = orc__levels(S), Lt = orc__levels(T);
+  const int64_t ns = orc__n(S), nt = orc__n(T);
+  const int64_t nbs = orc__n_boxes(S), nbt = orc__n_boxes(T);
+  const int32_t* perm_s = orc__perm(S);
+  const int32_t* perm_t = orc__perm(T);
+  const double* Xs = orc__pos_tree(S);
+  const double* Xt = orc__pos_tree(T);
+  const int64_t *bs_s = orc__box_start(S), *bc_s = orc__box_count(S);
+  const int64_t *bs_t = orc__box_start(T), *bc_t = orc__box_count(T);
+  const double* cen_s = orc__center(S);
+  const double* cen_t = orc__center(T);
+  const int64_t leaf_off_s = level_off(Ls, s), leaf_off_t = level_off(Lt, s);
+  const int64_t nl_s = (int64_t)1 << (s * Ls), nl_t = (int64_t)1 << (s * Lt);
+
+  /* sort: charges into source-tree order */
+  double* qt = (double*)malloc(sizeof(double) * (size_t)ns);
+  for (int64_t i = 0; i < ns; i++) qt[i] = q[perm_s[i]];
+  double* C = (double*)calloc((size_t)nbs * P, sizeof(double));
+  double* D = (double*)calloc((size_t)nbt * P, sizeof(double));
+
+  /* mpls and M2M on the source tree */
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t b = 0; b < nl_s; b++) {
+    int64_t g = leaf_off_s + b;
+    orc_p2m(p, Xs + 3 * bs_s[g], qt + bs_s[g], bc_s[g], cen_s + 3 * g, C + (size_t)g * P);
+  }
+  for (int l = Ls - 1; l >= 0; l--) {
+    int64_t off = level_off(l, s), offc = level_off(l + 1, s);
+    int64_t nb = (int64_t)1 << (s * l);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t b = 0; b < nb; b++)
+      for (int64_t c = 0; c < nch; c++) {
+        int64_t gc = offc + nch * b + c;
+        orc_m2m(p, C + (size_t)gc * P, cen_s + 3 * gc, cen_s + 3 * (off + b), C + (size_t)(off + b) * P);
+      }
+  }
+  /* M2L: source box -> target box (combined target id = nbs + g) */
+  const int64_t nm = orc2__n_m2l(t2);
+  const int32_t* mt = orc2__m2l_trg(t2);
+  const int32_t* ms = orc2__m2l_src(t2);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t g = 0; g < nbt; g++)
+    for (int64_t k = first_ge(mt, nm, (int32_t)(nbs + g)); k < nm && mt[k] == nbs + g; k++)
+      orc_m2l(p, C + (size_t)ms[k] * P, cen_s + 3 * (int64_t)ms[k], cen_t + 3 * g, D + (size_t)g * P);
+  /* L2L on the target tree */
+  for (int l = 1; l <= Lt; l++) {
+    int64_t off = level_off(l, s), offp = level_off(l - 1, s);
+    int64_t nb = (int64_t)1 << (s * l);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < nb; b++) {
+      int64_t gp = offp + b / nch;
+      orc_l2l(p, D + (size_t)gp * P, cen_t + 3 * gp, cen_t + 3 * (off + b), D + (size_t)(off + b) * P);
+    }
+  }
+  /* evloc and evdir at every target point, per target leaf */
+  const int64_t np = orc2__n_p2p(t2);
+  const int32_t* pt = orc2__p2p_trg(t2);
+  const int32_t* ps = orc2__p2p_src(t2);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t leaf = 0; leaf < nl_t; leaf++) {
+    int64_t g = leaf_off_t + leaf;
+    int64_t e0 = first_ge(pt, np, (int32_t)leaf);
+    for (int64_t i = bs_t[g]; i < bs_t[g] + bc_t[g]; i++) {
+      double grad[3];
+      double uf = orc_l2p(p, D + (size_t)g * P, cen_t + 3 * g, Xt + 3 * i, grad);
+      double un = 0.0, gn[3] = {0.0, 0.0, 0.0};
+      for (int64_t e = e0; e < np && pt[e] == leaf; e++) {
+        int64_t gs = leaf_off_s + ps[e];
+        for (int64_t j = bs_s[gs]; j < bs_s[gs] + bc_s[gs]; j++) {
+          double dx = Xt[3 * i] - Xs[3 * j], dy = Xt[3 * i + 1] - Xs[3 * j + 1], dz = Xt[3 * i + 2] - Xs[3 * j + 2];
+          double r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 == 0.0) continue;
+          double r = sqrt(r2);
+          un += qt[j] / r;
+          double w = qt[j] / (r2 * r);
+          gn[0] -= w * dx;
+          gn[1] -= w * dy;
+          gn[2] -= w * dz;
+        }
+      }
+      int64_t k = perm_t[i];
+      u[k] = -(uf + un) / FOUR_PI;
+      if (field)
+        for (int a = 0; a < 3; a++) field[3 * k + a] = (grad[a] + gn[a]) / FOUR_PI;
+    }
+  }
+  (void)nt;
+  free(qt);
+  free(C);
+  free(D);
+}
+
+void orc_direct2(const double* src_pos, const double* q, int64_t n_src, const double* trg_pos,
+                 int64_t n_trg, double* u, double* field) {
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n_trg; k++) {
+    double acc = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (int64_t j = 0; j < n_src; j++) {
+      double dx = trg_pos[3 * k] - src_pos[3 * j], dy = trg_pos[3 * k + 1] - src_pos[3 * j + 1],
+             dz = trg_pos[3 * k + 2] - src_pos[3 * j + 2];
+      double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 == 0.0) continue;
+      double r = sqrt(r2);
+      acc += q[j] / r;
+      double w = q[j] / (r2 * r);
+      g0 += w * dx;
+      g1 += w * dy;
+      g2 += w * dz;
+    }
+    u[k] = -acc / FOUR_PI;
     if (field) {
       field[3 * k] = -g0 / FOUR_PI;
       field[3 * k + 1] = -g1 / FOUR_PI;

@@ -65,6 +65,23 @@ void orc_tree_export(const orc_tree* t, int32_t* perm, int64_t* box_start,
 void orc_tree_export_lists(const orc_tree* t, int32_t* m2l_trg, int32_t* m2l_src,
                            int32_t* p2p_trg, int32_t* p2p_src);
 
+/* Separate source and target hierarchies (Sec. II.B, final part): two trees
+ * with the same leaf_size, s and theta, lists by the level march between
+ * them (flags bit 0: tie target; same-level lists are not offered).  M2L
+ * pairs use combined ids (source boxes first, target box g at n_boxes_src +
+ * g); near-field pairs are (target leaf, source leaf).  The two trees are
+ * exported with orc_tree_export on orc_tree2_source / orc_tree2_target. */
+typedef struct orc_tree2 orc_tree2;
+orc_tree2* orc_tree2_build(const double* src_pos, int64_t n_src, const double* trg_pos,
+                           int64_t n_trg, int leaf_size, int s, double theta, int flags);
+void orc_tree2_free(orc_tree2* t2);
+const orc_tree* orc_tree2_source(const orc_tree2* t2);
+const orc_tree* orc_tree2_target(const orc_tree2* t2);
+/* info[0]=n_m2l, [1]=n_p2p */
+void orc_tree2_info(const orc_tree2* t2, int64_t* info);
+void orc_tree2_export_lists(const orc_tree2* t2, int32_t* m2l_trg, int32_t* m2l_src,
+                            int32_t* p2p_trg, int32_t* p2p_src);
+
 /* ---- evaluation (Sec. II, Eq. 2-3, stages of Sec. III.A) ---- */
 /* u[i] = -1/(4 pi) sum_{j != i} q_j / |r_i - r_j|, field = -grad u.
  * targets == NULL: all points; else only the listed original indices,
@@ -73,6 +90,11 @@ void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targ
                   int64_t n_targets, double* u, double* field);
 void orc_direct(const double* pos, const double* q, int64_t n, const int64_t* targets,
                 int64_t n_targets, double* u, double* field);
+/* Potential and field of the charges q at src_pos evaluated at n_trg target
+ * positions (target order); zero distances contribute nothing. */
+void orc_fmm2_eval(const orc_tree2* t2, int p, const double* q, double* u, double* field);
+void orc_direct2(const double* src_pos, const double* q, int64_t n_src, const double* trg_pos,
+                 int64_t n_trg, double* u, double* field);
 /* vector-Jacobian product of u = K q at a fixed geometry:
  * dq = K g,  dpos_k = g_k grad u(r_k) + q_k grad v(r_k) with v = K g. */
 void orc_direct_vjp(const double* pos, const double* q, const double* g, int64_t n,

@@ -99,23 +99,23 @@ static void bbox(const double* pos, const int32_t* idx, int64_t cnt, double lo[3
     }
 }
 
-/* Well-separation criterion, Eq. 4. */
-static int well_separated(const orc_tree* t, int64_t gs, int64_t gt) {
-  double dx = t->center[3 * gs + 0] - t->center[3 * gt + 0];
-  double dy = t->center[3 * gs + 1] - t->center[3 * gt + 1];
-  double dz = t->center[3 * gs + 2] - t->center[3 * gt + 2];
+/* Well-separation criterion, Eq. 4, between a source box (centre cs, radius
+ * rs) and a target box (centre ct, radius rt). */
+static int well_separated(const double* cs, double rs, const double* ct, double rt, double theta) {
+  double dx = cs[0] - ct[0];
+  double dy = cs[1] - ct[1];
+  double dz = cs[2] - ct[2];
   double dxx = dx * dx;
   double dyy = dy * dy;
   double dzz = dz * dz;
   double d2 = dxx + dyy;
   d2 = d2 + dzz;
   double d = sqrt(d2);
-  double rs = t->radius[gs], rt = t->radius[gt];
   double R = (rs > rt) ? rs : rt;
   double r = (rs > rt) ? rt : rs;
-  double tr = t->theta * r;
+  double tr = theta * r;
   double lhs = R + tr;
-  double rhs = t->theta * d;
+  double rhs = theta * d;
   return (d > 0.0) && (lhs <= rhs);
 }
 
@@ -139,40 +139,55 @@ static void push(pair32** arr, int64_t* n, int64_t* cap, int32_t t, int32_t s) {
   (*n)++;
 }
 
-static void build_lists(orc_tree* t) {
-  int L = t->L, s = t->s;
-  int64_t nch = (int64_t)1 << s;
+typedef struct {
+  int64_t n_m2l, n_p2p;
+  int32_t *m2l_trg, *m2l_src;
+  int32_t *p2p_trg, *p2p_src;
+} lists;
+
+/* Interaction lists between the boxes of a source tree S and a target tree T
+ * (the same tree for the usual evaluation).  Level march of Sec. II.B: start
+ * at both roots; well-separated candidate pairs go to the M2L list; the others
+ * are replaced by the children of the side whose level has the larger average
+ * radius (ties: the source, or the target with tie_target), the other side's
+ * children once one side has no finer level; pairs left when both sides are
+ * at their leaf levels form the near field.  same_level: both sides descend
+ * together (Sec. II.B steps 1-3).  M2L target ids are offset by trg_base. */
+static void march(const orc_tree* S, const orc_tree* T, double theta, int tie_target, int same_level,
+                  int64_t trg_base, lists* out) {
+  const int s = S->s;
+  const int64_t nch = (int64_t)1 << s;
   pair32 *cand = NULL, *keep = NULL, *m2l = NULL;
   int64_t n_cand = 0, cap_cand = 0, n_keep = 0, cap_keep = 0, n_m2l = 0, cap_m2l = 0;
   push(&cand, &n_cand, &cap_cand, 0, 0);
   int ls = 0, lt = 0;
-  int64_t offs = 0, offt = 0;
-  t->n_p2p = 0;
-  t->p2p_trg = t->p2p_src = NULL;
+  out->n_p2p = 0;
+  out->p2p_trg = out->p2p_src = NULL;
   for (;;) {
-    offs = level_offset(ls, s);
-    offt = level_offset(lt, s);
+    int64_t offs = level_offset(ls, s), offt = level_offset(lt, s);
     n_keep = 0;
     for (int64_t i = 0; i < n_cand; i++) {
       int64_t gs = offs + cand[i].s, gt = offt + cand[i].t;
-      if (well_separated(t, gs, gt)) push(&m2l, &n_m2l, &cap_m2l, (int32_t)gt, (int32_t)gs);
-      else push(&keep, &n_keep, &cap_keep, cand[i].t, cand[i].s);
+      if (well_separated(S->center + 3 * gs, S->radius[gs], T->center + 3 * gt, T->radius[gt], theta))
+        push(&m2l, &n_m2l, &cap_m2l, (int32_t)(trg_base + gt), (int32_t)gs);
+      else
+        push(&keep, &n_keep, &cap_keep, cand[i].t, cand[i].s);
     }
     if (n_keep == 0) break;
-    int can_s = ls < L, can_t = lt < L;
+    int can_s = ls < S->L, can_t = lt < T->L;
     if (!can_s && !can_t) {
       qsort(keep, (size_t)n_keep, sizeof(pair32), cmp_pair);
-      t->n_p2p = n_keep;
-      t->p2p_trg = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_keep);
-      t->p2p_src = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_keep);
+      out->n_p2p = n_keep;
+      out->p2p_trg = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_keep);
+      out->p2p_src = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_keep);
       for (int64_t i = 0; i < n_keep; i++) {
-        t->p2p_trg[i] = keep[i].t;
-        t->p2p_src[i] = keep[i].s;
+        out->p2p_trg[i] = keep[i].t;
+        out->p2p_src[i] = keep[i].s;
       }
       break;
     }
     n_cand = 0;
-    if (t->same_level) {
+    if (same_level) {
       /* same-level lists (Sec. II.B steps 1-3): both sides descend together */
       for (int64_t i = 0; i < n_keep; i++)
         for (int64_t ct = 0; ct < nch; ct++)
@@ -184,10 +199,10 @@ static void build_lists(orc_tree* t) {
     }
     int adv_src;
     if (can_s && can_t) {
-      double as = t->level_avg[ls], at = t->level_avg[lt];
+      double as = S->level_avg[ls], at = T->level_avg[lt];
       if (as > at) adv_src = 1;
       else if (as < at) adv_src = 0;
-      else adv_src = !t->tie_target;
+      else adv_src = !tie_target;
     } else {
       adv_src = can_s;
     }
@@ -200,26 +215,38 @@ static void build_lists(orc_tree* t) {
     else lt++;
   }
   qsort(m2l, (size_t)n_m2l, sizeof(pair32), cmp_pair);
-  t->n_m2l = n_m2l;
-  t->m2l_trg = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_m2l + 1));
-  t->m2l_src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_m2l + 1));
+  out->n_m2l = n_m2l;
+  out->m2l_trg = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_m2l + 1));
+  out->m2l_src = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_m2l + 1));
   for (int64_t i = 0; i < n_m2l; i++) {
-    t->m2l_trg[i] = m2l[i].t;
-    t->m2l_src[i] = m2l[i].s;
+    out->m2l_trg[i] = m2l[i].t;
+    out->m2l_src[i] = m2l[i].s;
   }
-  if (!t->p2p_trg) {
-    t->p2p_trg = (int32_t*)malloc(sizeof(int32_t));
-    t->p2p_src = (int32_t*)malloc(sizeof(int32_t));
+  if (!out->p2p_trg) {
+    out->p2p_trg = (int32_t*)malloc(sizeof(int32_t));
+    out->p2p_src = (int32_t*)malloc(sizeof(int32_t));
   }
   free(cand);
   free(keep);
   free(m2l);
 }
 
+static void build_lists(orc_tree* t) {
+  lists li;
+  march(t, t, t->theta, t->tie_target, t->same_level, 0, &li);
+  t->n_m2l = li.n_m2l;
+  t->m2l_trg = li.m2l_trg;
+  t->m2l_src = li.m2l_src;
+  t->n_p2p = li.n_p2p;
+  t->p2p_trg = li.p2p_trg;
+  t->p2p_src = li.p2p_src;
+}
+
 orc_tree* orc_tree_build(const double* pos, int64_t n, int leaf_size, int s, double theta,
                          int flags) {
   if (n < 1 || s < 1 || leaf_size < (1 << s)) return NULL;
   orc_tree* t = (orc_tree*)calloc(1, sizeof(orc_tree));
+  /* flags bit 2 (internal): hierarchy only, no lists */
   /* -0.0 is treated as +0.0 (x + 0.0 rounds -0.0 to +0.0) */
   double* canon = (double*)malloc(sizeof(double) * 3 * (size_t)n);
   for (int64_t i = 0; i < 3 * n; i++) canon[i] = pos[i] + 0.0;
@@ -308,7 +335,7 @@ orc_tree* orc_tree_build(const double* pos, int64_t n, int leaf_size, int s, dou
   }
   free(seg_start);
   free(canon);
-  build_lists(t);
+  if (!(flags & 4)) build_lists(t);
   return t;
 }
 
@@ -353,6 +380,69 @@ void orc_tree_export_lists(const orc_tree* t, int32_t* m2l_trg, int32_t* m2l_src
   if (p2p_trg) memcpy(p2p_trg, t->p2p_trg, sizeof(int32_t) * (size_t)t->n_p2p);
   if (p2p_src) memcpy(p2p_src, t->p2p_src, sizeof(int32_t) * (size_t)t->n_p2p);
 }
+
+/* ---- separate source and target hierarchies (Sec. II.B, final part) ----
+ * Two trees built with the same N_max, s and theta; the lists compare source
+ * boxes with target boxes by the level march (same-level lists are not
+ * defined when the two trees have different depths).  Combined box ids:
+ * source boxes 0 .. NB_s - 1, target box g at NB_s + g. */
+struct orc_tree2 {
+  orc_tree* src;
+  orc_tree* trg;
+  lists li;
+};
+
+orc_tree2* orc_tree2_build(const double* src_pos, int64_t n_src, const double* trg_pos, int64_t n_trg,
+                           int leaf_size, int s, double theta, int flags) {
+  if (flags & ~1) return NULL;
+  orc_tree* S = orc_tree_build(src_pos, n_src, leaf_size, s, theta, 4);
+  orc_tree* T = orc_tree_build(trg_pos, n_trg, leaf_size, s, theta, 4);
+  if (!S || !T) {
+    orc_tree_free(S);
+    orc_tree_free(T);
+    return NULL;
+  }
+  orc_tree2* t2 = (orc_tree2*)calloc(1, sizeof(orc_tree2));
+  t2->src = S;
+  t2->trg = T;
+  march(S, T, theta, flags & 1, 0, S->n_boxes, &t2->li);
+  return t2;
+}
+
+void orc_tree2_free(orc_tree2* t2) {
+  if (!t2) return;
+  orc_tree_free(t2->src);
+  orc_tree_free(t2->trg);
+  free(t2->li.m2l_trg);
+  free(t2->li.m2l_src);
+  free(t2->li.p2p_trg);
+  free(t2->li.p2p_src);
+  free(t2);
+}
+
+const orc_tree* orc_tree2_source(const orc_tree2* t2) { return t2->src; }
+const orc_tree* orc_tree2_target(const orc_tree2* t2) { return t2->trg; }
+
+void orc_tree2_info(const orc_tree2* t2, int64_t* info) {
+  info[0] = t2->li.n_m2l;
+  info[1] = t2->li.n_p2p;
+}
+
+void orc_tree2_export_lists(const orc_tree2* t2, int32_t* m2l_trg, int32_t* m2l_src, int32_t* p2p_trg,
+                            int32_t* p2p_src) {
+  const lists* li = &t2->li;
+  if (m2l_trg) memcpy(m2l_trg, li->m2l_trg, sizeof(int32_t) * (size_t)li->n_m2l);
+  if (m2l_src) memcpy(m2l_src, li->m2l_src, sizeof(int32_t) * (size_t)li->n_m2l);
+  if (p2p_trg) memcpy(p2p_trg, li->p2p_trg, sizeof(int32_t) * (size_t)li->n_p2p);
+  if (p2p_src) memcpy(p2p_src, li->p2p_src, sizeof(int32_t) * (size_t)li->n_p2p);
+}
+
+int64_t orc2__n_m2l(const orc_tree2* t2) { return t2->li.n_m2l; }
+const int32_t* orc2__m2l_trg(const orc_tree2* t2) { return t2->li.m2l_trg; }
+const int32_t* orc2__m2l_src(const orc_tree2* t2) { return t2->li.m2l_src; }
+int64_t orc2__n_p2p(const orc_tree2* t2) { return t2->li.n_p2p; }
+const int32_t* orc2__p2p_trg(const orc_tree2* t2) { return t2->li.p2p_trg; }
+const int32_t* orc2__p2p_src(const orc_tree2* t2) { return t2->li.p2p_src; }
 
 /* Internal accessors for the evaluation file. */
 const int32_t* orc__perm(const orc_tree* t) { return t->perm; }
