@@ -90,12 +90,13 @@ typedef struct {
 typedef struct fmm_tree fmm_tree;
 
 typedef struct {
-  int64_t n;             /* points                                              */
-  int levels;            /* L: the leaf level; the root is level 0              */
+  int64_t n;             /* points (sources + targets for two hierarchies)      */
+  int levels;            /* L: the leaf level; the root is level 0 (the target
+                            tree's for two hierarchies)                         */
   int p, splits, leaf_size, precision;
   double theta;
   int64_t n_boxes;       /* sum over levels of 2^(s l)                          */
-  int64_t n_leaves;      /* 2^(s L)                                             */
+  int64_t n_leaves;      /* 2^(s L) (target leaves for two hierarchies)         */
   int64_t n_m2l;         /* multipole-to-local interactions, all levels         */
   int64_t n_p2p;         /* near-field leaf pairs (self pairs included)         */
   int64_t n_p2p_pairs;   /* near-field point pairs: sum over leaf pairs |S||T|  */
@@ -104,6 +105,10 @@ typedef struct {
   int64_t kernel_launches; /* kernels this library launched for evaluations of
                               this tree so far                                  */
   int n_trees;           /* 1, or the number of trees of a merged batch          */
+  int levels_src;        /* source tree depth (== levels for one point set)      */
+  int64_t n_sources;     /* charges (== n for one point set)                    */
+  int64_t n_targets;     /* evaluated points (== n for one point set)           */
+  int64_t n_src_leaves;  /* source leaves (== n_leaves for one point set)       */
 } fmm_stats;
 
 /* Evaluation stages in launch order, named after the stages of Sec. III.A:
@@ -119,6 +124,15 @@ enum {
   FMM_STAGE_L2P = 6,
   FMM_NUM_STAGES = 7
 };
+
+/* Measured arithmetic throughput of the current device, the denominators of
+ * the compute rooflines of the near field (FP32 FMA pipe and MUFU rsqrt) and
+ * of the FP64 path: out[0] FP32 FMA TFLOP/s (fma.rn.f32), out[1] packed
+ * FP32x2 FMA TFLOP/s (fma.rn.f32x2, 4 flops per lane), out[2] FP64 FMA
+ * TFLOP/s, out[3] rsqrt.approx.f32 Gop/s.  out: host, 4 doubles.  Runs a
+ * few short probe kernels on `stream` (tens of ms) and synchronises it; the
+ * paper has no counterpart (it is a measurement aid). */
+int fmm_device_peaks(double* out, void* stream);
 
 /* Thread-local description of the last failure on this thread. */
 const char* fmm_last_error(void);
@@ -143,6 +157,29 @@ int fmm_num_levels(int64_t n, int leaf_size, int splits);
  * FMM_ERR_OOM, FMM_ERR_CUDA.  On error *out is set to NULL. */
 int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void* stream,
                    fmm_tree** out);
+
+/* Separate source and target hierarchies (Sec. II.B, final part): the
+ * potential of charges at n_src source positions evaluated at n_trg other
+ * positions.  Two median-split trees are built with the same leaf_size,
+ * splits and theta (their depths may differ) and compared by the level march
+ * of Sec. II.B (ties as in fmm_params.flags; FMM_SAME_LEVEL is rejected
+ * because same-level lists need equal depths).  src_pos, trg_pos: DEVICE,
+ * 3 n_src / 3 n_trg doubles, x y z per point.  The resulting tree is used
+ * with fmm_eval_potential / fmm_eval_field / fmm_eval_potential_host: q has
+ * n_src entries (source order), u n_trg and field 3 n_trg (target order).  A
+ * target at exactly the position of a source does not see that charge (zero
+ * distances contribute nothing).  In fmm_tree_export the source boxes come
+ * first (ids 0 .. NB_s - 1; box b of source level l at (2^(s l) - 1)/(2^s - 1)
+ * + b), the target boxes follow (id NB_s + the same formula); perm maps
+ * source tree positions 0 .. n_src - 1 to source indices and target tree
+ * positions n_src .. to n_src + target index; level_avg_radius holds
+ * levels_src + 1 source averages, then levels + 1 target averages;
+ * near-field pairs are (target leaf, source leaf).  fmm_backward,
+ * fmm_tree_merge and fmm_eval_potential_static reject such trees (the
+ * transposed problem is a tree with the roles swapped).  Errors as for
+ * fmm_build_tree. */
+int fmm_build_tree2(const double* src_pos, int64_t n_src, const double* trg_pos,
+                    int64_t n_trg, const fmm_params* params, void* stream, fmm_tree** out);
 
 /* Releases a tree and its device memory (synchronises the device first).
  * NULL is accepted. */

@@ -32,31 +32,6 @@ __global__ void backward_combine_kernel(int64_t n, const double* __restrict__ q,
     for (int a = 0; a < 3; a++) out[3 * i + a] = -(g[i] * eq[3 * i + a] + q[i] * eg[3 * i + a]);
 }
 
-void free_tree(fmm_tree* t) {
-  if (!t) return;
-  cudaDeviceSynchronize();
-  void* ptrs[] = {t->perm,     t->box_start, t->box_count, t->center,   t->radius,   t->m2l_off,  t->m2l_src,
-                  t->m2l_trg,  t->m2l_order, t->p2p_off,   t->p2p_src,  t->p2p32,    t->leaf_order, t->pos_local,
-                  t->pos64,    t->inv_rho32, t->inv_rho64, t->geo32,    t->geo64,    t->m2m32,    t->m2m64,
-                  t->l2l32,    t->l2l64,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
-                  t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
-                  t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->down_ids};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  if (t->prof_ev) {
-    for (int i = 0; i < fmm_tree::kProfCalls * FMM_NUM_STAGES * 2; i++) cudaEventDestroy(t->prof_ev[i]);
-    delete[] t->prof_ev;
-  }
-  if (t->ev_fork) cudaEventDestroy(t->ev_fork);
-  if (t->ev_join) cudaEventDestroy(t->ev_join);
-  if (t->far_stream) cudaStreamDestroy(t->far_stream);
-  delete[] t->level_avg_host;
-  delete[] t->up_off_h;
-  delete[] t->down_off_h;
-  delete[] t->tree_point_off_h;
-  delete t;
-}
-
 void eval_any(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
   if (t->prm.precision == FMM_FP32C) eval_fp32(t, q, u, field, st);
   else eval_fp64(t, q, u, field, st);
@@ -76,6 +51,32 @@ int guarded(F&& f) {
 }
 
 }  // namespace
+
+void free_tree(fmm_tree* t) {
+  if (!t) return;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {t->perm,     t->box_start, t->box_count, t->center,   t->radius,   t->m2l_off,  t->m2l_src,
+                  t->m2l_trg,  t->m2l_order, t->p2p_off,   t->p2p_src,  t->p2p32,    t->leaf_order, t->pos_local,
+                  t->pos64,    t->inv_rho32, t->inv_rho64, t->geo32,    t->geo64,    t->m2m32,    t->m2m64,
+                  t->l2l32,    t->l2l64,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
+                  t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
+                  t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->down_ids,
+                  t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (t->prof_ev) {
+    for (int i = 0; i < fmm_tree::kProfCalls * FMM_NUM_STAGES * 2; i++) cudaEventDestroy(t->prof_ev[i]);
+    delete[] t->prof_ev;
+  }
+  if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+  if (t->ev_join) cudaEventDestroy(t->ev_join);
+  if (t->far_stream) cudaStreamDestroy(t->far_stream);
+  delete[] t->level_avg_host;
+  delete[] t->up_off_h;
+  delete[] t->down_off_h;
+  delete[] t->tree_point_off_h;
+  delete t;
+}
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -135,6 +136,37 @@ int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void*
   return FMM_OK;
 }
 
+int fmm_build_tree2(const double* src_pos, int64_t n_src, const double* trg_pos, int64_t n_trg,
+                    const fmm_params* params, void* stream, fmm_tree** out) {
+  if (out) *out = nullptr;
+  fmm_tree* t = nullptr;
+  int rc = guarded([&] {
+    require(out != nullptr, "out is NULL");
+    require(params != nullptr, "params is NULL");
+    require(src_pos != nullptr && trg_pos != nullptr, "positions are NULL");
+    const fmm_params& p = *params;
+    require(n_src >= 1 && n_trg >= 1 && n_src + n_trg < (int64_t)1 << 31, "n_src, n_trg >= 1, n_src + n_trg < 2^31");
+    require(p.p >= 1 && p.p <= FMM_MAX_P, "p must be in [1, FMM_MAX_P]");
+    require(p.splits >= 1 && p.splits <= 3, "splits must be 1, 2 or 3");
+    require(p.leaf_size >= (1 << p.splits) && p.leaf_size <= kMaxLeaf, "leaf_size must be in [2^splits, 256]");
+    require(p.theta > 0.0 && p.theta < 1.0, "theta must be in (0, 1)");
+    require(p.precision == FMM_FP64 || p.precision == FMM_FP32C, "precision must be FMM_FP64 or FMM_FP32C");
+    require((p.flags & ~FMM_TIE_TARGET) == 0, "flags must be 0 or FMM_TIE_TARGET for two hierarchies");
+    auto t0 = std::chrono::steady_clock::now();
+    ensure_tables();
+    t = new fmm_tree();
+    t->prm = p;
+    build_tree2(t, src_pos, n_src, trg_pos, n_trg, (cudaStream_t)stream);
+    t->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  });
+  if (rc != FMM_OK) {
+    free_tree(t);
+    return rc;
+  }
+  *out = t;
+  return FMM_OK;
+}
+
 void fmm_tree_free(fmm_tree* tree) { free_tree(tree); }
 
 int fmm_tree_merge(fmm_tree* const* trees, int n_trees, void* stream, fmm_tree** out) {
@@ -143,6 +175,8 @@ int fmm_tree_merge(fmm_tree* const* trees, int n_trees, void* stream, fmm_tree**
   int rc = guarded([&] {
     require(out != nullptr && trees != nullptr, "NULL argument");
     require(n_trees >= 1, "n_trees must be >= 1");
+    for (int k = 0; k < n_trees; k++)
+      require(trees[k] == nullptr || !trees[k]->two_trees, "trees with separate source and target sets cannot be merged");
     auto t0 = std::chrono::steady_clock::now();
     m = new fmm_tree();
     merge_trees(trees, n_trees, (cudaStream_t)stream, m);
@@ -196,6 +230,10 @@ int fmm_tree_stats(const fmm_tree* t, fmm_stats* s) {
     s->build_ms = t->build_ms;
     s->kernel_launches = t->launches;
     s->n_trees = t->n_trees;
+    s->n_sources = t->n_charges;
+    s->n_targets = t->two_trees ? t->n - t->n_charges : t->n;
+    s->levels_src = t->two_trees ? t->L_src : t->L;
+    s->n_src_leaves = t->n_src_leaves;
   });
 }
 
@@ -265,7 +303,9 @@ int fmm_tree_export(const fmm_tree* t, int32_t* perm, int64_t* box_start, int64_
     }
     cp(center, t->center, sizeof(double) * 3 * t->n_boxes);
     cp(radius, t->radius, sizeof(double) * t->n_boxes);
-    if (level_avg_radius) std::memcpy(level_avg_radius, t->level_avg_host, sizeof(double) * (t->L + 1));
+    if (level_avg_radius)
+      std::memcpy(level_avg_radius, t->level_avg_host,
+                  sizeof(double) * (t->two_trees ? t->L_src + t->L + 2 : t->L + 1));
     cp(m2l_trg, t->m2l_trg, sizeof(int32_t) * t->n_m2l);
     cp(m2l_src, t->m2l_src, sizeof(int32_t) * t->n_m2l);
     cp(p2p_src, t->p2p_src, sizeof(int32_t) * t->n_p2p);
@@ -296,9 +336,10 @@ int fmm_eval_potential_host(const fmm_tree* t, const double* q_host, double* u_h
   return guarded([&] {
     require(t != nullptr && q_host != nullptr && u_host != nullptr, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    FMM_CUDA_TRY(cudaMemcpyAsync(t->q_stage, q_host, sizeof(double) * t->n, cudaMemcpyHostToDevice, st));
+    const int64_t n_out = t->two_trees ? t->n - t->n_charges : t->n;
+    FMM_CUDA_TRY(cudaMemcpyAsync(t->q_stage, q_host, sizeof(double) * t->n_charges, cudaMemcpyHostToDevice, st));
     eval_any(t, t->q_stage, t->u_stage, nullptr, st);
-    FMM_CUDA_TRY(cudaMemcpyAsync(u_host, t->u_stage, sizeof(double) * t->n, cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(u_host, t->u_stage, sizeof(double) * n_out, cudaMemcpyDeviceToHost, st));
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
   });
 }
@@ -307,6 +348,9 @@ int fmm_backward(const fmm_tree* t, const double* q, const double* grad_u, doubl
                  void* stream) {
   return guarded([&] {
     require(t != nullptr && q != nullptr && grad_u != nullptr, "NULL argument");
+    require(!t->two_trees,
+            "fmm_backward needs one point set; for separate source and target trees evaluate the "
+            "transposed problem (sources and targets swapped) instead");
     cudaStream_t st = (cudaStream_t)stream;
     if (grad_pos) {
       eval_any(t, q, nullptr, t->f_stage, st);          // E of the charges

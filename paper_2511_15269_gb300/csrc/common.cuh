@@ -112,6 +112,7 @@ struct fmm_tree {
   int64_t* p2p_off = nullptr;    // n_leaves + 1, CSR by target leaf
   int32_t* p2p_src = nullptr;    // n_p2p
   fmm::P2PEntry* p2p32 = nullptr;  // n_p2p
+  float* p2p_thr = nullptr;        // n_p2p: FP32 coincidence threshold on r^2
   int32_t* leaf_order = nullptr;   // n_leaves: target leaves, most work first
   int32_t* leaf_box = nullptr;     // n_leaves: global box id of each leaf
   int32_t* box_parent = nullptr;   // n_boxes: parent box id (-1 for a root)
@@ -124,6 +125,19 @@ struct fmm_tree {
   int32_t* down_ids = nullptr;
   int n_trees = 1;                 // > 1 for a merged batch of trees
   int64_t* tree_point_off_h = nullptr;  // n_trees + 1 (merged batches)
+  // Roles of points and leaves.  One point set: every point carries a charge
+  // and is evaluated, every leaf is both a source and a target.  Separate
+  // source and target hierarchies (two_trees): points 0 .. n_charges - 1 are
+  // the charges, the rest the targets (output index perm[i] - out_base);
+  // leaf_box / n_leaves are the target leaves, src_leaf_box / n_src_leaves
+  // the source leaves; level_avg_host holds the source tree's L_src + 1
+  // averages, then the target tree's L + 1.
+  int two_trees = 0;
+  int L_src = 0;
+  int64_t n_charges = 0;
+  int64_t out_base = 0;
+  int64_t n_src_leaves = 0;
+  int32_t* src_leaf_box = nullptr;  // == leaf_box unless two_trees
 
   // per-point and per-box constants
   float4* pos_local = nullptr;   // n: tree order, x - c_leaf (FP32), w = 0
@@ -184,6 +198,10 @@ inline void stage_event(const fmm_tree* t, int s, bool end, cudaStream_t st) {
 
 // tree_build.cu
 void build_tree(fmm_tree* t, const double* pos, cudaStream_t st);
+// Separate source and target hierarchies (t->prm set on entry).
+void build_tree2(fmm_tree* t, const double* src, int64_t n_src, const double* trg, int64_t n_trg, cudaStream_t st);
+// api.cu: releases every device array, stream and event of a tree
+void free_tree(fmm_tree* t);
 // merge.cu: a batch of trees as one tree-shaped object
 void merge_trees(fmm_tree* const* in, int n, cudaStream_t st, fmm_tree* out);
 

@@ -70,13 +70,14 @@ __device__ __forceinline__ void load_coef(const real* src, real (&v)[ncoef(P)]) 
 }
 
 // ---- E0: sort charges into tree order ----------------------------------------
-__global__ void gather_kernel(int64_t n, const int32_t* __restrict__ perm,
+// Points at or after n_charges (targets of a separate target tree) get q = 0.
+__global__ void gather_kernel(int64_t n, int64_t n_charges, const int32_t* __restrict__ perm,
                               const double* __restrict__ q, const vec4* __restrict__ pos,
                               vec4* __restrict__ src, DupRec* __restrict__ dup) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     vec4 p = pos[i];
-    p.w = (real)q[perm[i]];
+    p.w = i < n_charges ? (real)q[perm[i]] : real(0);
     src[i] = p;
     if (dup) {
       const float x = (float)p.x, y = (float)p.y, z = (float)p.z, w = (float)p.w;
@@ -371,7 +372,7 @@ __device__ __forceinline__ float rsqrt_mufu(float x) {
 template <bool MASK, bool FIELD, int NP>
 __device__ __forceinline__ void p2p_tile_f32(const DupRec* sb, int scount, const f2 (&tx)[NP], const f2 (&ty)[NP],
                                              const f2 (&tz)[NP], f2 (&pu)[NP], f2 (&fx)[NP], f2 (&fy)[NP],
-                                             f2 (&fz)[NP]) {
+                                             f2 (&fz)[NP], float thr) {
   const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
 #pragma unroll 4
   for (int j = 0; j < scount; j++) {
@@ -385,8 +386,8 @@ __device__ __forceinline__ void p2p_tile_f32(const DupRec* sb, int scount, const
       f2unpack(r2, r0, r1);
       float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
       if (MASK) {
-        i0 = (r0 > 0.f) ? i0 : 0.f;
-        i1 = (r1 > 0.f) ? i1 : 0.f;
+        i0 = (r0 > thr) ? i0 : 0.f;
+        i1 = (r1 > thr) ? i1 : 0.f;
       }
       const f2 ri = f2pack(i0, i1);
       pu[k] = f2fma(b.y, ri, pu[k]);
@@ -406,7 +407,7 @@ __device__ __forceinline__ void p2p_tile_f32(const DupRec* sb, int scount, const
 template <bool MASK, bool FIELD, int NPH>
 __device__ __forceinline__ void p2p_pair_f32(const ulonglong2 a, const ulonglong2 b, const f2 (&tx)[NPH],
                                              const f2 (&ty)[NPH], const f2 (&tz)[NPH], f2 (&pu)[NPH],
-                                             f2 (&fx)[NPH], f2 (&fy)[NPH], f2 (&fz)[NPH]) {
+                                             f2 (&fx)[NPH], f2 (&fy)[NPH], f2 (&fz)[NPH], float thr) {
 #pragma unroll
   for (int k = 0; k < NPH; k++) {
     const f2 dx = f2sub(tx[k], a.x), dy = f2sub(ty[k], a.y), dz = f2sub(tz[k], b.x);
@@ -415,8 +416,8 @@ __device__ __forceinline__ void p2p_pair_f32(const ulonglong2 a, const ulonglong
     f2unpack(r2, r0, r1);
     float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
     if (MASK) {
-      i0 = (r0 > 0.f) ? i0 : 0.f;
-      i1 = (r1 > 0.f) ? i1 : 0.f;
+      i0 = (r0 > thr) ? i0 : 0.f;
+      i1 = (r1 > thr) ? i1 : 0.f;
     }
     const f2 ri = f2pack(i0, i1);
     pu[k] = f2fma(b.y, ri, pu[k]);
@@ -436,13 +437,13 @@ __device__ __forceinline__ void p2p_pair_f32(const ulonglong2 a, const ulonglong
 template <bool MASK, bool FIELD, int NPH>
 __device__ __forceinline__ void p2p_tile_f32h(const DupRec* sb, int scount, int half, const f2 (&tx)[NPH],
                                               const f2 (&ty)[NPH], const f2 (&tz)[NPH], f2 (&pu)[NPH],
-                                              f2 (&fx)[NPH], f2 (&fy)[NPH], f2 (&fz)[NPH]) {
+                                              f2 (&fx)[NPH], f2 (&fy)[NPH], f2 (&fz)[NPH], float thr) {
   const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
   if constexpr (FIELD || NPH > 2) {
     // one accumulator set (register budget of the field and large tiles)
 #pragma unroll 2
     for (int j = half; j < scount; j += 2)
-      p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz);
+      p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz, thr);
     return;
   }
   f2 pu2[NPH], fx2[NPH], fy2[NPH], fz2[NPH];
@@ -453,10 +454,10 @@ __device__ __forceinline__ void p2p_tile_f32h(const DupRec* sb, int scount, int 
   for (; j + 2 < scount; j += 4) {
     const ulonglong2 a0 = s2[2 * j], b0 = s2[2 * j + 1];
     const ulonglong2 a1 = s2[2 * j + 4], b1 = s2[2 * j + 5];
-    p2p_pair_f32<MASK, FIELD, NPH>(a0, b0, tx, ty, tz, pu, fx, fy, fz);
-    p2p_pair_f32<MASK, FIELD, NPH>(a1, b1, tx, ty, tz, pu2, fx2, fy2, fz2);
+    p2p_pair_f32<MASK, FIELD, NPH>(a0, b0, tx, ty, tz, pu, fx, fy, fz, thr);
+    p2p_pair_f32<MASK, FIELD, NPH>(a1, b1, tx, ty, tz, pu2, fx2, fy2, fz2, thr);
   }
-  if (j < scount) p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz);
+  if (j < scount) p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz, thr);
 #pragma unroll
   for (int k = 0; k < NPH; k++) {
     pu[k] = f2add(pu[k], pu2[k]);
@@ -470,10 +471,13 @@ __device__ __forceinline__ void p2p_tile_f32h(const DupRec* sb, int scount, int 
 
 struct P2PArgs {
   int64_t n_leaves;
-  const int32_t* leaf_box;  // global box id of each leaf
+  const int32_t* leaf_box;      // global box id of each target leaf
+  const int32_t* src_leaf_box;  // global box id of each source leaf
+  int self_pairs;               // target leaf l and source leaf l are the same box
   const int32_t* order;
   const int64_t* off;
   const P2PEntry* ent32;
+  const float* thr;  // per entry: squared FP32 distance at or below which points coincide
   const int32_t* ent_src;
   const int64_t* box_start;
   const int32_t* box_count;
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
       return kF32 ? (a.ent32[e].src & 0x7fffffff) : a.ent_src[e];
     };
     auto issue = [&](int64_t e, int buf) {
-      const int64_t gs = a.leaf_box[src_leaf(e)];
+      const int64_t gs = a.src_leaf_box[src_leaf(e)];
       if (lane == 0) {
         fence_proxy_async();
         tma_load_1d(sbuf[warp][buf], tile + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(rec)),
@@ -559,10 +563,10 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
       }
       phase ^= 1u << buf;
       const int ls = src_leaf(e);
-      const int scount = a.box_count[a.leaf_box[ls]];
+      const int scount = a.box_count[a.src_leaf_box[ls]];
       if constexpr (kF32) {
         const P2PEntry en = a.ent32[e];
-        const bool mask = (en.src < 0) || (ls == (int)leaf);
+        const bool mask = (en.src < 0) || (a.self_pairs && ls == (int)leaf);
         const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
         f2 tx[NP], ty[NP], tz[NP], pu[NP], px[NP], py[NP], pz[NP];
 #pragma unroll
@@ -573,8 +577,9 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
           tz[k] = f2add(f2pack(tz0[2 * k], tz0[k1]), ddz);
           pu[k] = px[k] = py[k] = pz[k] = 0ull;
         }
-        if (mask) p2p_tile_f32<true, FIELD, NP>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz);
-        else p2p_tile_f32<false, FIELD, NP>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz);
+        const float thr = mask ? a.thr[e] : 0.f;
+        if (mask) p2p_tile_f32<true, FIELD, NP>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz, thr);
+        else p2p_tile_f32<false, FIELD, NP>(sbuf[warp][buf], scount, tx, ty, tz, pu, px, py, pz, thr);
 #pragma unroll
         for (int k = 0; k < NP; k++) {
           float u0, u1, x0, x1, y0, y1, z0, z1;
@@ -681,7 +686,7 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_
   for (int k = 0; k < NT; k++) hi[k] = lo[k] = fx[k] = fy[k] = fz[k] = 0.f;
   const int64_t eb = a.off[leaf], ee = a.off[leaf + 1];
   auto issue = [&](int64_t e, int buf) {
-    const int64_t gs = a.leaf_box[a.ent32[e].src & 0x7fffffff];
+    const int64_t gs = a.src_leaf_box[a.ent32[e].src & 0x7fffffff];
     if (lane == 0) {
       fence_proxy_async();
       tma_load_1d(sbuf[warp][buf], tile + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(DupRec)), &bar[buf]);
@@ -702,8 +707,8 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_
     phase ^= 1u << buf;
     const P2PEntry en = a.ent32[e];
     const int ls = en.src & 0x7fffffff;
-    const int scount = a.box_count[a.leaf_box[ls]];
-    const bool mask = (en.src < 0) || (ls == (int)leaf);
+    const int scount = a.box_count[a.src_leaf_box[ls]];
+    const bool mask = (en.src < 0) || (a.self_pairs && ls == (int)leaf);
     const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
     f2 tx[NPH], ty[NPH], tz[NPH], pu[NPH], px[NPH], py[NPH], pz[NPH];
 #pragma unroll
@@ -713,8 +718,9 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_
       tz[k] = f2add(f2pack(tz0[2 * k], tz0[2 * k + 1]), ddz);
       pu[k] = px[k] = py[k] = pz[k] = 0ull;
     }
-    if (mask) p2p_tile_f32h<true, FIELD, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz);
-    else p2p_tile_f32h<false, FIELD, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz);
+    const float thr = mask ? a.thr[e] : 0.f;
+    if (mask) p2p_tile_f32h<true, FIELD, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz, thr);
+    else p2p_tile_f32h<false, FIELD, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz, thr);
 #pragma unroll
     for (int k = 0; k < NPH; k++) {
       float u0, u1, x0, x1, y0, y1, z0, z1;
@@ -771,7 +777,7 @@ __global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, const int32_
                                                   const int64_t* __restrict__ box_start,
                                                   const int32_t* __restrict__ box_count,
                                                   const double* __restrict__ center,
-                                                  const int32_t* __restrict__ perm,
+                                                  const int32_t* __restrict__ perm, int64_t out_base,
                                                   const vec4* __restrict__ src,
                                                   const real* __restrict__ inv_rho,
                                                   const real* __restrict__ Lam,
@@ -853,7 +859,7 @@ __global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, const int32_
       });
       const double far = (double)u0 + 2.0 * (double)um;
       double nearv = kF32 ? (double)near_u[2 * pidx] + (double)near_u[2 * pidx + 1] : (double)near_u[pidx];
-      const int64_t o = perm[pidx];
+      const int64_t o = perm[pidx] - out_base;
       if (u_out) u_out[o] = -kInv4Pi * (far + nearv);
       if (FIELD) {
         const double irr = (double)ir;
@@ -886,8 +892,8 @@ template <int P>
 void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   const int nch = 1 << t->s;
   stage_event(t, FMM_STAGE_P2M, false, st);
-  p2m_kernel<P><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-      t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->center, pp.src, pp.inv_rho, pp.M);
+  p2m_kernel<P><<<grid_for(t->n_src_leaves * 32, 128), 128, 0, st>>>(
+      t->n_src_leaves, t->src_leaf_box, t->box_start, t->box_count, t->center, pp.src, pp.inv_rho, pp.M);
   FMM_LAUNCH_CHECK();
   t->launches += 1 + t->n_up;
   stage_event(t, FMM_STAGE_P2M, true, st);
@@ -947,11 +953,11 @@ void run_l2p(const fmm_tree* t, const Ptrs& pp, const real* near_u, const real* 
   t->launches += 1;
   if (field)
     l2p_kernel<P, true><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
+        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->center, t->perm, t->out_base, pp.src, pp.inv_rho,
         pp.Lam, near_u, near_f, u, field);
   else
     l2p_kernel<P, false><<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->center, t->perm, pp.src, pp.inv_rho,
+        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->center, t->perm, t->out_base, pp.src, pp.inv_rho,
         pp.Lam, near_u, near_f, u, field);
   FMM_LAUNCH_CHECK();
 }
@@ -962,9 +968,12 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
   P2PArgs a;
   a.n_leaves = t->n_leaves;
   a.leaf_box = t->leaf_box;
+  a.src_leaf_box = t->src_leaf_box;
+  a.self_pairs = t->two_trees ? 0 : 1;
   a.order = t->leaf_order;
   a.off = t->p2p_off;
   a.ent32 = t->p2p32;
+  a.thr = t->p2p_thr;
   a.ent_src = t->p2p_src;
   a.box_start = t->box_start;
   a.box_count = t->box_count;
@@ -1041,7 +1050,7 @@ void dispatch_p(int p, F&& f) {
 void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
   Ptrs pp = ptrs(t);
   stage_event(t, FMM_STAGE_SORT, false, st);
-  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->perm, q, pp.pos, pp.src,
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, q, pp.pos, pp.src,
                                                      kF32 ? t->src_dup : nullptr);
   FMM_LAUNCH_CHECK();
   t->launches += 1;

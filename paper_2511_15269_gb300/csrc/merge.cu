@@ -56,6 +56,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   for (int k = 0; k < nt; k++) {
     require(in[k] != nullptr, "NULL tree");
     require(in[k]->n_trees == 1, "trees to merge must not be merged batches");
+    require(!in[k]->two_trees, "trees with separate source and target sets cannot be merged");
     require(in[k]->prm.p == t0.prm.p && in[k]->prm.splits == t0.prm.splits, "trees must share p and splits");
   }
   const int p = t0.prm.p, s = t0.prm.splits;
@@ -105,6 +106,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   m->p2p_off = dev_alloc<int64_t>(m, NL + 1);
   m->p2p_src = dev_alloc<int32_t>(m, NP);
   m->p2p32 = dev_alloc<P2PEntry>(m, NP);
+  m->p2p_thr = dev_alloc<float>(m, NP);
   m->leaf_box = dev_alloc<int32_t>(m, NL);
   m->box_parent = dev_alloc<int32_t>(m, NB);
   m->pos_local = dev_alloc<float4>(m, N);
@@ -131,6 +133,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
     add_i64_kernel<<<grid_for(t.n_leaves, 256), 256, 0, st>>>(m->p2p_off + lo[k], t.p2p_off, t.n_leaves, eo[k]);
     add_i32_kernel<<<grid_for(t.n_p2p, 256), 256, 0, st>>>(m->p2p_src + eo[k], t.p2p_src, t.n_p2p, (int32_t)lo[k], 0);
     shift_entries_kernel<<<grid_for(t.n_p2p, 256), 256, 0, st>>>(m->p2p32 + eo[k], t.p2p32, t.n_p2p, (int32_t)lo[k]);
+    copy_d2d(m->p2p_thr + eo[k], t.p2p_thr, t.n_p2p, st);
     add_i32_kernel<<<grid_for(t.n_leaves, 256), 256, 0, st>>>(m->leaf_box + lo[k], t.leaf_box, t.n_leaves,
                                                               (int32_t)bo[k], 0);
     add_i32_kernel<<<grid_for(t.n_boxes, 256), 256, 0, st>>>(m->box_parent + bo[k], t.box_parent, t.n_boxes,
@@ -231,6 +234,10 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   FMM_CUDA_TRY(cudaStreamCreateWithPriority(&m->far_stream, cudaStreamNonBlocking, hi_prio));
   FMM_CUDA_TRY(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
   FMM_CUDA_TRY(cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming));
+  m->n_charges = N;
+  m->out_base = 0;
+  m->n_src_leaves = NL;
+  m->src_leaf_box = m->leaf_box;
   m->counters = dev_alloc<int>(m, 8);
   m->status = dev_alloc<int>(m, 1);
   FMM_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));

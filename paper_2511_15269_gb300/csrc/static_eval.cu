@@ -59,6 +59,7 @@ extern "C" int fmm_eval_potential_static(const fmm_tree* tree, const double* q, 
   using namespace fmm;
   try {
     require(tree != nullptr && q != nullptr && u != nullptr, "NULL argument");
+    require(!tree->two_trees, "fmm_eval_potential_static takes trees of one point set");
     if (tree->n > kMaxPts || tree->n_boxes > kMaxBoxes) {
       set_error("fmm_eval_potential_static: tree with %lld points and %lld boxes exceeds the static scratch "
                 "capacity of %lld points and %lld boxes",

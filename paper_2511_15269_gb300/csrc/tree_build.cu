@@ -802,27 +802,42 @@ __global__ void duplicate_kernel(const double* __restrict__ X, int64_t n, int* _
   }
 }
 
-// near-field entries: source leaf, FP32 centre offset, and the flag that
-// zero distances are possible (coincident points exist and the leaves'
-// bounding boxes touch)
+// near-field entries: source leaf, FP32 centre offset, the flag that zero
+// distances are possible (coincident points may exist and the leaves'
+// bounding boxes touch; without boxes (lo == NULL) the bounding spheres of
+// radius `radius` are tested instead) and the FP32 coincidence threshold
 __global__ void p2p_entry_kernel(const int32_t* __restrict__ pt, const int32_t* __restrict__ ps, int64_t np,
-                                 int64_t leaf_off, const double* __restrict__ center,
-                                 const double* __restrict__ lo, const double* __restrict__ hi,
-                                 const int32_t* __restrict__ bc, int has_dup, P2PEntry* __restrict__ ent,
+                                 int64_t trg_base, int64_t src_base, const double* __restrict__ center,
+                                 const double* __restrict__ radius, const double* __restrict__ lo,
+                                 const double* __restrict__ hi, const int32_t* __restrict__ bc, int has_dup,
+                                 P2PEntry* __restrict__ ent, float* __restrict__ thr,
                                  unsigned long long* __restrict__ pairs) {
   for (int64_t e0 = (blockIdx.x * (int64_t)blockDim.x) & ~31ll; e0 < np; e0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = e0 + (threadIdx.x & 31) + (threadIdx.x & ~31);
     unsigned long long w = 0;
     if (e < np) {
-      const int64_t gt = leaf_off + pt[e], gs = leaf_off + ps[e];
+      const int64_t gt = trg_base + pt[e], gs = src_base + ps[e];
       bool touch = has_dup != 0;
-      for (int a = 0; a < 3; a++) touch = touch && lo[3 * gt + a] <= hi[3 * gs + a] && lo[3 * gs + a] <= hi[3 * gt + a];
+      if (lo) {
+        for (int a = 0; a < 3; a++)
+          touch = touch && lo[3 * gt + a] <= hi[3 * gs + a] && lo[3 * gs + a] <= hi[3 * gt + a];
+      } else {
+        const double dx = center[3 * gt] - center[3 * gs], dy = center[3 * gt + 1] - center[3 * gs + 1],
+                     dz = center[3 * gt + 2] - center[3 * gs + 2];
+        const double rr = radius[gt] + radius[gs];
+        touch = touch && (dx * dx + dy * dy + dz * dz) <= 1.0000001 * rr * rr;
+      }
       P2PEntry en;
       en.src = ps[e] | (touch ? (int)0x80000000 : 0);
       en.dx = (float)(center[3 * gt] - center[3 * gs]);
       en.dy = (float)(center[3 * gt + 1] - center[3 * gs + 1]);
       en.dz = (float)(center[3 * gt + 2] - center[3 * gs + 2]);
       ent[e] = en;
+      // FP32 leaf-local coordinates of coincident points differ by at most a
+      // few units in the last place of the leaves' extent: squared distances
+      // below (1e-5 max radius)^2 are taken as zero distances
+      const double rm = 1e-5 * fmax(radius[gt], radius[gs]);
+      thr[e] = (float)(rm * rm);
       w = (unsigned long long)bc[gt] * (unsigned long long)bc[gs];
     }
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
@@ -864,9 +879,10 @@ std::vector<T> to_host(const T* d, int64_t n, cudaStream_t st) {
   return h;
 }
 
-}  // namespace
-
-void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
+// Hierarchy of one point set (Sec. II.A): tree order, box ranges, geometry,
+// index lists, level averages, point records and M2M/L2L edge coefficients.
+// The leaf bounding boxes (3 n_boxes lo and hi) are handed to the caller.
+void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** blo_out, double** bhi_out) {
   const int64_t n = t->n;
   const int s = t->prm.splits;
   const int nch = 1 << s;
@@ -1058,12 +1074,48 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     cudaFree(buf0), cudaFree(buf1);
   }
 
-  // ---- level march ----
-  struct Step {
-    int32_t *t, *s;
-    int64_t n;
-  };
-  std::vector<Step> steps;
+  // ---- point records and M2M/L2L edge coefficients ----
+  const int p = t->prm.p;
+  t->pos_local = dev_alloc<float4>(t, n);
+  t->pos64 = dev_alloc<dvec4>(t, n);
+  point_records_kernel<<<grid_for(NL * 32, 256, 1 << 30), 256, 0, st>>>(Xa, n, t->box_start, t->box_count, leaf_off,
+                                                                        NL, t->center, t->pos_local, t->pos64);
+  FMM_LAUNCH_CHECK();
+  t->m2m64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
+  t->m2m32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
+  t->l2l64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
+  t->l2l32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
+  edge_geo_kernel<<<grid_for(NB, 128, 1 << 30), 128, 0, st>>>(NB, s, t->center, t->radius, p, t->m2m64, t->m2m32,
+                                                              t->l2l64, t->l2l32);
+  FMM_LAUNCH_CHECK();
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  t->device_bytes -= sizeof(double) * 6 * NB;  // bounding boxes leave with the caller
+  *blo_out = blo;
+  *bhi_out = bhi;
+  cudaFree(starts);
+  cudaFree(Xa), cudaFree(Xb), cudaFree(Ia), cudaFree(Ib), cudaFree(flag);
+}
+
+// One side of the list construction: the combined id of the side's root and
+// its depth and level averages.
+struct Side {
+  int64_t base;
+  int L;
+  const double* avg;
+};
+struct Step {
+  int32_t *t, *s;
+  int64_t n;
+};
+
+// Interaction lists between the boxes of a source side and a target side
+// (Sec. II.B): level march, or same-level lists with FMM_SAME_LEVEL.  M2L
+// pairs (combined ids) per step; the pairs left at both leaf levels are the
+// near field (target leaf, source leaf), sorted by (target, source).
+void march(const fmm_tree* t, Side S, Side T, cudaStream_t st, std::vector<Step>& steps, int32_t** p2p_t_out,
+           int32_t** p2p_s_out, int64_t* np_out) {
+  const int s = t->prm.splits;
+  const int nch = 1 << s;
   int32_t* ct = dev_alloc<int32_t>(nullptr, 1);
   int32_t* cs = dev_alloc<int32_t>(nullptr, 1);
   FMM_CUDA_TRY(cudaMemsetAsync(ct, 0, sizeof(int32_t), st));
@@ -1079,16 +1131,16 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     int64_t* fkeep = scratch_alloc<int64_t>(nc);
     int64_t* pws = scratch_alloc<int64_t>(nc);
     int64_t* pkeep = scratch_alloc<int64_t>(nc);
-    ws_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, level_offset(lt, s), level_offset(ls, s), t->center,
-                                                 t->radius, t->prm.theta, fws, fkeep);
+    const int64_t offt = T.base + level_offset(lt, s), offs = S.base + level_offset(ls, s);
+    ws_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, t->center, t->radius, t->prm.theta, fws,
+                                                 fkeep);
     FMM_LAUNCH_CHECK();
     const int64_t nws = exclusive_scan(fws, pws, nc, st);
     const int64_t nkeep = exclusive_scan(fkeep, pkeep, nc, st);
     Step stp{dev_alloc<int32_t>(nullptr, nws), dev_alloc<int32_t>(nullptr, nws), nws};
     int32_t* kt = dev_alloc<int32_t>(nullptr, nkeep);
     int32_t* ks = dev_alloc<int32_t>(nullptr, nkeep);
-    emit_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, level_offset(lt, s), level_offset(ls, s), fws, pws,
-                                                   pkeep, stp.t, stp.s, kt, ks);
+    emit_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, fws, pws, pkeep, stp.t, stp.s, kt, ks);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(fws), cudaFree(fkeep), cudaFree(pws), cudaFree(pkeep), cudaFree(ct), cudaFree(cs);
@@ -1099,7 +1151,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
       ct = cs = nullptr;
       break;
     }
-    const bool can_s = ls < L, can_t = lt < L;
+    const bool can_s = ls < S.L, can_t = lt < T.L;
     if (!can_s && !can_t) {
       p2p_t = kt;
       p2p_s = ks;
@@ -1111,7 +1163,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     if (same_level) {
       adv = 2;
     } else if (can_s && can_t) {
-      const double as = t->level_avg_host[ls], at = t->level_avg_host[lt];
+      const double as = S.avg[ls], at = T.avg[lt];
       adv = (as > at) || (as == at && !tie_target) ? 1 : 0;
     } else {
       adv = can_s ? 1 : 0;
@@ -1126,6 +1178,21 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     if (adv != 0) ls++;
     if (adv != 1) lt++;
   }
+  *p2p_t_out = p2p_t;
+  *p2p_s_out = p2p_s;
+  *np_out = np;
+}
+
+// Lists into their device form, per-interaction coefficients, near-field
+// entries, work orders and the evaluation workspace.  Target leaves are the
+// boxes trg_leaf_base .. + n_leaves - 1, source leaves src_leaf_base .. +
+// n_src_leaves - 1 (combined ids).  blo/bhi: leaf bounding boxes for the
+// coincident-point test, or NULL for the bounding-sphere test.
+void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t* p2p_s, int64_t np,
+                 int64_t trg_leaf_base, int64_t src_leaf_base, const double* blo, const double* bhi, int has_dup,
+                 cudaStream_t st) {
+  const int64_t NB = t->n_boxes, NL = t->n_leaves, NLS = t->n_src_leaves, n = t->n;
+  const int p = t->prm.p;
 
   // ---- M2L lists as CSR by target, sources ascending ----
   int64_t nm = 0;
@@ -1153,6 +1220,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(cnt), cudaFree(fill);
     for (auto& x : steps) cudaFree(x.t), cudaFree(x.s);
+    steps.clear();
   }
 
   // ---- near-field lists as CSR by target leaf ----
@@ -1160,6 +1228,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   t->p2p_off = dev_alloc<int64_t>(t, NL + 1);
   t->p2p_src = dev_alloc<int32_t>(t, np);
   t->p2p32 = dev_alloc<P2PEntry>(t, np);
+  t->p2p_thr = dev_alloc<float>(t, np);
   int32_t* p2p_trg = dev_alloc<int32_t>(nullptr, np);
   {
     int64_t* cnt = scratch_alloc<int64_t>(NL + 1);
@@ -1171,17 +1240,12 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
       FMM_CUDA_TRY(cudaMemcpyAsync(p2p_trg, p2p_t, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st));
     }
     exclusive_scan(cnt, t->p2p_off, NL + 1, st);
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(cnt);
     if (p2p_t) cudaFree(p2p_t), cudaFree(p2p_s);
   }
 
-  // ---- point records, rotation coefficients, near-field entries ----
-  const int p = t->prm.p;
-  t->pos_local = dev_alloc<float4>(t, n);
-  t->pos64 = dev_alloc<dvec4>(t, n);
-  point_records_kernel<<<grid_for(NL * 32, 256, 1 << 30), 256, 0, st>>>(Xa, n, t->box_start, t->box_count, leaf_off,
-                                                                        NL, t->center, t->pos_local, t->pos64);
-  FMM_LAUNCH_CHECK();
+  // ---- rotation coefficients and near-field entries ----
   t->geo64 = dev_alloc<double>(t, (size_t)m2l_fields(p) * std::max<int64_t>(nm, 1));
   t->geo32 = dev_alloc<float>(t, (size_t)m2l_fields(p) * std::max<int64_t>(nm, 1));
   if (nm > 0) {
@@ -1189,19 +1253,13 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
                                                       t->geo32);
     FMM_LAUNCH_CHECK();
   }
-  t->m2m64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
-  t->m2m32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
-  t->l2l64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
-  t->l2l32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
-  edge_geo_kernel<<<grid_for(NB, 128, 1 << 30), 128, 0, st>>>(NB, s, t->center, t->radius, p, t->m2m64, t->m2m32,
-                                                              t->l2l64, t->l2l32);
-  FMM_LAUNCH_CHECK();
   {
     unsigned long long* pairs = scratch_alloc<unsigned long long>(1);
     FMM_CUDA_TRY(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), st));
     if (np > 0) {
-      p2p_entry_kernel<<<grid_for(np, 256), 256, 0, st>>>(p2p_trg, t->p2p_src, np, leaf_off, t->center, blo, bhi,
-                                                          t->box_count, has_dup, t->p2p32, pairs);
+      p2p_entry_kernel<<<grid_for(np, 256), 256, 0, st>>>(p2p_trg, t->p2p_src, np, trg_leaf_base, src_leaf_base,
+                                                          t->center, t->radius, blo, bhi, t->box_count, has_dup,
+                                                          t->p2p32, t->p2p_thr, pairs);
       FMM_LAUNCH_CHECK();
     }
     unsigned long long hp = 0;
@@ -1210,6 +1268,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     t->n_p2p_pairs = (int64_t)hp;
     cudaFree(pairs);
   }
+  cudaFree(p2p_trg);
 
   // ---- work orders: longest M2L lists and heaviest near fields first ----
   {
@@ -1222,10 +1281,10 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     FMM_CUDA_TRY(cudaMemcpyAsync(t->m2l_order, ord.data(), sizeof(int32_t) * NB, cudaMemcpyHostToDevice, st));
     std::vector<int64_t> poff = to_host(t->p2p_off, NL + 1, st);
     std::vector<int32_t> psrc = to_host(t->p2p_src, np, st);
-    std::vector<int32_t> bcnt = to_host(t->box_count + leaf_off, NL, st);
+    std::vector<int32_t> scnt = to_host(t->box_count + src_leaf_base, NLS, st);
     std::vector<int64_t> work(NL, 0);
     for (int64_t l = 0; l < NL; l++)
-      for (int64_t e = poff[l]; e < poff[l + 1]; e++) work[l] += bcnt[psrc[e]];
+      for (int64_t e = poff[l]; e < poff[l + 1]; e++) work[l] += scnt[psrc[e]];
     std::vector<int32_t> lord(NL);
     for (int64_t l = 0; l < NL; l++) lord[l] = (int32_t)l;
     std::stable_sort(lord.begin(), lord.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
@@ -1264,12 +1323,219 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   t->status = dev_alloc<int>(t, 1);
   FMM_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), st));
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
+}
 
+template <class T>
+void copy_d2d(T* dst, const T* src, int64_t n, cudaStream_t st) {
+  if (n > 0) FMM_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+}
+
+// field-major rows of `width` entries into rows of `total` entries at `col`
+template <class T>
+void copy_rows(T* dst, int64_t total, int64_t col, const T* src, int64_t width, int rows, cudaStream_t st) {
+  if (width > 0)
+    FMM_CUDA_TRY(cudaMemcpy2DAsync(dst + col, sizeof(T) * total, src, sizeof(T) * width, sizeof(T) * width, rows,
+                                   cudaMemcpyDeviceToDevice, st));
+}
+
+// FP64 tree-order records into x[], y[], z[] rows
+__global__ void soa_kernel(const dvec4* __restrict__ p, int64_t n, double* __restrict__ X) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const dvec4 v = p[i];
+    X[i] = v.x;
+    X[n + i] = v.y;
+    X[2 * n + i] = v.z;
+  }
+}
+
+__global__ void offset_i32_kernel(int32_t* __restrict__ dst, const int32_t* __restrict__ src, int64_t n, int32_t add,
+                                  int keep_negative) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = src[i];
+    dst[i] = (keep_negative && v < 0) ? v : v + add;
+  }
+}
+__global__ void offset_i64_kernel(int64_t* __restrict__ dst, const int64_t* __restrict__ src, int64_t n,
+                                  int64_t add) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i] + add;
+}
+
+}  // namespace
+
+void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
+  double *blo = nullptr, *bhi = nullptr;
+  build_hierarchy(t, pos, st, &blo, &bhi);
+  t->n_charges = t->n;
+  t->out_base = 0;
+  t->n_src_leaves = t->n_leaves;
+  t->src_leaf_box = t->leaf_box;
+  const int64_t leaf_off = level_offset(t->L, t->s);
+  std::vector<Step> steps;
+  int32_t *p2p_t = nullptr, *p2p_s = nullptr;
+  int64_t np = 0;
+  const Side side{0, t->L, t->level_avg_host};
+  try {
+    march(t, side, side, st, steps, &p2p_t, &p2p_s, &np);
+    finish_tree(t, steps, p2p_t, p2p_s, np, leaf_off, leaf_off, blo, bhi, t->has_duplicates, st);
+  } catch (...) {
+    cudaFree(blo), cudaFree(bhi);
+    throw;
+  }
   cudaFree(blo), cudaFree(bhi);
-  t->device_bytes -= sizeof(double) * 6 * NB;
-  cudaFree(p2p_trg);
-  cudaFree(starts);
-  cudaFree(Xa), cudaFree(Xb), cudaFree(Ia), cudaFree(Ib), cudaFree(flag);
+}
+
+// Two hierarchies (Sec. II.B, final part): the source tree's boxes come first
+// (ids 0 .. NB_s - 1), the target tree's follow; points likewise (sources
+// 0 .. n_s - 1 carry the charges, targets n_s .. n - 1 are evaluated).
+void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg, int64_t n_t, cudaStream_t st) {
+  const fmm_params prm = m->prm;
+  const int s = prm.splits, p = prm.p;
+  fmm_tree* S = new fmm_tree();
+  fmm_tree* T = new fmm_tree();
+  double *blo_s = nullptr, *bhi_s = nullptr, *blo_t = nullptr, *bhi_t = nullptr;
+  auto cleanup = [&] {
+    cudaFree(blo_s), cudaFree(bhi_s), cudaFree(blo_t), cudaFree(bhi_t);
+    S->src_leaf_box = T->src_leaf_box = nullptr;
+    free_tree(S);
+    free_tree(T);
+  };
+  try {
+    S->prm = prm;
+    S->n = n_s;
+    S->L = fmm_num_levels(n_s, prm.leaf_size, s);
+    T->prm = prm;
+    T->n = n_t;
+    T->L = fmm_num_levels(n_t, prm.leaf_size, s);
+    build_hierarchy(S, src, st, &blo_s, &bhi_s);
+    build_hierarchy(T, trg, st, &blo_t, &bhi_t);
+    const int64_t NBs = S->n_boxes, NBt = T->n_boxes, NB = NBs + NBt, N = n_s + n_t;
+    require(NB < ((int64_t)1 << 31) && N < ((int64_t)1 << 31), "source and target sets too large");
+    m->n = N;
+    m->s = s;
+    m->L = T->L;
+    m->L_src = S->L;
+    m->two_trees = 1;
+    m->n_charges = n_s;
+    m->out_base = n_s;
+    m->n_boxes = NB;
+    m->n_leaves = T->n_leaves;
+    m->n_src_leaves = S->n_leaves;
+    m->max_leaf = std::max(S->max_leaf, T->max_leaf);
+    m->level_avg_host = new double[S->L + T->L + 2];
+    for (int l = 0; l <= S->L; l++) m->level_avg_host[l] = S->level_avg_host[l];
+    for (int l = 0; l <= T->L; l++) m->level_avg_host[S->L + 1 + l] = T->level_avg_host[l];
+
+    m->perm = dev_alloc<int32_t>(m, N);
+    m->box_start = dev_alloc<int64_t>(m, NB);
+    m->box_count = dev_alloc<int32_t>(m, NB);
+    m->center = dev_alloc<double>(m, 3 * NB);
+    m->radius = dev_alloc<double>(m, NB);
+    m->inv_rho32 = dev_alloc<float>(m, NB);
+    m->inv_rho64 = dev_alloc<double>(m, NB);
+    m->leaf_box = dev_alloc<int32_t>(m, T->n_leaves);
+    m->src_leaf_box = dev_alloc<int32_t>(m, S->n_leaves);
+    m->box_parent = dev_alloc<int32_t>(m, NB);
+    m->pos_local = dev_alloc<float4>(m, N);
+    m->pos64 = dev_alloc<dvec4>(m, N);
+    m->m2m32 = dev_alloc<float>(m, (size_t)edge_fields(p) * NB);
+    m->m2m64 = dev_alloc<double>(m, (size_t)edge_fields(p) * NB);
+    m->l2l32 = dev_alloc<float>(m, (size_t)edge_fields(p) * NB);
+    m->l2l64 = dev_alloc<double>(m, (size_t)edge_fields(p) * NB);
+    FMM_CUDA_TRY(cudaMemsetAsync(m->m2m32, 0, sizeof(float) * edge_fields(p) * NB, st));
+    FMM_CUDA_TRY(cudaMemsetAsync(m->m2m64, 0, sizeof(double) * edge_fields(p) * NB, st));
+    FMM_CUDA_TRY(cudaMemsetAsync(m->l2l32, 0, sizeof(float) * edge_fields(p) * NB, st));
+    FMM_CUDA_TRY(cudaMemsetAsync(m->l2l64, 0, sizeof(double) * edge_fields(p) * NB, st));
+
+    copy_d2d(m->perm, S->perm, n_s, st);
+    offset_i32_kernel<<<grid_for(n_t, 256), 256, 0, st>>>(m->perm + n_s, T->perm, n_t, (int32_t)n_s, 0);
+    copy_d2d(m->box_start, S->box_start, NBs, st);
+    offset_i64_kernel<<<grid_for(NBt, 256), 256, 0, st>>>(m->box_start + NBs, T->box_start, NBt, n_s);
+    copy_d2d(m->box_count, S->box_count, NBs, st);
+    copy_d2d(m->box_count + NBs, T->box_count, NBt, st);
+    copy_d2d(m->center, S->center, 3 * NBs, st);
+    copy_d2d(m->center + 3 * NBs, T->center, 3 * NBt, st);
+    copy_d2d(m->radius, S->radius, NBs, st);
+    copy_d2d(m->radius + NBs, T->radius, NBt, st);
+    copy_d2d(m->inv_rho32, S->inv_rho32, NBs, st);
+    copy_d2d(m->inv_rho32 + NBs, T->inv_rho32, NBt, st);
+    copy_d2d(m->inv_rho64, S->inv_rho64, NBs, st);
+    copy_d2d(m->inv_rho64 + NBs, T->inv_rho64, NBt, st);
+    offset_i32_kernel<<<grid_for(T->n_leaves, 256), 256, 0, st>>>(m->leaf_box, T->leaf_box, T->n_leaves,
+                                                                  (int32_t)NBs, 0);
+    copy_d2d(m->src_leaf_box, S->leaf_box, S->n_leaves, st);
+    copy_d2d(m->box_parent, S->box_parent, NBs, st);
+    offset_i32_kernel<<<grid_for(NBt, 256), 256, 0, st>>>(m->box_parent + NBs, T->box_parent, NBt, (int32_t)NBs, 1);
+    FMM_LAUNCH_CHECK();
+    copy_d2d(m->pos_local, S->pos_local, n_s, st);
+    copy_d2d(m->pos_local + n_s, T->pos_local, n_t, st);
+    copy_d2d(m->pos64, S->pos64, n_s, st);
+    copy_d2d(m->pos64 + n_s, T->pos64, n_t, st);
+    // multipoles move up the source tree, locals down the target tree
+    copy_rows(m->m2m32, NB, 0, S->m2m32, NBs, edge_fields(p), st);
+    copy_rows(m->m2m64, NB, 0, S->m2m64, NBs, edge_fields(p), st);
+    copy_rows(m->l2l32, NB, NBs, T->l2l32, NBt, edge_fields(p), st);
+    copy_rows(m->l2l64, NB, NBs, T->l2l64, NBt, edge_fields(p), st);
+
+    // M2M rounds over the source tree, L2L rounds over the target tree
+    m->n_up = S->L;
+    m->n_down = T->L;
+    m->up_off_h = new int64_t[S->L + 1];
+    m->down_off_h = new int64_t[T->L + 1];
+    for (int r = 0; r <= S->L; r++) m->up_off_h[r] = S->up_off_h[r];
+    for (int r = 0; r <= T->L; r++) m->down_off_h[r] = T->down_off_h[r];
+    m->up_ids = dev_alloc<int32_t>(m, std::max<int64_t>(NBs, 1));
+    m->down_ids = dev_alloc<int32_t>(m, std::max<int64_t>(NBt, 1));
+    copy_d2d(m->up_ids, S->up_ids, NBs, st);
+    offset_i32_kernel<<<grid_for(NBt, 256), 256, 0, st>>>(m->down_ids, T->down_ids, NBt, (int32_t)NBs, 0);
+    FMM_LAUNCH_CHECK();
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+
+    // can a target coincide with a source?  (duplicates among the union;
+    // conservative when a set has duplicates of its own)
+    int has_dup = S->has_duplicates | T->has_duplicates;
+    if (!has_dup) {
+      double* X = scratch_alloc<double>(3 * (size_t)N);
+      soa_kernel<<<grid_for(N, 256), 256, 0, st>>>(m->pos64, N, X);
+      FMM_LAUNCH_CHECK();
+      int64_t tsize = 1;
+      while (tsize < 2 * N) tsize <<= 1;
+      int* tab = scratch_alloc<int>(tsize);
+      int* flag = scratch_alloc<int>(1);
+      FMM_CUDA_TRY(cudaMemsetAsync(tab, 0xff, sizeof(int) * tsize, st));
+      FMM_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+      duplicate_kernel<<<grid_for(N, 256), 256, 0, st>>>(X, N, tab, tsize - 1, flag);
+      FMM_LAUNCH_CHECK();
+      FMM_CUDA_TRY(cudaMemcpyAsync(&has_dup, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FMM_CUDA_TRY(cudaStreamSynchronize(st));
+      cudaFree(X), cudaFree(tab), cudaFree(flag);
+    }
+    m->has_duplicates = has_dup;
+    double* blo = scratch_alloc<double>(3 * (size_t)NB);
+    double* bhi = scratch_alloc<double>(3 * (size_t)NB);
+    copy_d2d(blo, blo_s, 3 * NBs, st);
+    copy_d2d(blo + 3 * NBs, blo_t, 3 * NBt, st);
+    copy_d2d(bhi, bhi_s, 3 * NBs, st);
+    copy_d2d(bhi + 3 * NBs, bhi_t, 3 * NBt, st);
+
+    std::vector<Step> steps;
+    int32_t *p2p_t = nullptr, *p2p_s = nullptr;
+    int64_t np = 0;
+    try {
+      march(m, Side{0, S->L, S->level_avg_host}, Side{NBs, T->L, T->level_avg_host}, st, steps, &p2p_t, &p2p_s,
+            &np);
+      finish_tree(m, steps, p2p_t, p2p_s, np, NBs + level_offset(T->L, s), level_offset(S->L, s), blo, bhi,
+                  has_dup, st);
+    } catch (...) {
+      cudaFree(blo), cudaFree(bhi);
+      throw;
+    }
+    cudaFree(blo), cudaFree(bhi);
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
 }
 
 }  // namespace fmm

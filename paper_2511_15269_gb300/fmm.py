@@ -21,7 +21,8 @@ FMM_SAME_LEVEL = 2
 FMM_MAX_P = 10
 
 # exported entry points, in include/fmm.h order
-ENTRY_POINTS = ["fmm_last_error", "fmm_num_levels", "fmm_build_tree", "fmm_tree_free", "fmm_tree_merge",
+ENTRY_POINTS = ["fmm_device_peaks", "fmm_last_error", "fmm_num_levels", "fmm_build_tree", "fmm_build_tree2", "fmm_tree_free",
+                "fmm_tree_merge",
                 "fmm_tree_point_offsets",
                 "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_export",
                 "fmm_tree_profile", "fmm_tree_stage_times", "fmm_eval_potential", "fmm_eval_field",
@@ -45,7 +46,9 @@ class fmm_stats(C.Structure):
                 ("leaf_size", C.c_int), ("precision", C.c_int), ("theta", C.c_double),
                 ("n_boxes", C.c_int64), ("n_leaves", C.c_int64), ("n_m2l", C.c_int64),
                 ("n_p2p", C.c_int64), ("n_p2p_pairs", C.c_int64), ("device_bytes", C.c_size_t),
-                ("build_ms", C.c_double), ("kernel_launches", C.c_int64), ("n_trees", C.c_int)]
+                ("build_ms", C.c_double), ("kernel_launches", C.c_int64), ("n_trees", C.c_int),
+                ("levels_src", C.c_int), ("n_sources", C.c_int64), ("n_targets", C.c_int64),
+                ("n_src_leaves", C.c_int64)]
 
 
 def library_path():
@@ -62,9 +65,11 @@ def lib():
         L = C.CDLL(_LIB_PATH)
         vp, i64, i = C.c_void_p, C.c_int64, C.c_int
         L.fmm_last_error.restype = C.c_char_p
+        L.fmm_device_peaks.argtypes = [vp, vp]
         L.fmm_num_levels.argtypes = [i64, i, i]
         L.fmm_num_levels.restype = i
         L.fmm_build_tree.argtypes = [vp, i64, C.POINTER(fmm_params), vp, C.POINTER(vp)]
+        L.fmm_build_tree2.argtypes = [vp, i64, vp, i64, C.POINTER(fmm_params), vp, C.POINTER(vp)]
         L.fmm_tree_free.argtypes = [vp]
         L.fmm_tree_merge.argtypes = [vp, i, vp, C.POINTER(vp)]
         L.fmm_tree_point_offsets.argtypes = [vp, vp]
@@ -102,6 +107,15 @@ def _dev(t, shape_last=None):
     return C.c_void_p(t.data_ptr())
 
 
+def fmm_device_peaks():
+    """Measured FP32 / packed FP32x2 / FP64 FMA TFLOP/s and rsqrt Gop/s."""
+    import numpy as np
+    out = np.zeros(4)
+    _check(lib().fmm_device_peaks(C.c_void_p(out.ctypes.data), _stream()))
+    return {"fp32_fma_tflops": out[0], "fp32x2_fma_tflops": out[1], "fp64_fma_tflops": out[2],
+            "rsqrt_gops": out[3]}
+
+
 def fmm_last_error():
     return lib().fmm_last_error().decode(errors="replace")
 
@@ -111,12 +125,16 @@ def fmm_num_levels(n, leaf_size, splits=2):
 
 
 class Tree:
-    """Owner of an fmm_tree* built by fmm_build_tree."""
+    """Owner of an fmm_tree* built by fmm_build_tree / fmm_build_tree2.
+    n_charges: length of q; n_out: length of u (both n for one point set)."""
 
-    def __init__(self, handle, n, params):
+    def __init__(self, handle, n, params, n_charges=None, n_out=None):
         self._h = handle
         self.n = n
         self.params = params
+        self.n_charges = n if n_charges is None else n_charges
+        self.n_out = n if n_out is None else n_out
+        self.two_trees = n_charges is not None
 
     @property
     def handle(self):
@@ -148,6 +166,17 @@ def fmm_build_tree(pos, p, leaf_size, splits=2, theta=0.5, precision=FMM_FP32C, 
     h = C.c_void_p()
     _check(lib().fmm_build_tree(_dev(pos), n, C.byref(prm), _stream(), C.byref(h)))
     return Tree(h, n, prm)
+
+
+def fmm_build_tree2(src_pos, trg_pos, p, leaf_size, splits=2, theta=0.5, precision=FMM_FP32C, flags=0):
+    """Separate source and target hierarchies: evaluations take charges at
+    src_pos (N_s x 3) and return potentials / fields at trg_pos (N_t x 3)."""
+    src_pos, trg_pos = src_pos.contiguous(), trg_pos.contiguous()
+    ns, nt = src_pos.shape[0], trg_pos.shape[0]
+    prm = fmm_params(int(p), int(leaf_size), int(splits), float(theta), int(precision), int(flags))
+    h = C.c_void_p()
+    _check(lib().fmm_build_tree2(_dev(src_pos), ns, _dev(trg_pos), nt, C.byref(prm), _stream(), C.byref(h)))
+    return Tree(h, ns + nt, prm, n_charges=ns, n_out=nt)
 
 
 def fmm_tree_free(tree):
@@ -191,9 +220,10 @@ def fmm_tree_export(tree):
     import numpy as np
     st = fmm_tree_stats(tree)
     nb, L = st["n_boxes"], st["levels"]
+    n_avg = st["levels_src"] + L + 2 if tree.two_trees else L + 1
     out = dict(perm=np.zeros(st["n"], np.int32), box_start=np.zeros(nb, np.int64),
                box_count=np.zeros(nb, np.int64), center=np.zeros((nb, 3)), radius=np.zeros(nb),
-               level_avg_radius=np.zeros(L + 1), m2l_trg=np.zeros(st["n_m2l"], np.int32),
+               level_avg_radius=np.zeros(n_avg), m2l_trg=np.zeros(st["n_m2l"], np.int32),
                m2l_src=np.zeros(st["n_m2l"], np.int32), p2p_trg=np.zeros(st["n_p2p"], np.int32),
                p2p_src=np.zeros(st["n_p2p"], np.int32))
     keys = ["perm", "box_start", "box_count", "center", "radius", "level_avg_radius", "m2l_trg",
@@ -216,14 +246,14 @@ def fmm_tree_stage_times(tree):
 
 
 def fmm_eval_potential(tree, q, out=None):
-    u = out if out is not None else torch.empty(tree.n, dtype=torch.float64, device=q.device)
+    u = out if out is not None else torch.empty(tree.n_out, dtype=torch.float64, device=q.device)
     _check(lib().fmm_eval_potential(tree.handle, _dev(q), _dev(u), _stream()))
     return u
 
 
 def fmm_eval_field(tree, q, potential=True):
-    f = torch.empty((tree.n, 3), dtype=torch.float64, device=q.device)
-    u = torch.empty(tree.n, dtype=torch.float64, device=q.device) if potential else None
+    f = torch.empty((tree.n_out, 3), dtype=torch.float64, device=q.device)
+    u = torch.empty(tree.n_out, dtype=torch.float64, device=q.device) if potential else None
     _check(lib().fmm_eval_field(tree.handle, _dev(q), _dev(u) if u is not None else None, _dev(f),
                                 _stream()))
     return (u, f) if potential else f
@@ -232,7 +262,7 @@ def fmm_eval_field(tree, q, potential=True):
 def fmm_eval_potential_host(tree, q_host, u_host=None):
     """Host-buffer evaluation: q_host, u_host are float64 CPU tensors (pinned is fastest)."""
     if u_host is None:
-        u_host = torch.empty(tree.n, dtype=torch.float64, pin_memory=True)
+        u_host = torch.empty(tree.n_out, dtype=torch.float64, pin_memory=True)
     assert q_host.dtype == torch.float64 and not q_host.is_cuda and q_host.is_contiguous()
     _check(lib().fmm_eval_potential_host(tree.handle, C.c_void_p(q_host.data_ptr()),
                                          C.c_void_p(u_host.data_ptr()), _stream()))
@@ -276,3 +306,22 @@ class FMMPotential(torch.autograd.Function):
         gq, gp = fmm_backward(ctx.tree, q.contiguous(), grad_u.contiguous(), need_q=need_q,
                               need_pos=need_pos)
         return gp, gq, None
+
+
+class FMMPotential2(torch.autograd.Function):
+    """u = FMM potential at the targets of charges q at the sources of a
+    source/target tree pair built by fmm_build_tree2.
+
+    dL/dq = K^T dL/du is the potential at the sources of charges dL/du at the
+    targets, evaluated with the reverse tree (sources and targets swapped), to
+    FMM accuracy.  Position gradients are not offered for separate trees."""
+
+    @staticmethod
+    def forward(ctx, q, tree, tree_rev):
+        ctx.tree_rev = tree_rev
+        return fmm_eval_potential(tree, q.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        gq = fmm_eval_potential(ctx.tree_rev, grad_u.contiguous()) if ctx.needs_input_grad[0] else None
+        return gq, None, None

@@ -73,6 +73,13 @@ def dup_grid(n, seed):
     return np.round(rng.random((n, 3)) * 8) / 8  # many exact duplicates
 
 
+def random_dups(n, seed):
+    # exact copies of random FP64 points, which land in other leaves too
+    rng = np.random.default_rng(seed)
+    base = rng.random((n - n // 6, 3))
+    return np.concatenate([base, base[rng.choice(len(base), n // 6)]])
+
+
 TREE_CASES = [
     ("cube4k_cfg", lambda: workloads.uniform_cube(4096, 0)[0], 64, 2, 0.4, 0),
     ("plummer30k", lambda: workloads.plummer_sphere(30000, 1)[0], 64, 2, 0.5, 0),
@@ -112,6 +119,8 @@ POT_CASES = [
     ("cube3k_p1", lambda: workloads.uniform_cube(3000, 6), 1, 32, 2, 0.5),
     ("ragged_p5_leaf200", lambda: workloads.uniform_cube(7777, 7), 5, 200, 2, 0.5),
     ("duplicates_p6", lambda: (dup_grid(5000, 8), np.random.default_rng(8).uniform(-1, 1, 5000)), 6, 16, 2, 0.5),
+    ("random_duplicates_p6", lambda: (random_dups(6000, 9), np.random.default_rng(9).uniform(-1, 1, 6000)), 6, 16, 2,
+     0.5),
 ]
 
 

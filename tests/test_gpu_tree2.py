@@ -1,0 +1,172 @@
+"""Separate source and target hierarchies (Sec. II.B, final part) on the GPU,
+through the C ABI, against the oracle's two-tree FMM and direct sums.
+
+Trees, geometry and lists must be bit-identical to the oracle's; potentials
+and fields obey the tolerances of the single-tree parity tests."""
+import numpy as np
+import pytest
+
+from paper_2511_15269_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL_FP64 = 1e-12
+TOL_FP64_FIELD = 1e-11
+TOL_FP32 = 3e-6
+TOL_FP32_FIELD = 3e-5
+
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_15269_gb300 import build, fmm
+    build.build()
+    fmm.lib()
+    return fmm
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def halo(n, seed, lo=-0.2, hi=1.2):
+    return lo + (hi - lo) * np.random.default_rng(seed).random((n, 3))
+
+
+def shell(n, seed, c=0.5, r=0.3):
+    v = np.random.default_rng(seed).normal(size=(n, 3))
+    return c + r * v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+CASES = [
+    # name, sources, targets, leaf, s, theta, flags
+    ("cube_halo", lambda: workloads.uniform_cube(20000, 1)[0], lambda: halo(5000, 2), 32, 2, 0.5, 0),
+    ("few_targets", lambda: workloads.uniform_cube(30000, 3)[0], lambda: halo(300, 4), 32, 2, 0.5, 0),
+    ("few_sources", lambda: workloads.gaussian_clusters(700, 5)[0], lambda: halo(25000, 6), 32, 2, 0.5, 0),
+    ("shell_in_plummer", lambda: workloads.plummer_sphere(20000, 7)[0], lambda: shell(4000, 8, 0.0, 0.5), 64, 2,
+     0.5, 0),
+    ("helix_s3_tie_target", lambda: workloads.double_helix(9000, 9, 5.0, 1.0, 3.4, 0.1)[0],
+     lambda: halo(3000, 10, -2.0, 2.0) * np.array([1.0, 1.0, 5.0]), 16, 3, 0.6, 1),
+    ("far_targets", lambda: workloads.uniform_cube(8000, 11)[0], lambda: halo(900, 12) + 6.0, 32, 2, 0.5, 0),
+    ("s1", lambda: workloads.uniform_cube(5000, 13)[0], lambda: halo(4000, 14), 8, 1, 0.5, 0),
+]
+
+
+def build_both(F, orc, sp, tp, p, leaf, s, theta, prec, flags):
+    T = F.fmm_build_tree2(cuda(sp), cuda(tp), p, leaf, s, theta, prec, flags)
+    O = orc.Tree2(sp, tp, leaf, s, theta, tie_target=bool(flags & F.FMM_TIE_TARGET))
+    return T, O
+
+
+@pytest.mark.parametrize("name,mks,mkt,leaf,s,theta,flags", CASES, ids=[c[0] for c in CASES])
+def test_tree2_hierarchies_and_lists_bit_exact(F, orc, name, mks, mkt, leaf, s, theta, flags):
+    sp, tp = mks(), mkt()
+    T, O = build_both(F, orc, sp, tp, 4, leaf, s, theta, F.FMM_FP32C, flags)
+    st = F.fmm_tree_stats(T)
+    S, G = O.src, O.trg
+    assert (st["levels_src"], st["levels"]) == (S.L, G.L)
+    assert (st["n_sources"], st["n_targets"], st["n"]) == (len(sp), len(tp), len(sp) + len(tp))
+    assert (st["n_boxes"], st["n_leaves"], st["n_src_leaves"]) == (S.n_boxes + G.n_boxes, G.n_leaves, S.n_leaves)
+    assert (st["n_m2l"], st["n_p2p"]) == (O.n_m2l, O.n_p2p)
+    ex = F.fmm_tree_export(T)
+    np.testing.assert_array_equal(ex["perm"], np.concatenate([S.perm, G.perm + len(sp)]))
+    np.testing.assert_array_equal(ex["box_start"], np.concatenate([S.box_start, G.box_start + len(sp)]))
+    np.testing.assert_array_equal(ex["box_count"], np.concatenate([S.box_count, G.box_count]))
+    for k in ("center", "radius"):
+        ref = np.concatenate([getattr(S, k), getattr(G, k)])
+        np.testing.assert_array_equal(ex[k].view(np.uint64), ref.view(np.uint64))
+    avg = np.concatenate([S.level_avg_radius, G.level_avg_radius])
+    np.testing.assert_array_equal(ex["level_avg_radius"].view(np.uint64), avg.view(np.uint64))
+    for k in ("m2l_trg", "m2l_src", "p2p_trg", "p2p_src"):
+        np.testing.assert_array_equal(ex[k], getattr(O, k))
+    ls_off, lt_off = S.level_offset(S.L), G.level_offset(G.L)
+    pairs = sum(int(G.box_count[lt_off + t]) * int(S.box_count[ls_off + s_]) for t, s_ in zip(O.p2p_trg, O.p2p_src))
+    assert st["n_p2p_pairs"] == pairs
+    F.fmm_tree_status(T)
+
+
+@pytest.mark.parametrize("name,mks,mkt,leaf,s,theta,flags", CASES, ids=[c[0] for c in CASES])
+def test_tree2_potential_and_field_parity(F, orc, name, mks, mkt, leaf, s, theta, flags):
+    sp, tp = mks(), mkt()
+    q = np.random.default_rng(99).uniform(-1, 1, len(sp))
+    p = 7
+    T, O = build_both(F, orc, sp, tp, p, leaf, s, theta, F.FMM_FP64, flags)
+    u_o, f_o = O.eval(q, p, field=True)
+    u64, f64 = (x.cpu().numpy() for x in F.fmm_eval_field(T, cuda(q)))
+    assert u64.shape == (len(tp),) and f64.shape == (len(tp), 3)
+    F.fmm_tree_set_precision(T, F.FMM_FP32C)
+    u32, f32 = (x.cpu().numpy() for x in F.fmm_eval_field(T, cuda(q)))
+    u32p = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    F.fmm_tree_status(T)
+    e = (rel_l2(u64, u_o), rel_l2(f64, f_o), rel_l2(u32, u_o), rel_l2(f32, f_o), rel_l2(u32p, u_o))
+    print("%s: fp64 u %.2e f %.2e, fp32c u %.2e f %.2e (potential-only %.2e)" % ((name,) + e))
+    assert e[0] <= TOL_FP64 and e[1] <= TOL_FP64_FIELD
+    assert e[2] <= TOL_FP32 and e[3] <= TOL_FP32_FIELD and e[4] <= TOL_FP32
+
+
+def test_tree2_targets_on_sources(F, orc):
+    """Targets at exactly the positions of sources skip those charges."""
+    sp, q = workloads.uniform_cube(12000, 15)
+    idx = np.random.default_rng(16).choice(len(sp), 2000, replace=False)
+    tp = np.concatenate([sp[idx], halo(1000, 17)])
+    T, O = build_both(F, orc, sp, tp, 8, 32, 2, 0.5, F.FMM_FP64, 0)
+    u_o = O.eval(q, 8)
+    u64 = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    F.fmm_tree_set_precision(T, F.FMM_FP32C)
+    u32 = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    assert np.all(np.isfinite(u32))
+    assert rel_l2(u64, u_o) <= TOL_FP64
+    assert rel_l2(u32, u_o) <= TOL_FP32
+    assert rel_l2(u32, orc.direct2(sp, q, tp)) < 1e-5
+
+
+def test_tree2_equal_sets_match_the_single_tree(F):
+    pos, q = workloads.plummer_sphere(30000, 18)
+    A = F.fmm_build_tree(cuda(pos), 8, 64, 2, 0.5, F.FMM_FP64)
+    B = F.fmm_build_tree2(cuda(pos), cuda(pos), 8, 64, 2, 0.5, F.FMM_FP64)
+    ua = F.fmm_eval_potential(A, cuda(q)).cpu().numpy()
+    ub = F.fmm_eval_potential(B, cuda(q)).cpu().numpy()
+    assert rel_l2(ub, ua) <= 1e-14
+
+
+def test_tree2_host_buffers_and_rejections(F):
+    sp, q = workloads.uniform_cube(6000, 19)
+    tp = halo(1500, 20)
+    T = F.fmm_build_tree2(cuda(sp), cuda(tp), 6, 32)
+    qh = torch.from_numpy(q).pin_memory()
+    uh = F.fmm_eval_potential_host(T, qh)
+    assert uh.shape == (1500,)
+    ud = F.fmm_eval_potential(T, cuda(q)).cpu()
+    assert torch.equal(uh, ud)
+    with pytest.raises(F.FmmError):
+        F.fmm_backward(T, cuda(q), torch.ones(1500, dtype=torch.float64, device="cuda"))
+    with pytest.raises(F.FmmError):
+        F.fmm_tree_merge([T])
+    with pytest.raises(F.FmmError):
+        F.fmm_eval_potential_static(T, cuda(q))
+    with pytest.raises(F.FmmError):
+        F.fmm_build_tree2(cuda(sp), cuda(tp), 6, 32, 2, 0.5, F.FMM_FP32C, F.FMM_SAME_LEVEL)
+    F.fmm_tree_status(T)
+
+
+def test_tree2_autograd_charge_gradient(F, orc):
+    """dL/dq for L = <w, u(targets)> through FMMPotential2 equals the
+    transposed direct sum (potential at the sources of charges w)."""
+    sp, q = workloads.uniform_cube(8000, 21)
+    tp = shell(3000, 22, 0.5, 0.8)
+    w = np.random.default_rng(23).normal(size=len(tp))
+    T = F.fmm_build_tree2(cuda(sp), cuda(tp), 8, 32, 2, 0.5)
+    R = F.fmm_build_tree2(cuda(tp), cuda(sp), 8, 32, 2, 0.5)
+    qt = cuda(q).requires_grad_(True)
+    u = F.FMMPotential2.apply(qt, T, R)
+    (u * cuda(w)).sum().backward()
+    g_ref = orc.direct2(tp, w, sp)
+    assert rel_l2(qt.grad.cpu().numpy(), g_ref) < 1e-5
+    assert rel_l2(u.detach().cpu().numpy(), orc.direct2(sp, q, tp)) < 1e-5
