@@ -262,6 +262,41 @@ def bench_batched(fmm, workloads, oracle, dev):
             "rel_l2_vs_direct_64_targets_per_set": float(np.sqrt(errs_num / errs_den))}
 
 
+PAPER_SETS = [  # Sec. III.A parameter sets: (name, N_max, p, theta, precision, A100 Mpoints/s at 2^20)
+    ("set1", 128, 5, 0.70, "fp32c", 30.4),
+    ("set2", 256, 9, 0.50, "fp32c", 4.04),
+    ("set3", 256, 10, 0.27, "fp64", 0.736),
+]
+
+
+def bench_paper_sets(fmm, dev, pos_d, q_d, tg, ud):
+    """The three parameter sets of Sec. III.A on the uniform cube N = 2^20 (the
+    bench's own points): evaluation time with a prebuilt tree, rel L-inf and
+    L2 error on the sampled targets vs the direct sum, per-stage times."""
+    import torch
+    n = q_d.shape[0]
+    out = {}
+    for name, leaf, p, theta, prec, a100 in PAPER_SETS:
+        pr = fmm.FMM_FP64 if prec == "fp64" else fmm.FMM_FP32C
+        T = fmm.fmm_build_tree(pos_d, p, leaf, 2, theta, pr)
+        u = torch.empty_like(q_d)
+        ms = event_ms(lambda: fmm.fmm_eval_potential(T, q_d, u), 1 if prec == "fp64" else 5)
+        fmm.fmm_tree_profile(T, True)
+        fmm.fmm_eval_potential(T, q_d, u)
+        torch.cuda.synchronize()
+        fmm.fmm_tree_profile(T, False)
+        stages, calls = fmm.fmm_tree_stage_times(T)
+        uu = u.cpu().numpy()[tg]
+        st = fmm.fmm_tree_stats(T)
+        T.free()
+        out[name] = {"N_max": leaf, "p": p, "theta": theta, "precision": prec, "ms": ms,
+                     "Mpoints/s": n / ms / 1e3, "rel_linf": rel_linf(uu, ud), "rel_l2": rel_l2(uu, ud),
+                     "n_p2p_pairs": st["n_p2p_pairs"], "n_m2l": st["n_m2l"],
+                     "stage_ms": {k: v / max(calls, 1) for k, v in stages.items()},
+                     "paper_a100_Mpoints/s": a100}
+    return out
+
+
 def config_dict(cfg, path):
     return {"workload": "uniform cube N=%d (U[0,1)^3, q U[-1,1], seed 0), p=%d, leaf %d, s=%d, theta=%g, %s"
             % (cfg["n"], cfg["p"], cfg["leaf_size"], cfg["s"], cfg["theta"], path),
@@ -444,6 +479,7 @@ def main():
             m, dt = oracle_sample_eval(O, q, cfg["p"], rng.choice(O.n_leaves, 32, replace=False), O.n_leaves)
             pts += m
             secs += dt
+        line["paper_sets_cube1m"] = bench_paper_sets(fmm, dev, pos_d, q_d, tg, ud)
         line["plummer4m_p10"] = bench_plummer(fmm, workloads, oracle, dev)
         line["batched64_p6"] = bench_batched(fmm, workloads, oracle, dev)
         line["cpu_baseline"] = {

@@ -355,3 +355,45 @@ def direct_vjp(pos, q, g):
     dpos = np.zeros((len(q), 3))
     lib().orc_direct_vjp(_p(pos), _p(q), _p(g), len(q), _p(dq), _p(dpos))
     return dq, dpos
+
+
+# ---- active shielding (Sec. III.B) ----
+def _kernel_matrix(src_pos, trg_pos):
+    """K[i, j]: potential at target i of a unit charge at source j (columns
+    by the direct sum)."""
+    sp = _f64(src_pos).reshape(-1, 3)
+    K = np.zeros((len(_f64(trg_pos).reshape(-1, 3)), len(sp)))
+    for j in range(len(sp)):
+        e = np.zeros(len(sp))
+        e[j] = 1.0
+        K[:, j] = direct2(sp, e, trg_pos)
+    return K
+
+
+def shielding_loss(geo, q_sh, weights=(1.0, 0.2, 0.1)):
+    """Loss of Sec. III.B with direct-sum potentials: (total, L_in, L_out, L_reg)."""
+    src = np.concatenate([geo["ext"], geo["shield"]])
+    q_all = np.concatenate([geo["q_ext"], q_sh])
+    phi_in = direct2(src, q_all, geo["inside"])
+    phi_out = direct2(geo["shield"], q_sh, geo["outside"])
+    l_in = float(np.sum((phi_in - phi_in.mean()) ** 2))
+    l_out = float(np.sum(phi_out ** 2))
+    l_reg = float(np.sum(np.asarray(q_sh) ** 2))
+    w_in, w_out, w_reg = weights
+    return w_in * l_in + w_out * l_out + w_reg * l_reg, l_in, l_out, l_reg
+
+
+def shielding_optimum(geo, weights=(1.0, 0.2, 0.1)):
+    """Minimiser of the Sec. III.B loss, which is quadratic in the shield
+    charges: with C the centring projector, A, B the direct-sum potential
+    matrices of the shield at the inner and outer points and b the external
+    potential at the inner points, the normal equations read
+    (w_in A^T C A + w_out B^T B + w_reg I) q = -w_in A^T C b."""
+    w_in, w_out, w_reg = weights
+    A = _kernel_matrix(geo["shield"], geo["inside"])
+    B = _kernel_matrix(geo["shield"], geo["outside"])
+    b = direct2(geo["ext"], geo["q_ext"], geo["inside"])
+    Ac = A - A.mean(axis=0, keepdims=True)
+    bc = b - b.mean()
+    H = w_in * Ac.T @ Ac + w_out * B.T @ B + w_reg * np.eye(A.shape[1])
+    return np.linalg.solve(H, -w_in * Ac.T @ bc)

@@ -89,6 +89,28 @@ def double_helix(n, seed=0, turns=4.0, radius=1.0, pitch=0.5, tube=0.05):
     return pos, q
 
 
+def fibonacci_sphere(n, radius):
+    """n points spread evenly over a sphere (golden-angle spiral): z_k equally
+    spaced in (-1, 1), azimuth advancing by the golden angle."""
+    k = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * k + 1.0) / n
+    rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = k * np.pi * (3.0 - np.sqrt(5.0))
+    return radius * np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+
+
+def active_shielding(seed=0, n_sh=128, r_sh=2.0, n_ext=256, r_ext=5.0, n_in=1024, r_in=1.5, n_out=1024,
+                     r_out=2.5):
+    """Geometry of the active-shielding demonstration (Sec. III.B): shield
+    charge sites spread evenly on a sphere of radius r_sh, external charges
+    U[-1,1] at uniformly random positions on a sphere of radius r_ext, and
+    evenly spread sampling points inside (r_in) and outside (r_out)."""
+    rng = np.random.default_rng(seed)
+    return dict(shield=fibonacci_sphere(n_sh, r_sh), ext=_unit_vectors(rng, n_ext) * r_ext,
+                q_ext=rng.uniform(-1.0, 1.0, n_ext), inside=fibonacci_sphere(n_in, r_in),
+                outside=fibonacci_sphere(n_out, r_out))
+
+
 def thin_film(cells=256, seed=0):
     """Film [0,1]^2 x [0,h], h = 1/cells, one random unit magnetisation m per
     cell.  Surface charges of div m sit at the top face centres (z = h,
