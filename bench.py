@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpoints/s per FMM eval at 1M pts, FP32 vs FP64 at stated error; bwd/fwd ratio"
 WORKLOAD = "cube1m_p8"
-FP32_FLOPS_PER_PAIR = 10  # potential: 3 sub, 3 for r^2, 1 rsqrt-scale, 2 accumulate (+1 select)
+FP32_FLOPS_PER_PAIR = 10  # potential, per ordered pair: 3 sub, 5 for r^2, 2 for the accumulating FMA
 SMS = 152
 FP32_LANES = 128
 
@@ -339,6 +339,7 @@ def main():
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
     st = fmm.fmm_tree_stats(T)
+    peaks = fmm.fmm_device_peaks()  # measured FFMA / FFMA2 / DFMA / rsqrt throughput
     u_d = torch.empty(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -389,18 +390,25 @@ def main():
 
     # ---- roofline of the dominant kernel (near field, P2P) ----
     clk = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak_tflops = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+    derived_tflops = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+    peak_tflops = max(peaks["fp32_fma_tflops"], peaks["fp32x2_fma_tflops"])
     pairs = st["n_p2p_pairs"]
+    leaf_counts = fmm.fmm_tree_export(T)["box_count"][-st["n_leaves"]:]
+    self_pairs = int(np.sum(leaf_counts.astype(np.int64) ** 2))
+    rsqrt_count = (pairs - self_pairs) // 2 + self_pairs  # one rsqrt per unordered off-diagonal pair
     p2p_s = stage_ms["p2p"] * 1e-3
     achieved = pairs * FP32_FLOPS_PER_PAIR / p2p_s / 1e12
-    roofline = {"bound": "alu", "kernel": "p2p_kernel (near field, FP32 + MUFU rsqrt)",
+    roofline = {"bound": "alu", "kernel": "p2p_kernel_f32s (symmetric near field, FP32 + MUFU rsqrt)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "traffic": None,
-                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
-                               % (SMS, FP32_LANES, clk),
+                "peak_source": "measured: fmm_device_peaks FP32 FMA probe (scalar %.1f, packed %.1f TFLOP/s); "
+                               "derived 152 SMs x 128 lanes x 2 x %.0f MHz = %.1f"
+                               % (peaks["fp32_fma_tflops"], peaks["fp32x2_fma_tflops"], clk, derived_tflops),
                 "pairs_per_launch": pairs, "flops_per_pair": FP32_FLOPS_PER_PAIR,
                 "p2p_ms": stage_ms["p2p"],
-                "mufu_frac": pairs / p2p_s / (SMS * 16 * clk * 1e6)}
+                "rsqrt_per_launch": rsqrt_count,
+                "mufu_frac": rsqrt_count / p2p_s / (peaks["rsqrt_gops"] * 1e9),
+                "mufu_peak_gops": peaks["rsqrt_gops"]}
 
     # ---- end to end through the host-buffer entry point ----
     qh = torch.from_numpy(q).pin_memory()
@@ -424,6 +432,7 @@ def main():
         "wall_s_timed": wall, "tree_build_ms": build_ms,
         "stage_ms": stage_ms,
         "tree": {k: st[k] for k in ("levels", "n_boxes", "n_m2l", "n_p2p", "n_p2p_pairs", "device_bytes")},
+        "device_peaks": peaks,
     }
 
     if not args.no_extras and world == 1:

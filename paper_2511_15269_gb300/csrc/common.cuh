@@ -113,6 +113,17 @@ struct fmm_tree {
   int32_t* p2p_src = nullptr;    // n_p2p
   fmm::P2PEntry* p2p32 = nullptr;  // n_p2p
   float* p2p_thr = nullptr;        // n_p2p: FP32 coincidence threshold on r^2
+  // symmetric near field (one point set or a batch of them; symmetric.cu)
+  int sym = 0;
+  int64_t n_slots = 0;                // leaf pairs evaluated once for both sides
+  int sym_stride = 0;                 // floats per slot (>= largest leaf)
+  int32_t* sym_slot = nullptr;        // n_p2p: slot of a symmetric or received entry, else -1
+  int64_t* sym_work_off = nullptr;    // n_leaves + 1
+  int32_t* sym_work = nullptr;        // entries each leaf's warp evaluates, list order
+  int64_t* sym_recv_off = nullptr;    // n_leaves + 1
+  int32_t* sym_recv = nullptr;        // slots each leaf's local evaluation adds, list order
+  float* sym_partial = nullptr;       // n_slots x sym_stride
+  int32_t* leaf_order_sym = nullptr;  // n_leaves: heaviest symmetric work first
   int32_t* leaf_order = nullptr;   // n_leaves: target leaves, most work first
   int32_t* leaf_box = nullptr;     // n_leaves: global box id of each leaf
   int32_t* box_parent = nullptr;   // n_boxes: parent box id (-1 for a root)
@@ -200,6 +211,8 @@ inline void stage_event(const fmm_tree* t, int s, bool end, cudaStream_t st) {
 void build_tree(fmm_tree* t, const double* pos, cudaStream_t st);
 // Separate source and target hierarchies (t->prm set on entry).
 void build_tree2(fmm_tree* t, const double* src, int64_t n_src, const double* trg, int64_t n_trg, cudaStream_t st);
+// symmetric.cu: symmetric near-field metadata of a one-point-set tree or batch
+void build_symmetric(fmm_tree* t, cudaStream_t st);
 // api.cu: releases every device array, stream and event of a tree
 void free_tree(fmm_tree* t);
 // merge.cu: a batch of trees as one tree-shaped object

@@ -19,11 +19,12 @@ constexpr double kInv4Pi = 0.079577471545947667884441881686257181;
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 // Knuth's two-sum: s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(real& s, real& e, real b) {
-  real a = s;
-  real t = a + b;
-  real bb = t - a;
-  real err = (a - (t - bb)) + (b - bb);
+template <class T>
+__device__ __forceinline__ void two_sum(T& s, T& e, T b) {
+  T a = s;
+  T t = a + b;
+  T bb = t - a;
+  T err = (a - (t - bb)) + (b - bb);
   s = t;
   e += err;
 }
@@ -478,6 +479,13 @@ struct P2PArgs {
   const int64_t* off;
   const P2PEntry* ent32;
   const float* thr;  // per entry: squared FP32 distance at or below which points coincide
+  // symmetric near field (one point set): per-leaf work entries, the slot of
+  // every entry (>= 0: evaluated for both sides) and the slots' sums
+  const int64_t* work_off;
+  const int32_t* work;
+  const int32_t* slot;
+  float* partial;
+  int stride;
   const int32_t* ent_src;
   const int64_t* box_start;
   const int32_t* box_count;
@@ -643,7 +651,8 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
 // a two-sum at the end.  Source leaves arrive by double-buffered 1D TMA bulk
 // copies completing on per-warp mbarriers.
 template <int TPL, bool FIELD>
-__global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_f32h(P2PArgs a) {
+__global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : ((TPL >= 8 || (FIELD && TPL >= 4)) ? 2 : 4))
+    p2p_kernel_f32h(P2PArgs a) {
   constexpr int CAP = TPL * 32;
   constexpr int WARPS = 4;
   constexpr int NT = 2 * TPL;
@@ -765,6 +774,241 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : 4) p2p_kernel_
           a.near_f[3 * pidx + 1] = fy[k];
           a.near_f[3 * pidx + 2] = fz[k];
         }
+      }
+    }
+  }
+}
+
+// ---- E6 (FP32, potential, one point set): symmetric near field ----------------
+// A leaf pair {A, B} listed in both directions is evaluated once, by the warp
+// of the smaller leaf A: every 1/r serves both q_B / r (A's potentials,
+// accumulated in registers) and q_A / r (B's potentials).  The second sums,
+// per source point of B, are reduced across the half-warp by a reduce-scatter
+// butterfly over chunks of 16 sources and stored to the pair's slot; the
+// local evaluation of leaf B adds its slots in list order.  The self pair and
+// pairs listed in one direction only are evaluated one-sided.  Lane layout
+// and staging as in p2p_kernel_f32h.
+template <int NPH>
+__device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* dst, int j0, int jstep, int scount) {
+  // after the stages with masks 8, 4, 2, 1 lane l16 holds the half-warp sum of P[l16]
+#pragma unroll
+  for (int m = 8; m >= 1; m >>= 1) {
+    const bool up = (l16 & m) != 0;
+#pragma unroll
+    for (int i = 0; i < m; i++) {
+      const float keep = up ? P[i + m] : P[i];
+      const float send = up ? P[i] : P[i + m];
+      P[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  const int j = j0 + jstep * l16;
+  if (j < scount) dst[j] = P[0];
+}
+
+// One chunk of 16 sources per half-warp of a symmetric pair: u of the lane's
+// targets in pu, and per source the lane's share of sum_i q_i / r in P.
+// FULL: all 32 sources of the chunk exist (no bounds checks).
+template <bool MASK, bool FULL, int NPH>
+__device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half, int scount, const f2 (&tx)[NPH],
+                                          const f2 (&ty)[NPH], const f2 (&tz)[NPH], const f2 (&tq)[NPH],
+                                          f2 (&pu)[NPH], float (&P)[16], float thr) {
+#pragma unroll
+  for (int jj = 0; jj < 16; jj++) {
+    const int j = c0 + 2 * jj + half;
+    P[jj] = 0.f;
+    if (FULL || j < scount) {
+      const ulonglong2 sa = s2[2 * j], sb = s2[2 * j + 1];
+      f2 acc = 0ull;
+#pragma unroll
+      for (int k = 0; k < NPH; k++) {
+        const f2 dx = f2sub(tx[k], sa.x), dy = f2sub(ty[k], sa.y), dz = f2sub(tz[k], sb.x);
+        const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+        float r0, r1;
+        f2unpack(r2, r0, r1);
+        float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
+        if (MASK) {
+          i0 = (r0 > thr) ? i0 : 0.f;
+          i1 = (r1 > thr) ? i1 : 0.f;
+        }
+        const f2 ri = f2pack(i0, i1);
+        pu[k] = f2fma(sb.y, ri, pu[k]);
+        acc = f2fma(tq[k], ri, acc);
+      }
+      float a0, a1;
+      f2unpack(acc, a0, a1);
+      P[jj] = a0 + a1;
+    }
+  }
+}
+
+template <int TPL>
+__global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_kernel_f32s(P2PArgs a) {
+  constexpr int CAP = TPL * 32;
+  constexpr int WARPS = 4;
+  constexpr int NT = 2 * TPL;
+  constexpr int NPH = TPL;
+  extern __shared__ __align__(128) unsigned char p2p_smem[];
+  DupRec (*sbuf)[2][CAP] = reinterpret_cast<DupRec (*)[2][CAP]>(p2p_smem);
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const DupRec* tile = reinterpret_cast<const DupRec*>(a.tile);
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int half = lane >> 4, l16 = lane & 15;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+  if (t >= a.n_leaves) return;
+  const int64_t leaf = a.order[t];
+  const int64_t g = a.leaf_box[leaf];
+  const int64_t tstart = a.box_start[g];
+  const int tcnt = a.box_count[g];
+  float tx0[NT], ty0[NT], tz0[NT], tq0[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const int i = l16 + 16 * k;
+    if (i < tcnt) {
+      const float4 p = reinterpret_cast<const float4*>(a.src)[tstart + i];
+      tx0[k] = p.x;
+      ty0[k] = p.y;
+      tz0[k] = p.z;
+      tq0[k] = p.w;
+    } else {
+      tx0[k] = ty0[k] = tz0[k] = tq0[k] = 0.f;
+    }
+  }
+  f2 tq[NPH];
+#pragma unroll
+  for (int k = 0; k < NPH; k++) tq[k] = f2pack(tq0[2 * k], tq0[2 * k + 1]);
+  float hi[NT], lo[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) hi[k] = lo[k] = 0.f;
+  const int64_t kb = a.work_off[leaf], ke = a.work_off[leaf + 1];
+  auto issue = [&](int64_t w, int buf) {
+    const int64_t gs = a.src_leaf_box[a.ent32[a.work[w]].src & 0x7fffffff];
+    if (lane == 0) {
+      fence_proxy_async();
+      tma_load_1d(sbuf[warp][buf], tile + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(DupRec)), &bar[buf]);
+    }
+  };
+  uint32_t phase = 0;
+  if (kb < ke) issue(kb, 0);
+  for (int64_t w = kb; w < ke; w++) {
+    const int buf = (int)((w - kb) & 1);
+    if (w + 1 < ke) issue(w + 1, buf ^ 1);
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      // copies still in flight into this warp's buffers must land first
+      mbar_wait(&bar[buf], (phase >> buf) & 1u);
+      if (w + 1 < ke) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      return;
+    }
+    phase ^= 1u << buf;
+    const int64_t e = a.work[w];
+    const P2PEntry en = a.ent32[e];
+    const int ls = en.src & 0x7fffffff;
+    const int scount = a.box_count[a.src_leaf_box[ls]];
+    const bool mask = (en.src < 0) || ls == (int)leaf;
+    const float thr = mask ? a.thr[e] : 0.f;
+    const int slot = a.slot[e];
+    const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
+    f2 tx[NPH], ty[NPH], tz[NPH], pu[NPH];
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      tx[k] = f2add(f2pack(tx0[2 * k], tx0[2 * k + 1]), ddx);
+      ty[k] = f2add(f2pack(ty0[2 * k], ty0[2 * k + 1]), ddy);
+      tz[k] = f2add(f2pack(tz0[2 * k], tz0[2 * k + 1]), ddz);
+      pu[k] = 0ull;
+    }
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sbuf[warp][buf]);
+    if (slot < 0) {
+      // one-sided: the self pair and pairs listed in one direction only
+      f2 px[NPH], py[NPH], pz[NPH];
+      if (mask) p2p_tile_f32h<true, false, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz, thr);
+      else p2p_tile_f32h<false, false, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz, thr);
+    } else {
+      float* dst = a.partial + (int64_t)slot * a.stride;
+      float P[16];
+      int c0 = 0;
+      for (; c0 + 32 <= scount; c0 += 32) {
+        if (mask) sym_chunk<true, true, NPH>(s2, c0, half, scount, tx, ty, tz, tq, pu, P, thr);
+        else sym_chunk<false, true, NPH>(s2, c0, half, scount, tx, ty, tz, tq, pu, P, thr);
+        butterfly_store<NPH>(P, l16, dst, c0 + half, 2, scount);
+      }
+      if (c0 < scount) {
+        if (mask) sym_chunk<true, false, NPH>(s2, c0, half, scount, tx, ty, tz, tq, pu, P, thr);
+        else sym_chunk<false, false, NPH>(s2, c0, half, scount, tx, ty, tz, tq, pu, P, thr);
+        butterfly_store<NPH>(P, l16, dst, c0 + half, 2, scount);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      float u0, u1;
+      f2unpack(pu[k], u0, u1);
+      two_sum(hi[2 * k], lo[2 * k], u0);
+      two_sum(hi[2 * k + 1], lo[2 * k + 1], u1);
+    }
+    __syncwarp();
+  }
+  // combine the two halves
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi[k], 16);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo[k], 16);
+    two_sum(hi[k], lo[k], oh);
+    lo[k] += ol;
+  }
+  if (half == 0) {
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+      const int i = l16 + 16 * k;
+      if (i < tcnt) {
+        const int64_t pidx = tstart + i;
+        a.near_u[2 * pidx] = hi[k];
+        a.near_u[2 * pidx + 1] = lo[k];
+      }
+    }
+  }
+}
+
+// Symmetric near field, second half: every leaf adds the slots it received
+// (sums computed by the warps of its lower partners) to its near-field sums,
+// in list order; warp per leaf, lanes over points.
+__global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
+                                                         const int64_t* __restrict__ box_start,
+                                                         const int32_t* __restrict__ box_count,
+                                                         const int64_t* __restrict__ recv_off,
+                                                         const int32_t* __restrict__ recv,
+                                                         const float* __restrict__ partial, int64_t stride,
+                                                         float* __restrict__ near_u) {
+  const int lane = lane_id();
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves; leaf += warps) {
+    const int64_t r0 = recv_off[leaf], r1 = recv_off[leaf + 1];
+    if (r0 == r1) continue;
+    const int64_t g = leaf_box[leaf];
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    for (int base = 0; base < cnt; base += 32) {  // warp-uniform
+      const int i = base + lane;
+      const bool ok = i < cnt;
+      float hi = ok ? near_u[2 * (start + i)] : 0.f, lo = ok ? near_u[2 * (start + i) + 1] : 0.f;
+      for (int64_t rb = r0; rb < r1; rb += 32) {
+        // up to 32 slots per round, fetched once and broadcast
+        const int nr = (int)min((int64_t)32, r1 - rb);
+        const int my = lane < nr ? recv[rb + lane] : 0;
+        for (int k = 0; k < nr; k++) {
+          const int slot = __shfl_sync(0xffffffffu, my, k);
+          if (ok) two_sum(hi, lo, partial[(int64_t)slot * stride + i]);
+        }
+      }
+      if (ok) {
+        near_u[2 * (start + i)] = hi;
+        near_u[2 * (start + i) + 1] = lo;
       }
     }
   }
@@ -907,8 +1151,12 @@ void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   stage_event(t, FMM_STAGE_M2M, true, st);
 }
 
-// M2L blocks per SM while the near field runs beside it: one M2L block
-// (4 warps, ~30K registers) leaves room for four near-field blocks.
+// Far field beside the near field (M2L and L2L on the tree's second stream
+// while P2P runs on the caller's stream) or after it on one stream.  Both are
+// FP32-issue bound, so overlap only pays while one of them cannot fill the
+// GPU; kM2LBlocksPerSM caps the M2L blocks per SM when they overlap (one
+// block, 4 warps and ~30K registers, leaves room for four near-field blocks).
+constexpr bool kOverlapFarField = true;
 constexpr int kM2LBlocksPerSM = 1;
 
 // Downward pass: M2L over the whole list, then L2L round by round (round r
@@ -928,7 +1176,7 @@ void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, m2l_kernel<P>, 128, smem));
   if (occ < 1) occ = 1;
-  if (occ > kM2LBlocksPerSM) occ = kM2LBlocksPerSM;
+  if (kOverlapFarField && occ > kM2LBlocksPerSM) occ = kM2LBlocksPerSM;
   int64_t blocks = (int64_t)nsm * occ;
   const int64_t need = (t->n_boxes + 3) / 4;
   if (blocks > need) blocks = need;
@@ -965,7 +1213,7 @@ void run_l2p(const fmm_tree* t, const Ptrs& pp, const real* near_u, const real* 
 template <int TPL>
 void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool field,
                  cudaStream_t st) {
-  P2PArgs a;
+  P2PArgs a{};
   a.n_leaves = t->n_leaves;
   a.leaf_box = t->leaf_box;
   a.src_leaf_box = t->src_leaf_box;
@@ -997,6 +1245,29 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       attr_set = true;
     }
     const int64_t blocks = (t->n_leaves + 3) / 4;
+    if (!field && t->sym) {
+      static bool sym_attr = false;
+      if (!sym_attr) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32s<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32s<TPL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared));
+        sym_attr = true;
+      }
+      a.order = t->leaf_order_sym;
+      a.work_off = t->sym_work_off;
+      a.work = t->sym_work;
+      a.slot = t->sym_slot;
+      a.partial = t->sym_partial;
+      a.stride = t->sym_stride;
+      p2p_kernel_f32s<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);
+      FMM_LAUNCH_CHECK();
+      sym_gather_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
+          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_recv, t->sym_partial,
+          (int64_t)t->sym_stride, reinterpret_cast<float*>(near_u));
+      FMM_LAUNCH_CHECK();
+      t->launches += 1;
+      return;
+    }
     if (field) p2p_kernel_f32h<TPL, true><<<(unsigned)blocks, 128, smem, st>>>(a);
     else p2p_kernel_f32h<TPL, false><<<(unsigned)blocks, 128, smem, st>>>(a);
     FMM_LAUNCH_CHECK();
@@ -1057,24 +1328,28 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
   stage_event(t, FMM_STAGE_SORT, true, st);
   real* near_u = reinterpret_cast<real*>(t->near_u);
   real* near_f = reinterpret_cast<real*>(t->near_f);
-  // upward pass on the caller's stream, then fork: M2L and L2L on the
+  // upward pass on the caller's stream; then either fork (M2L and L2L on the
   // tree's higher-priority stream beside the near field on the caller's
-  // stream; join before the local evaluation
+  // stream, joined before the local evaluation) or all on the caller's stream
   dispatch_p(t->prm.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
     run_upward<P>(t, pp, st);
   });
-  FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
-  FMM_CUDA_TRY(cudaStreamWaitEvent(t->far_stream, t->ev_fork, 0));
+  cudaStream_t far = st;
+  if (kOverlapFarField) {
+    FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(t->far_stream, t->ev_fork, 0));
+    far = t->far_stream;
+  }
   dispatch_p(t->prm.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
-    run_downward<P>(t, pp, t->far_stream);
+    run_downward<P>(t, pp, far);
   });
-  FMM_CUDA_TRY(cudaEventRecord(t->ev_join, t->far_stream));
+  if (kOverlapFarField) FMM_CUDA_TRY(cudaEventRecord(t->ev_join, far));
   stage_event(t, FMM_STAGE_P2P, false, st);
   run_p2p(t, pp, near_u, near_f, field != nullptr, st);
   stage_event(t, FMM_STAGE_P2P, true, st);
-  FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+  if (kOverlapFarField) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
   stage_event(t, FMM_STAGE_L2P, false, st);
   dispatch_p(t->prm.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;

@@ -238,6 +238,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   m->out_base = 0;
   m->n_src_leaves = NL;
   m->src_leaf_box = m->leaf_box;
+  build_symmetric(m, st);
   m->counters = dev_alloc<int>(m, 8);
   m->status = dev_alloc<int>(m, 1);
   FMM_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));

@@ -1378,6 +1378,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   try {
     march(t, side, side, st, steps, &p2p_t, &p2p_s, &np);
     finish_tree(t, steps, p2p_t, p2p_s, np, leaf_off, leaf_off, blo, bhi, t->has_duplicates, st);
+    build_symmetric(t, st);
   } catch (...) {
     cudaFree(blo), cudaFree(bhi);
     throw;
