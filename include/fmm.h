@@ -27,13 +27,12 @@
  *  - Every call returns an fmm_status; on failure fmm_last_error() gives a
  *    thread-local message.  Nothing throws or aborts.
  *  - A tree owns the device workspace its evaluations use (allocated once
- *    by fmm_build_tree) and a second, higher-priority CUDA stream: each
- *    evaluation forks its M2L and L2L stages onto it from the caller's
- *    stream and joins them back before its last stage, so the
- *    caller sees ordinary stream-ordered semantics (stream capture included).
- *    Evaluations of one tree must be ordered on one stream; two evaluations
- *    of the same tree in flight at once race.  Distinct trees are
- *    independent.
+ *    by fmm_build_tree).  Evaluations run their stages in order on the
+ *    caller's stream (stream capture included); the tree also holds a second,
+ *    higher-priority stream on which a build variant overlapping the far
+ *    field with the near field forks and joins M2L and L2L.  Evaluations of
+ *    one tree must be ordered on one stream; two evaluations of the same tree
+ *    in flight at once race.  Distinct trees are independent.
  */
 #ifndef GB300_FMM_H
 #define GB300_FMM_H
@@ -224,10 +223,8 @@ int fmm_tree_export(const fmm_tree* tree, int32_t* perm, int64_t* box_start,
 
 /* Per-stage device timing.  enable = 1 clears the record and starts
  * recording CUDA events at the start and end of every stage of the next
- * evaluation calls of this tree (on the stream each stage runs on: the
- * caller's stream for sort, P2M, M2M, P2P and L2P, the tree's second stream
- * for M2L and L2L, which overlap with P2P; up to 512 calls);
- * enable = 0 stops.
+ * evaluation calls of this tree (on the stream each stage runs on, up to 512
+ * calls); enable = 0 stops.
  * fmm_tree_stage_times synchronises the recorded events and writes the summed
  * milliseconds per stage (FMM_NUM_STAGES doubles, host) and the number of
  * recorded calls. */

@@ -84,6 +84,16 @@ struct __align__(32) DupRec {
   float x0, x1, y0, y1, z0, z1, q0, q1;
 };
 
+// One work entry of the symmetric near field, read with one coalesced load:
+// the source leaf's point range, the pair's slot (-1: one-sided), the FP32
+// centre offset c_T - c_S and the coincidence threshold (< 0: no masking).
+struct __align__(16) SymRec {
+  int64_t start;
+  int32_t count;
+  int32_t slot;
+  float dx, dy, dz, thr;
+};
+
 }  // namespace fmm
 
 struct fmm_tree {
@@ -123,6 +133,7 @@ struct fmm_tree {
   int64_t* sym_recv_off = nullptr;    // n_leaves + 1
   int32_t* sym_recv = nullptr;        // slots each leaf's local evaluation adds, list order
   float* sym_partial = nullptr;       // n_slots x sym_stride
+  fmm::SymRec* sym_rec = nullptr;     // per work entry, in work-list order
   int32_t* leaf_order_sym = nullptr;  // n_leaves: heaviest symmetric work first
   int32_t* leaf_order = nullptr;   // n_leaves: target leaves, most work first
   int32_t* leaf_box = nullptr;     // n_leaves: global box id of each leaf

@@ -479,11 +479,10 @@ struct P2PArgs {
   const int64_t* off;
   const P2PEntry* ent32;
   const float* thr;  // per entry: squared FP32 distance at or below which points coincide
-  // symmetric near field (one point set): per-leaf work entries, the slot of
-  // every entry (>= 0: evaluated for both sides) and the slots' sums
+  // symmetric near field (one point set): per-leaf work entries as records
+  // and the slots' sums
   const int64_t* work_off;
-  const int32_t* work;
-  const int32_t* slot;
+  const SymRec* rec;
   float* partial;
   int stride;
   const int32_t* ent_src;
@@ -887,34 +886,56 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
   float hi[NT], lo[NT];
 #pragma unroll
   for (int k = 0; k < NT; k++) hi[k] = lo[k] = 0.f;
-  const int64_t kb = a.work_off[leaf], ke = a.work_off[leaf + 1];
-  auto issue = [&](int64_t w, int buf) {
-    const int64_t gs = a.src_leaf_box[a.ent32[a.work[w]].src & 0x7fffffff];
+  const int64_t kb = a.work_off[leaf];
+  const int nwk = (int)(a.work_off[leaf + 1] - kb);
+  // work records: lane l holds the record of entry base + l of the current
+  // batch of 32; fields are broadcast per entry
+  SymRec mine{};
+  auto load_batch = [&](int base) {
+    if (base + lane < nwk) mine = a.rec[kb + base + lane];
+  };
+  auto bcast = [&](int src_lane) {
+    SymRec r;
+    r.start = __shfl_sync(0xffffffffu, mine.start, src_lane);
+    r.count = __shfl_sync(0xffffffffu, mine.count, src_lane);
+    r.slot = __shfl_sync(0xffffffffu, mine.slot, src_lane);
+    r.dx = __shfl_sync(0xffffffffu, mine.dx, src_lane);
+    r.dy = __shfl_sync(0xffffffffu, mine.dy, src_lane);
+    r.dz = __shfl_sync(0xffffffffu, mine.dz, src_lane);
+    r.thr = __shfl_sync(0xffffffffu, mine.thr, src_lane);
+    return r;
+  };
+  auto issue = [&](const SymRec& r, int buf) {
     if (lane == 0) {
       fence_proxy_async();
-      tma_load_1d(sbuf[warp][buf], tile + a.box_start[gs], (uint32_t)(a.box_count[gs] * sizeof(DupRec)), &bar[buf]);
+      tma_load_1d(sbuf[warp][buf], tile + r.start, (uint32_t)(r.count * sizeof(DupRec)), &bar[buf]);
     }
   };
   uint32_t phase = 0;
-  if (kb < ke) issue(kb, 0);
-  for (int64_t w = kb; w < ke; w++) {
-    const int buf = (int)((w - kb) & 1);
-    if (w + 1 < ke) issue(w + 1, buf ^ 1);
+  if (nwk > 0) {
+    load_batch(0);
+    issue(bcast(0), 0);
+  }
+  for (int w = 0; w < nwk; w++) {
+    const int buf = w & 1;
+    if (w > 0 && (w & 31) == 0) load_batch(w);  // warp-uniform
+    const SymRec en = bcast(w & 31);
+    if (w + 1 < nwk) {
+      const SymRec nx = ((w + 1) & 31) ? bcast((w + 1) & 31) : a.rec[kb + w + 1];
+      issue(nx, buf ^ 1);
+    }
     if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
       if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
       // copies still in flight into this warp's buffers must land first
       mbar_wait(&bar[buf], (phase >> buf) & 1u);
-      if (w + 1 < ke) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
       return;
     }
     phase ^= 1u << buf;
-    const int64_t e = a.work[w];
-    const P2PEntry en = a.ent32[e];
-    const int ls = en.src & 0x7fffffff;
-    const int scount = a.box_count[a.src_leaf_box[ls]];
-    const bool mask = (en.src < 0) || ls == (int)leaf;
-    const float thr = mask ? a.thr[e] : 0.f;
-    const int slot = a.slot[e];
+    const int scount = en.count;
+    const bool mask = en.thr >= 0.f;
+    const float thr = en.thr;
+    const int slot = en.slot;
     const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
     f2 tx[NPH], ty[NPH], tz[NPH], pu[NPH];
 #pragma unroll
@@ -1001,9 +1022,17 @@ __global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_leaves, const
         // up to 32 slots per round, fetched once and broadcast
         const int nr = (int)min((int64_t)32, r1 - rb);
         const int my = lane < nr ? recv[rb + lane] : 0;
-        for (int k = 0; k < nr; k++) {
-          const int slot = __shfl_sync(0xffffffffu, my, k);
-          if (ok) two_sum(hi, lo, partial[(int64_t)slot * stride + i]);
+        for (int k0 = 0; k0 < nr; k0 += 8) {
+          // eight independent loads in flight, then the ordered sums
+          float v[8];
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            const int slot = __shfl_sync(0xffffffffu, my, (k0 + k) & 31);
+            v[k] = (ok && k0 + k < nr) ? partial[(int64_t)slot * stride + i] : 0.f;
+          }
+#pragma unroll
+          for (int k = 0; k < 8; k++)
+            if (k0 + k < nr) two_sum(hi, lo, v[k]);
         }
       }
       if (ok) {
@@ -1152,11 +1181,13 @@ void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 }
 
 // Far field beside the near field (M2L and L2L on the tree's second stream
-// while P2P runs on the caller's stream) or after it on one stream.  Both are
-// FP32-issue bound, so overlap only pays while one of them cannot fill the
-// GPU; kM2LBlocksPerSM caps the M2L blocks per SM when they overlap (one
-// block, 4 warps and ~30K registers, leaves room for four near-field blocks).
-constexpr bool kOverlapFarField = true;
+// while P2P runs on the caller's stream) or before it on one stream.  Both
+// are FP32-issue bound: on the 2^20-point cube the serial order took 2.43 ms
+// per evaluation against 2.53-2.70 ms overlapped (M2L at 1-3 blocks per SM
+// beside the symmetric near field), so the stages run in order and M2L gets
+// every SM at full occupancy.  kM2LBlocksPerSM caps the M2L blocks per SM
+// when they overlap.
+constexpr bool kOverlapFarField = false;
 constexpr int kM2LBlocksPerSM = 1;
 
 // Downward pass: M2L over the whole list, then L2L round by round (round r
@@ -1255,8 +1286,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       }
       a.order = t->leaf_order_sym;
       a.work_off = t->sym_work_off;
-      a.work = t->sym_work;
-      a.slot = t->sym_slot;
+      a.rec = t->sym_rec;
       a.partial = t->sym_partial;
       a.stride = t->sym_stride;
       p2p_kernel_f32s<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);

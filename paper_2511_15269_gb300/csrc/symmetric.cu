@@ -3,10 +3,10 @@
 // level march is not (ties advance one side), so a leaf pair can sit in the
 // near field in one direction only.  Per entry (target leaf l, source leaf s)
 // of the near-field list (sorted by source within each leaf):
-//   * s > l and (s, l) is listed too: a symmetric pair.  The warp of l
+//   * (s, l) is listed too and l owns the pair (see owner()): the warp of l
 //     evaluates it once and leaves the sums q_l / r at s's points in a slot;
-//   * s < l and (s, l) is listed: received.  Leaf s's warp computes it; the
-//     local evaluation of l adds the slot;
+//   * (s, l) is listed and s owns the pair: received.  Leaf s's warp computes
+//     it; the gather before the local evaluation of l adds the slot;
 //   * anything else (the self pair, pairs listed in one direction only):
 //     evaluated one-sided by the warp of l, as in the one-sided kernel.
 // All orders are fixed, so results do not depend on scheduling.
@@ -27,8 +27,17 @@ __device__ __forceinline__ int64_t find_src(const int32_t* __restrict__ src, int
   return lo;
 }
 
+// Which leaf evaluates a pair listed both ways: the one with the shorter
+// list (ties: the smaller index), so leaves with very long lists (boxes
+// around outliers, whose bounding boxes are large) hand their pairs to their
+// partners and no single warp becomes the long pole.
+__device__ __forceinline__ bool owner(const int64_t* __restrict__ off, int32_t l, int32_t s) {
+  const int64_t nl = off[l + 1] - off[l], ns = off[s + 1] - off[s];
+  return nl < ns || (nl == ns && l < s);
+}
+
 // mirror entry index of every entry (-1: not listed the other way), and the
-// flag of the upper entries that own a slot
+// flag of the entries whose leaf owns the pair (and a slot)
 __global__ void mirror_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int32_t* __restrict__ src,
                               int64_t* __restrict__ mirror, int64_t* __restrict__ owns) {
   const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
@@ -41,7 +50,7 @@ __global__ void mirror_kernel(int64_t n_leaves, const int64_t* __restrict__ off,
         if (f < off[s + 1] && src[f] == (int32_t)l) m = f;
       }
       mirror[e] = m;
-      owns[e] = (m >= 0 && s > (int32_t)l) ? 1 : 0;
+      owns[e] = (m >= 0 && owner(off, (int32_t)l, s)) ? 1 : 0;
     }
   }
 }
@@ -61,7 +70,7 @@ __global__ void slot_kernel(int64_t n_leaves, const int64_t* __restrict__ off, c
       if (owns[e]) {
         slot[e] = (int32_t)slot_scan[e];
         w++;
-      } else if (m >= 0 && src[e] < (int32_t)l) {
+      } else if (m >= 0) {  // the partner owns the pair
         slot[e] = (int32_t)slot_scan[m];
         r++;
       } else {
@@ -75,7 +84,7 @@ __global__ void slot_kernel(int64_t n_leaves, const int64_t* __restrict__ off, c
 }
 
 // work entries (list order) and received slots (list order) per leaf
-__global__ void fill_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int32_t* __restrict__ src,
+__global__ void fill_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int64_t* __restrict__ owns,
                             const int32_t* __restrict__ slot, const int64_t* __restrict__ work_off,
                             const int64_t* __restrict__ recv_off, int32_t* __restrict__ work,
                             int32_t* __restrict__ recv) {
@@ -83,8 +92,27 @@ __global__ void fill_kernel(int64_t n_leaves, const int64_t* __restrict__ off, c
        l += (int64_t)gridDim.x * blockDim.x) {
     int64_t w = work_off[l], r = recv_off[l];
     for (int64_t e = off[l]; e < off[l + 1]; e++) {
-      if (slot[e] >= 0 && src[e] < (int32_t)l) recv[r++] = slot[e];
+      if (slot[e] >= 0 && !owns[e]) recv[r++] = slot[e];
       else work[w++] = (int32_t)e;
+    }
+  }
+}
+
+// one record per work entry (see SymRec)
+__global__ void rec_kernel(int64_t n_leaves, const int64_t* __restrict__ work_off, const int32_t* __restrict__ work,
+                           const P2PEntry* __restrict__ ent, const float* __restrict__ thr,
+                           const int32_t* __restrict__ slot, const int32_t* __restrict__ src_leaf_box,
+                           const int64_t* __restrict__ box_start, const int32_t* __restrict__ box_count,
+                           SymRec* __restrict__ rec) {
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; l < n_leaves; l += warps) {
+    for (int64_t k = work_off[l] + (threadIdx.x & 31); k < work_off[l + 1]; k += 32) {
+      const int64_t e = work[k];
+      const P2PEntry en = ent[e];
+      const int ls = en.src & 0x7fffffff;
+      const int64_t gs = src_leaf_box[ls];
+      const bool mask = en.src < 0 || ls == (int)l;
+      rec[k] = SymRec{box_start[gs], box_count[gs], slot[e], en.dx, en.dy, en.dz, mask ? thr[e] : -1.f};
     }
   }
 }
@@ -124,8 +152,13 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
   const int64_t nr = exclusive_scan(n_recv, t->sym_recv_off, NL + 1, st);
   t->sym_work = dev_alloc<int32_t>(t, std::max<int64_t>(nw, 1));
   t->sym_recv = dev_alloc<int32_t>(t, std::max<int64_t>(nr, 1));
-  fill_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->p2p_off, t->p2p_src, t->sym_slot, t->sym_work_off,
+  fill_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->p2p_off, owns, t->sym_slot, t->sym_work_off,
                                                  t->sym_recv_off, t->sym_work, t->sym_recv);
+  FMM_LAUNCH_CHECK();
+  t->sym_rec = dev_alloc<SymRec>(t, std::max<int64_t>(nw, 1));
+  rec_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->sym_work_off, t->sym_work, t->p2p32, t->p2p_thr,
+                                                     t->sym_slot, t->src_leaf_box, t->box_start, t->box_count,
+                                                     t->sym_rec);
   FMM_LAUNCH_CHECK();
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
   cudaFree(mirror), cudaFree(owns), cudaFree(slot_scan), cudaFree(n_work), cudaFree(n_recv);
