@@ -62,7 +62,7 @@ void free_tree(fmm_tree* t) {
                   t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
                   t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->down_ids,
                   t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr, t->sym_slot, t->sym_work_off,
-                  t->sym_work, t->sym_recv_off, t->sym_recv, t->sym_partial, t->leaf_order_sym, t->sym_rec};
+                  t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->prof_ev) {

@@ -127,11 +127,10 @@ struct fmm_tree {
   int sym = 0;
   int64_t n_slots = 0;                // leaf pairs evaluated once for both sides
   int sym_stride = 0;                 // floats per slot (>= largest leaf)
-  int32_t* sym_slot = nullptr;        // n_p2p: slot of a symmetric or received entry, else -1
+  int32_t* sym_slot = nullptr;        // n_p2p: slot of a pair evaluated for both sides, else -1
   int64_t* sym_work_off = nullptr;    // n_leaves + 1
   int32_t* sym_work = nullptr;        // entries each leaf's warp evaluates, list order
-  int64_t* sym_recv_off = nullptr;    // n_leaves + 1
-  int32_t* sym_recv = nullptr;        // slots each leaf's local evaluation adds, list order
+  int64_t* sym_recv_off = nullptr;    // n_leaves + 1: the slots each leaf receives (contiguous)
   float* sym_partial = nullptr;       // n_slots x sym_stride
   fmm::SymRec* sym_rec = nullptr;     // per work entry, in work-list order
   int32_t* leaf_order_sym = nullptr;  // n_leaves: heaviest symmetric work first

@@ -807,10 +807,17 @@ __device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* 
 // One chunk of 16 sources per half-warp of a symmetric pair: u of the lane's
 // targets in pu, and per source the lane's share of sum_i q_i / r in P.
 // FULL: all 32 sources of the chunk exist (no bounds checks).
+// Two accumulator sets for the targets' sums (even and odd sources) shorten
+// the dependency chain of the accumulating FMAs.
+constexpr bool kSymDualAcc = false;
+
 template <bool MASK, bool FULL, int NPH>
 __device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half, int scount, const f2 (&tx)[NPH],
                                           const f2 (&ty)[NPH], const f2 (&tz)[NPH], const f2 (&tq)[NPH],
                                           f2 (&pu)[NPH], float (&P)[16], float thr) {
+  f2 pu2[NPH];
+#pragma unroll
+  for (int k = 0; k < NPH; k++) pu2[k] = 0ull;
 #pragma unroll
   for (int jj = 0; jj < 16; jj++) {
     const int j = c0 + 2 * jj + half;
@@ -830,13 +837,18 @@ __device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half
           i1 = (r1 > thr) ? i1 : 0.f;
         }
         const f2 ri = f2pack(i0, i1);
-        pu[k] = f2fma(sb.y, ri, pu[k]);
+        if (kSymDualAcc && (jj & 1)) pu2[k] = f2fma(sb.y, ri, pu2[k]);
+        else pu[k] = f2fma(sb.y, ri, pu[k]);
         acc = f2fma(tq[k], ri, acc);
       }
       float a0, a1;
       f2unpack(acc, a0, a1);
       P[jj] = a0 + a1;
     }
+  }
+  if (kSymDualAcc) {
+#pragma unroll
+    for (int k = 0; k < NPH; k++) pu[k] = f2add(pu[k], pu2[k]);
   }
 }
 
@@ -997,13 +1009,13 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
 }
 
 // Symmetric near field, second half: every leaf adds the slots it received
-// (sums computed by the warps of its lower partners) to its near-field sums,
-// in list order; warp per leaf, lanes over points.
+// (sums computed by the warps of its partners; contiguous, in list order) to
+// its near-field sums.  Warp per leaf, each lane two points, eight slots'
+// loads in flight per point.
 __global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
                                                          const int64_t* __restrict__ box_start,
                                                          const int32_t* __restrict__ box_count,
                                                          const int64_t* __restrict__ recv_off,
-                                                         const int32_t* __restrict__ recv,
                                                          const float* __restrict__ partial, int64_t stride,
                                                          float* __restrict__ near_u) {
   const int lane = lane_id();
@@ -1014,30 +1026,35 @@ __global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_leaves, const
     const int64_t g = leaf_box[leaf];
     const int64_t start = box_start[g];
     const int cnt = box_count[g];
-    for (int base = 0; base < cnt; base += 32) {  // warp-uniform
-      const int i = base + lane;
-      const bool ok = i < cnt;
-      float hi = ok ? near_u[2 * (start + i)] : 0.f, lo = ok ? near_u[2 * (start + i) + 1] : 0.f;
-      for (int64_t rb = r0; rb < r1; rb += 32) {
-        // up to 32 slots per round, fetched once and broadcast
-        const int nr = (int)min((int64_t)32, r1 - rb);
-        const int my = lane < nr ? recv[rb + lane] : 0;
-        for (int k0 = 0; k0 < nr; k0 += 8) {
-          // eight independent loads in flight, then the ordered sums
-          float v[8];
+    for (int base = 0; base < cnt; base += 64) {
+      const int i0 = base + lane, i1 = base + 32 + lane;
+      const bool ok0 = i0 < cnt, ok1 = i1 < cnt;
+      float h0 = ok0 ? near_u[2 * (start + i0)] : 0.f, l0 = ok0 ? near_u[2 * (start + i0) + 1] : 0.f;
+      float h1 = ok1 ? near_u[2 * (start + i1)] : 0.f, l1 = ok1 ? near_u[2 * (start + i1) + 1] : 0.f;
+      for (int64_t r = r0; r < r1; r += 8) {
+        float v0[8], v1[8];
 #pragma unroll
-          for (int k = 0; k < 8; k++) {
-            const int slot = __shfl_sync(0xffffffffu, my, (k0 + k) & 31);
-            v[k] = (ok && k0 + k < nr) ? partial[(int64_t)slot * stride + i] : 0.f;
+        for (int k = 0; k < 8; k++) {
+          const bool in = r + k < r1;
+          const float* row = partial + (r + k) * stride;
+          v0[k] = (in && ok0) ? row[i0] : 0.f;
+          v1[k] = (in && ok1) ? row[i1] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          if (r + k < r1) {
+            two_sum(h0, l0, v0[k]);
+            two_sum(h1, l1, v1[k]);
           }
-#pragma unroll
-          for (int k = 0; k < 8; k++)
-            if (k0 + k < nr) two_sum(hi, lo, v[k]);
         }
       }
-      if (ok) {
-        near_u[2 * (start + i)] = hi;
-        near_u[2 * (start + i) + 1] = lo;
+      if (ok0) {
+        near_u[2 * (start + i0)] = h0;
+        near_u[2 * (start + i0) + 1] = l0;
+      }
+      if (ok1) {
+        near_u[2 * (start + i1)] = h1;
+        near_u[2 * (start + i1) + 1] = l1;
       }
     }
   }
@@ -1292,7 +1309,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       p2p_kernel_f32s<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
       sym_gather_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_recv, t->sym_partial,
+          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_partial,
           (int64_t)t->sym_stride, reinterpret_cast<float*>(near_u));
       FMM_LAUNCH_CHECK();
       t->launches += 1;

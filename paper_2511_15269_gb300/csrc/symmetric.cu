@@ -55,45 +55,42 @@ __global__ void mirror_kernel(int64_t n_leaves, const int64_t* __restrict__ off,
   }
 }
 
-// slot of every entry: owners get theirs from the scan, received entries the
-// slot of their mirror, the rest -1; per-leaf counts of work and received
-// entries
-__global__ void slot_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int32_t* __restrict__ src,
-                            const int64_t* __restrict__ mirror, const int64_t* __restrict__ owns,
-                            const int64_t* __restrict__ slot_scan, int32_t* __restrict__ slot,
-                            int64_t* __restrict__ n_work, int64_t* __restrict__ n_recv) {
+// per leaf: entries its warp evaluates (owned pairs and one-sided entries)
+// and entries it receives (pairs owned by the partner)
+__global__ void count_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int64_t* __restrict__ mirror,
+                             const int64_t* __restrict__ owns, int64_t* __restrict__ n_work,
+                             int64_t* __restrict__ n_recv) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n_leaves;
        l += (int64_t)gridDim.x * blockDim.x) {
     int64_t w = 0, r = 0;
     for (int64_t e = off[l]; e < off[l + 1]; e++) {
-      const int64_t m = mirror[e];
-      if (owns[e]) {
-        slot[e] = (int32_t)slot_scan[e];
-        w++;
-      } else if (m >= 0) {  // the partner owns the pair
-        slot[e] = (int32_t)slot_scan[m];
-        r++;
-      } else {
-        slot[e] = -1;
-        w++;
-      }
+      if (!owns[e] && mirror[e] >= 0) r++;
+      else w++;
     }
     n_work[l] = w;
     n_recv[l] = r;
   }
 }
 
-// work entries (list order) and received slots (list order) per leaf
-__global__ void fill_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int64_t* __restrict__ owns,
-                            const int32_t* __restrict__ slot, const int64_t* __restrict__ work_off,
+// Work entries in list order, and slots: a received entry's slot is its
+// position in the receivers' concatenated lists, so the slots a leaf adds are
+// contiguous; the owning entry (its mirror) writes to the same slot.
+__global__ void fill_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int64_t* __restrict__ mirror,
+                            const int64_t* __restrict__ owns, const int64_t* __restrict__ work_off,
                             const int64_t* __restrict__ recv_off, int32_t* __restrict__ work,
-                            int32_t* __restrict__ recv) {
+                            int32_t* __restrict__ slot) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n_leaves;
        l += (int64_t)gridDim.x * blockDim.x) {
     int64_t w = work_off[l], r = recv_off[l];
     for (int64_t e = off[l]; e < off[l + 1]; e++) {
-      if (slot[e] >= 0 && !owns[e]) recv[r++] = slot[e];
-      else work[w++] = (int32_t)e;
+      if (!owns[e] && mirror[e] >= 0) {
+        slot[e] = (int32_t)r;
+        slot[mirror[e]] = (int32_t)r;
+        r++;
+      } else {
+        if (!owns[e]) slot[e] = -1;
+        work[w++] = (int32_t)e;
+      }
     }
   }
 }
@@ -132,28 +129,24 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
   require(NE < ((int64_t)1 << 31), "near-field list too long for the symmetric kernel");
   const int64_t NE1 = std::max<int64_t>(NE, 1);
   int64_t* mirror = scratch_alloc<int64_t>(NE1);
-  int64_t* owns = scratch_alloc<int64_t>(NE1 + 1);
-  int64_t* slot_scan = scratch_alloc<int64_t>(NE1 + 1);
+  int64_t* owns = scratch_alloc<int64_t>(NE1);
   int64_t* n_work = scratch_alloc<int64_t>(NL + 1);
   int64_t* n_recv = scratch_alloc<int64_t>(NL + 1);
-  FMM_CUDA_TRY(cudaMemsetAsync(owns, 0, sizeof(int64_t) * (NE1 + 1), st));
   FMM_CUDA_TRY(cudaMemsetAsync(n_work + NL, 0, sizeof(int64_t), st));
   FMM_CUDA_TRY(cudaMemsetAsync(n_recv + NL, 0, sizeof(int64_t), st));
   mirror_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->p2p_off, t->p2p_src, mirror, owns);
   FMM_LAUNCH_CHECK();
-  t->n_slots = exclusive_scan(owns, slot_scan, NE + 1, st);
-  t->sym_slot = dev_alloc<int32_t>(t, NE1);
-  slot_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->p2p_off, t->p2p_src, mirror, owns, slot_scan, t->sym_slot,
-                                                 n_work, n_recv);
+  count_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->p2p_off, mirror, owns, n_work, n_recv);
   FMM_LAUNCH_CHECK();
   t->sym_work_off = dev_alloc<int64_t>(t, NL + 1);
   t->sym_recv_off = dev_alloc<int64_t>(t, NL + 1);
   const int64_t nw = exclusive_scan(n_work, t->sym_work_off, NL + 1, st);
-  const int64_t nr = exclusive_scan(n_recv, t->sym_recv_off, NL + 1, st);
+  t->n_slots = exclusive_scan(n_recv, t->sym_recv_off, NL + 1, st);
+  require(t->n_slots < ((int64_t)1 << 31), "too many symmetric pairs");
+  t->sym_slot = dev_alloc<int32_t>(t, NE1);
   t->sym_work = dev_alloc<int32_t>(t, std::max<int64_t>(nw, 1));
-  t->sym_recv = dev_alloc<int32_t>(t, std::max<int64_t>(nr, 1));
-  fill_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->p2p_off, owns, t->sym_slot, t->sym_work_off,
-                                                 t->sym_recv_off, t->sym_work, t->sym_recv);
+  fill_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->p2p_off, mirror, owns, t->sym_work_off, t->sym_recv_off,
+                                                 t->sym_work, t->sym_slot);
   FMM_LAUNCH_CHECK();
   t->sym_rec = dev_alloc<SymRec>(t, std::max<int64_t>(nw, 1));
   rec_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->sym_work_off, t->sym_work, t->p2p32, t->p2p_thr,
@@ -161,7 +154,7 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
                                                      t->sym_rec);
   FMM_LAUNCH_CHECK();
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  cudaFree(mirror), cudaFree(owns), cudaFree(slot_scan), cudaFree(n_work), cudaFree(n_recv);
+  cudaFree(mirror), cudaFree(owns), cudaFree(n_work), cudaFree(n_recv);
   t->sym_stride = std::max(t->max_leaf, 1);
   t->sym_partial = dev_alloc<float>(t, std::max<int64_t>(t->n_slots, 1) * t->sym_stride);
 
