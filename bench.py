@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpoints/s per FMM eval at 1M pts, FP32 vs FP64 at stated error; bwd/fwd ratio"
 WORKLOAD = "cube1m_p8"
 FP32_FLOPS_PER_PAIR = 10  # potential, per ordered pair: 3 sub, 5 for r^2, 2 for the accumulating FMA
+# DRAM bytes (read + write) of one launch of the symmetric near-field kernel on
+# this workload, from the ncu capture in profiles/p2p_kernel_f32s_dram_cube1m_p8.md
+# (100.51 MB read + 231.45 MB write); None once the kernel changes.
+P2P_TRAFFIC_BYTES = 331.96e6
 SMS = 152
 FP32_LANES = 128
 
@@ -400,7 +404,7 @@ def main():
     achieved = pairs * FP32_FLOPS_PER_PAIR / p2p_s / 1e12
     roofline = {"bound": "alu", "kernel": "p2p_kernel_f32s (symmetric near field, FP32 + MUFU rsqrt)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                "traffic": None,
+                "traffic": P2P_TRAFFIC_BYTES if n == 1 << 20 else None,
                 "peak_source": "measured: fmm_device_peaks FP32 FMA probe (scalar %.1f, packed %.1f TFLOP/s); "
                                "derived 152 SMs x 128 lanes x 2 x %.0f MHz = %.1f"
                                % (peaks["fp32_fma_tflops"], peaks["fp32x2_fma_tflops"], clk, derived_tflops),

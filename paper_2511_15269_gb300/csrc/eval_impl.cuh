@@ -807,17 +807,10 @@ __device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* 
 // One chunk of 16 sources per half-warp of a symmetric pair: u of the lane's
 // targets in pu, and per source the lane's share of sum_i q_i / r in P.
 // FULL: all 32 sources of the chunk exist (no bounds checks).
-// Two accumulator sets for the targets' sums (even and odd sources) shorten
-// the dependency chain of the accumulating FMAs.
-constexpr bool kSymDualAcc = false;
-
 template <bool MASK, bool FULL, int NPH>
 __device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half, int scount, const f2 (&tx)[NPH],
                                           const f2 (&ty)[NPH], const f2 (&tz)[NPH], const f2 (&tq)[NPH],
                                           f2 (&pu)[NPH], float (&P)[16], float thr) {
-  f2 pu2[NPH];
-#pragma unroll
-  for (int k = 0; k < NPH; k++) pu2[k] = 0ull;
 #pragma unroll
   for (int jj = 0; jj < 16; jj++) {
     const int j = c0 + 2 * jj + half;
@@ -837,18 +830,13 @@ __device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half
           i1 = (r1 > thr) ? i1 : 0.f;
         }
         const f2 ri = f2pack(i0, i1);
-        if (kSymDualAcc && (jj & 1)) pu2[k] = f2fma(sb.y, ri, pu2[k]);
-        else pu[k] = f2fma(sb.y, ri, pu[k]);
+        pu[k] = f2fma(sb.y, ri, pu[k]);
         acc = f2fma(tq[k], ri, acc);
       }
       float a0, a1;
       f2unpack(acc, a0, a1);
       P[jj] = a0 + a1;
     }
-  }
-  if (kSymDualAcc) {
-#pragma unroll
-    for (int k = 0; k < NPH; k++) pu[k] = f2add(pu[k], pu2[k]);
   }
 }
 
