@@ -131,7 +131,7 @@ struct fmm_tree {
   int64_t* sym_work_off = nullptr;    // n_leaves + 1
   int32_t* sym_work = nullptr;        // entries each leaf's warp evaluates, list order
   int64_t* sym_recv_off = nullptr;    // n_leaves + 1: the slots each leaf receives (contiguous)
-  float* sym_partial = nullptr;       // n_slots x sym_stride
+  double* sym_partial = nullptr;      // n_slots x sym_stride (read as float by the FP32C path)
   fmm::SymRec* sym_rec = nullptr;     // per work entry, in work-list order
   int32_t* leaf_order_sym = nullptr;  // n_leaves: heaviest symmetric work first
   int32_t* leaf_order = nullptr;   // n_leaves: target leaves, most work first

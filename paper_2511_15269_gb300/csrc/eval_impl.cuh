@@ -483,7 +483,7 @@ struct P2PArgs {
   // and the slots' sums
   const int64_t* work_off;
   const SymRec* rec;
-  float* partial;
+  void* partial;  // float (FP32C) or double (FP64) slot sums
   int stride;
   const int32_t* ent_src;
   const int64_t* box_start;
@@ -952,7 +952,7 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
       if (mask) p2p_tile_f32h<true, false, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz, thr);
       else p2p_tile_f32h<false, false, NPH>(sbuf[warp][buf], scount, half, tx, ty, tz, pu, px, py, pz, thr);
     } else {
-      float* dst = a.partial + (int64_t)slot * a.stride;
+      float* dst = reinterpret_cast<float*>(a.partial) + (int64_t)slot * a.stride;
       float P[16];
       int c0 = 0;
       for (; c0 + 32 <= scount; c0 += 32) {
@@ -1044,6 +1044,197 @@ __global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_leaves, const
         near_u[2 * (start + i1)] = h1;
         near_u[2 * (start + i1) + 1] = l1;
       }
+    }
+  }
+}
+
+// ---- E6 (FP64, potential, one point set): symmetric near field ----------------
+// As p2p_kernel_f32s, in FP64 on absolute positions: a warp per leaf, lane l
+// holds targets l + 32 k; pairs listed both ways are evaluated once and the
+// sources' sums q_i / r are reduced over the warp in chunks of 16 sources
+// (reduce-scatter butterfly on lane bits 4..1, then the lane pair).  1/r is an
+// FP32 MUFU seed refined by one Newton step, y (3/2 - r^2 y^2 / 2): relative
+// error about 1.5 e^2 with e the seed's error (~2^-23), so near 3e-14.
+__device__ __forceinline__ double rsqrt_f64(double r2) {
+  double y = (double)rsqrt_mufu((float)r2);
+  const double h = 0.5 * r2;
+  y = y * fma(-h * y, y, 1.5);
+  if (!(r2 >= 1e-30 && r2 <= 1e30)) y = (r2 > 0.0) ? 1.0 / sqrt(r2) : 0.0;
+  return y;
+}
+
+template <int TPL>
+__global__ void __launch_bounds__(128) p2p_kernel_f64s(P2PArgs a) {
+  constexpr int CAP = TPL * 32;
+  constexpr int WARPS = 4;
+  extern __shared__ __align__(128) unsigned char p2p_smem[];
+  dvec4 (*sbuf)[2][CAP] = reinterpret_cast<dvec4 (*)[2][CAP]>(p2p_smem);
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const dvec4* tile = reinterpret_cast<const dvec4*>(a.tile);
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+  if (t >= a.n_leaves) return;
+  const int64_t leaf = a.order[t];
+  const int64_t g = a.leaf_box[leaf];
+  const int64_t tstart = a.box_start[g];
+  const int tcnt = a.box_count[g];
+  const dvec4* tsrc = reinterpret_cast<const dvec4*>(a.src);
+  double tx[TPL], ty[TPL], tz[TPL], tq[TPL], u[TPL];
+#pragma unroll
+  for (int k = 0; k < TPL; k++) {
+    const int i = lane + 32 * k;
+    if (i < tcnt) {
+      const dvec4 p = tsrc[tstart + i];
+      tx[k] = p.x;
+      ty[k] = p.y;
+      tz[k] = p.z;
+      tq[k] = p.w;
+    } else {
+      tx[k] = ty[k] = tz[k] = tq[k] = 0.0;
+    }
+    u[k] = 0.0;
+  }
+  const int64_t kb = a.work_off[leaf];
+  const int nwk = (int)(a.work_off[leaf + 1] - kb);
+  SymRec mine{};
+  auto load_batch = [&](int base) {
+    if (base + lane < nwk) mine = a.rec[kb + base + lane];
+  };
+  auto bcast = [&](int src_lane) {
+    SymRec r;
+    r.start = __shfl_sync(0xffffffffu, mine.start, src_lane);
+    r.count = __shfl_sync(0xffffffffu, mine.count, src_lane);
+    r.slot = __shfl_sync(0xffffffffu, mine.slot, src_lane);
+    r.thr = __shfl_sync(0xffffffffu, mine.thr, src_lane);
+    return r;
+  };
+  auto issue = [&](const SymRec& r, int buf) {
+    if (lane == 0) {
+      fence_proxy_async();
+      tma_load_1d(sbuf[warp][buf], tile + r.start, (uint32_t)(r.count * sizeof(dvec4)), &bar[buf]);
+    }
+  };
+  uint32_t phase = 0;
+  if (nwk > 0) {
+    load_batch(0);
+    issue(bcast(0), 0);
+  }
+  for (int w = 0; w < nwk; w++) {
+    const int buf = w & 1;
+    if (w > 0 && (w & 31) == 0) load_batch(w);  // warp-uniform
+    const SymRec en = bcast(w & 31);
+    if (w + 1 < nwk) {
+      const SymRec nx = ((w + 1) & 31) ? bcast((w + 1) & 31) : a.rec[kb + w + 1];
+      issue(nx, buf ^ 1);
+    }
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      // copies still in flight into this warp's buffers must land first
+      mbar_wait(&bar[buf], (phase >> buf) & 1u);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      return;
+    }
+    phase ^= 1u << buf;
+    const int scount = en.count;
+    const bool mask = en.thr >= 0.f;  // coincident points possible: exact zero test
+    const dvec4* sb = sbuf[warp][buf];
+    if (en.slot < 0) {
+      // one-sided: the self pair and pairs listed in one direction only
+#pragma unroll 2
+      for (int j = 0; j < scount; j++) {
+        const dvec4 s = sb[j];
+#pragma unroll
+        for (int k = 0; k < TPL; k++) {
+          const double dx = tx[k] - s.x, dy = ty[k] - s.y, dz = tz[k] - s.z;
+          const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+          double ri = rsqrt_f64(r2);
+          if (mask) ri = (r2 > 0.0) ? ri : 0.0;
+          u[k] = fma(s.w, ri, u[k]);
+        }
+      }
+    } else {
+      double* dst = reinterpret_cast<double*>(a.partial) + (int64_t)en.slot * a.stride;
+      for (int c0 = 0; c0 < scount; c0 += 16) {
+        double P[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; jj++) {
+          const int j = c0 + jj;
+          P[jj] = 0.0;
+          if (j < scount) {
+            const dvec4 s = sb[j];
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < TPL; k++) {
+              const double dx = tx[k] - s.x, dy = ty[k] - s.y, dz = tz[k] - s.z;
+              const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+              double ri = rsqrt_f64(r2);
+              if (mask) ri = (r2 > 0.0) ? ri : 0.0;
+              u[k] = fma(s.w, ri, u[k]);
+              acc = fma(tq[k], ri, acc);
+            }
+            P[jj] = acc;
+          }
+        }
+        // reduce-scatter over lane bits 4..1: lane l ends with P[l >> 1]
+#pragma unroll
+        for (int m = 16, h = 8; h >= 1; m >>= 1, h >>= 1) {
+          const bool up = (lane & m) != 0;
+#pragma unroll
+          for (int i = 0; i < h; i++) {
+            const double keep = up ? P[i + h] : P[i];
+            const double send = up ? P[i] : P[i + h];
+            P[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+          }
+        }
+        P[0] += __shfl_xor_sync(0xffffffffu, P[0], 1);
+        const int j = c0 + (lane >> 1);
+        if ((lane & 1) == 0 && j < scount) dst[j] = P[0];
+      }
+    }
+    __syncwarp();
+  }
+  double* near = reinterpret_cast<double*>(a.near_u);
+#pragma unroll
+  for (int k = 0; k < TPL; k++) {
+    const int i = lane + 32 * k;
+    if (i < tcnt) near[tstart + i] = u[k];
+  }
+}
+
+// FP64 counterpart of sym_gather_kernel: plain FP64 sums in list order.
+__global__ void __launch_bounds__(128) sym_gather_f64_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
+                                                             const int64_t* __restrict__ box_start,
+                                                             const int32_t* __restrict__ box_count,
+                                                             const int64_t* __restrict__ recv_off,
+                                                             const double* __restrict__ partial, int64_t stride,
+                                                             double* __restrict__ near_u) {
+  const int lane = lane_id();
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves; leaf += warps) {
+    const int64_t r0 = recv_off[leaf], r1 = recv_off[leaf + 1];
+    if (r0 == r1) continue;
+    const int64_t g = leaf_box[leaf];
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    for (int i = lane; i < cnt; i += 32) {
+      double acc = near_u[start + i];
+      for (int64_t r = r0; r < r1; r += 8) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = (r + k < r1) ? partial[(r + k) * stride + i] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+          if (r + k < r1) acc += v[k];
+      }
+      near_u[start + i] = acc;
     }
   }
 }
@@ -1297,8 +1488,8 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       p2p_kernel_f32s<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
       sym_gather_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_partial,
-          (int64_t)t->sym_stride, reinterpret_cast<float*>(near_u));
+          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off,
+          reinterpret_cast<const float*>(t->sym_partial), (int64_t)t->sym_stride, reinterpret_cast<float*>(near_u));
       FMM_LAUNCH_CHECK();
       t->launches += 1;
       return;
@@ -1307,6 +1498,28 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
     else p2p_kernel_f32h<TPL, false><<<(unsigned)blocks, 128, smem, st>>>(a);
     FMM_LAUNCH_CHECK();
     return;
+  }
+  if constexpr (!kF32) {
+    if (!field && t->sym) {
+      static bool sym_attr = false;
+      if (!sym_attr) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f64s<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sym_attr = true;
+      }
+      a.order = t->leaf_order_sym;
+      a.work_off = t->sym_work_off;
+      a.rec = t->sym_rec;
+      a.partial = t->sym_partial;
+      a.stride = t->sym_stride;
+      p2p_kernel_f64s<TPL><<<(unsigned)((t->n_leaves + 3) / 4), 128, smem, st>>>(a);
+      FMM_LAUNCH_CHECK();
+      sym_gather_f64_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
+          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_partial,
+          (int64_t)t->sym_stride, reinterpret_cast<double*>(near_u));
+      FMM_LAUNCH_CHECK();
+      t->launches += 1;
+      return;
+    }
   }
   FMM_CUDA_TRY(cudaMemsetAsync(t->counters + 1, 0, sizeof(int), st));
   static bool attr_set = false;

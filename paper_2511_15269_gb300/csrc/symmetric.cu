@@ -156,7 +156,8 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
   cudaFree(mirror), cudaFree(owns), cudaFree(n_work), cudaFree(n_recv);
   t->sym_stride = std::max(t->max_leaf, 1);
-  t->sym_partial = dev_alloc<float>(t, std::max<int64_t>(t->n_slots, 1) * t->sym_stride);
+  // slot sums in FP32 (FP32C path) or FP64 (FP64 path): room for doubles
+  t->sym_partial = dev_alloc<double>(t, std::max<int64_t>(t->n_slots, 1) * t->sym_stride);
 
   // work order of the symmetric kernel: heaviest work list first
   std::vector<int64_t> woff = host_copy(t->sym_work_off, NL + 1, st);
