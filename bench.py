@@ -270,6 +270,7 @@ PAPER_SETS = [  # Sec. III.A parameter sets: (name, N_max, p, theta, precision, 
     ("set1", 128, 5, 0.70, "fp32c", 30.4),
     ("set2", 256, 9, 0.50, "fp32c", 4.04),
     ("set3", 256, 10, 0.27, "fp64", 0.736),
+    ("set3_fp64df", 256, 10, 0.27, "fp64df", 0.736),
 ]
 
 
@@ -281,10 +282,10 @@ def bench_paper_sets(fmm, dev, pos_d, q_d, tg, ud):
     n = q_d.shape[0]
     out = {}
     for name, leaf, p, theta, prec, a100 in PAPER_SETS:
-        pr = fmm.FMM_FP64 if prec == "fp64" else fmm.FMM_FP32C
+        pr = {"fp64": fmm.FMM_FP64, "fp64df": fmm.FMM_FP64DF, "fp32c": fmm.FMM_FP32C}[prec]
         T = fmm.fmm_build_tree(pos_d, p, leaf, 2, theta, pr)
         u = torch.empty_like(q_d)
-        ms = event_ms(lambda: fmm.fmm_eval_potential(T, q_d, u), 1 if prec == "fp64" else 5)
+        ms = event_ms(lambda: fmm.fmm_eval_potential(T, q_d, u), 1 if prec != "fp32c" else 5)
         fmm.fmm_tree_profile(T, True)
         fmm.fmm_eval_potential(T, q_d, u)
         torch.cuda.synchronize()
@@ -457,6 +458,17 @@ def main():
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1) / 2
         u64 = u64_d.cpu().numpy()[tg]
+        # FP64 accuracy with the double-float near field
+        fmm.fmm_tree_set_precision(T, fmm.FMM_FP64DF)
+        fmm.fmm_eval_potential(T, q_d, u64_d)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            fmm.fmm_eval_potential(T, q_d, u64_d)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64df = e0.elapsed_time(e1) / 3
+        u64df = u64_d.cpu().numpy()[tg]
         fmm.fmm_tree_set_precision(T, fmm.FMM_FP32C)
         # backward (charges and positions) and field, FP32C
         g_d = torch.from_numpy(np.random.default_rng(3).normal(size=n)).to(dev)
@@ -477,6 +489,9 @@ def main():
         ms_field = e0.elapsed_time(e1) / 3
         line["fp64"] = {"value": n / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
                         "fp32c_speedup": ms64 / ms}
+        line["fp64df"] = {"value": n / (ms64df * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64df,
+                          "what": "FP64 far field, double-float near field (FMM_FP64DF)",
+                          "rel_l2_vs_fp64": rel_l2(u64df, u64), "rel_l2_vs_direct": rel_l2(u64df, ud)}
         line["errors_vs_direct_4096_targets"] = {
             "fp32c_rel_l2": rel_l2(u32, ud), "fp32c_rel_linf": rel_linf(u32, ud),
             "fp64_rel_l2": rel_l2(u64, ud), "fp64_rel_linf": rel_linf(u64, ud),

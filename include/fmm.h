@@ -55,10 +55,16 @@ typedef enum {
 
 enum {
   FMM_FP64 = 0,  /* every stage in FP64                                        */
-  FMM_FP32C = 1  /* P2M/M2M/M2L/L2L/L2P/P2P in FP32 on box-radius-scaled
+  FMM_FP32C = 1, /* P2M/M2M/M2L/L2L/L2P/P2P in FP32 on box-radius-scaled
                     coefficients, compensated (two-sum) accumulation of leaf and
                     local sums; rotation coefficients generated in FP64; final
                     near + far combination in FP64                             */
+  FMM_FP64DF = 2  /* FP64 accuracy: as FMM_FP64, except that the potential
+                    near field of a tree of one point set (or a batch of them)
+                    runs in double-float arithmetic (unevaluated sums of two
+                    FP32 values, error-free transformations) on the FP32 pipes,
+                    with results within a few 1e-14 of FP64; fields, backward
+                    and two-hierarchy trees use the FP64 near field            */
 };
 
 enum {
@@ -82,7 +88,7 @@ typedef struct {
                      must be >= 2^splits                                         */
   int splits;     /* s: bisections per level, 2^s children per box, 1..3        */
   double theta;   /* well-separation parameter of Eq. 4, 0 < theta < 1          */
-  int precision;  /* FMM_FP64 or FMM_FP32C, used by the evaluation calls        */
+  int precision;  /* FMM_FP64, FMM_FP32C or FMM_FP64DF, used by evaluations     */
   int flags;      /* 0 or a combination of FMM_TIE_TARGET, FMM_SAME_LEVEL      */
 } fmm_params;
 

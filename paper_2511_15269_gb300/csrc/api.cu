@@ -62,7 +62,7 @@ void free_tree(fmm_tree* t) {
                   t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
                   t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->down_ids,
                   t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr, t->sym_slot, t->sym_work_off,
-                  t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec};
+                  t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec, t->src_df, t->sym_frame};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->prof_ev) {
@@ -118,7 +118,8 @@ int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void*
     require(p.splits >= 1 && p.splits <= 3, "splits must be 1, 2 or 3");
     require(p.leaf_size >= (1 << p.splits) && p.leaf_size <= kMaxLeaf, "leaf_size must be in [2^splits, 256]");
     require(p.theta > 0.0 && p.theta < 1.0, "theta must be in (0, 1)");
-    require(p.precision == FMM_FP64 || p.precision == FMM_FP32C, "precision must be FMM_FP64 or FMM_FP32C");
+    require(p.precision == FMM_FP64 || p.precision == FMM_FP32C || p.precision == FMM_FP64DF,
+            "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
     require((p.flags & ~(FMM_TIE_TARGET | FMM_SAME_LEVEL)) == 0, "unknown flags");
     auto t0 = std::chrono::steady_clock::now();
     ensure_tables();
@@ -151,7 +152,8 @@ int fmm_build_tree2(const double* src_pos, int64_t n_src, const double* trg_pos,
     require(p.splits >= 1 && p.splits <= 3, "splits must be 1, 2 or 3");
     require(p.leaf_size >= (1 << p.splits) && p.leaf_size <= kMaxLeaf, "leaf_size must be in [2^splits, 256]");
     require(p.theta > 0.0 && p.theta < 1.0, "theta must be in (0, 1)");
-    require(p.precision == FMM_FP64 || p.precision == FMM_FP32C, "precision must be FMM_FP64 or FMM_FP32C");
+    require(p.precision == FMM_FP64 || p.precision == FMM_FP32C || p.precision == FMM_FP64DF,
+            "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
     require((p.flags & ~FMM_TIE_TARGET) == 0, "flags must be 0 or FMM_TIE_TARGET for two hierarchies");
     auto t0 = std::chrono::steady_clock::now();
     ensure_tables();
@@ -206,7 +208,8 @@ int fmm_tree_point_offsets(const fmm_tree* t, int64_t* offsets) {
 int fmm_tree_set_precision(fmm_tree* tree, int precision) {
   return guarded([&] {
     require(tree != nullptr, "tree is NULL");
-    require(precision == FMM_FP64 || precision == FMM_FP32C, "precision must be FMM_FP64 or FMM_FP32C");
+    require(precision == FMM_FP64 || precision == FMM_FP32C || precision == FMM_FP64DF,
+            "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
     tree->prm.precision = precision;
   });
 }

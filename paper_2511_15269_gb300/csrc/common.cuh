@@ -84,6 +84,19 @@ struct __align__(32) DupRec {
   float x0, x1, y0, y1, z0, z1, q0, q1;
 };
 
+// Double-float point record of the FP64DF near field: the position relative
+// to its leaf's centre and the charge, each split as hi + lo.
+struct __align__(32) DFRec {
+  float xh, yh, zh, qh, xl, yl, zl, ql;
+};
+
+// Frame of a work entry's source leaf for the FP64DF near field: its centre
+// (FP64).
+struct __align__(32) SymFrame {
+  double cx, cy, cz;
+  float g, pad;
+};
+
 // One work entry of the symmetric near field, read with one coalesced load:
 // the source leaf's point range, the pair's slot (-1: one-sided), the FP32
 // centre offset c_T - c_S and the coincidence threshold (< 0: no masking).
@@ -133,6 +146,11 @@ struct fmm_tree {
   int64_t* sym_recv_off = nullptr;    // n_leaves + 1: the slots each leaf receives (contiguous)
   double* sym_partial = nullptr;      // n_slots x sym_stride (read as float by the FP32C path)
   fmm::SymRec* sym_rec = nullptr;     // per work entry, in work-list order
+  // FP64DF near field: per-point double-float records (coordinates set at
+  // build, charges by every evaluation's gather) and the source frame of
+  // every work entry
+  fmm::DFRec* src_df = nullptr;       // n, tree order
+  fmm::SymFrame* sym_frame = nullptr; // per work entry, in work-list order
   int32_t* leaf_order_sym = nullptr;  // n_leaves: heaviest symmetric work first
   int32_t* leaf_order = nullptr;   // n_leaves: target leaves, most work first
   int32_t* leaf_box = nullptr;     // n_leaves: global box id of each leaf

@@ -72,17 +72,25 @@ __device__ __forceinline__ void load_coef(const real* src, real (&v)[ncoef(P)]) 
 
 // ---- E0: sort charges into tree order ----------------------------------------
 // Points at or after n_charges (targets of a separate target tree) get q = 0.
+// dup: FP32 near-field records (FP32C); df: charges of the double-float
+// records (FP64DF), whose coordinates are set at build.
 __global__ void gather_kernel(int64_t n, int64_t n_charges, const int32_t* __restrict__ perm,
                               const double* __restrict__ q, const vec4* __restrict__ pos,
-                              vec4* __restrict__ src, DupRec* __restrict__ dup) {
+                              vec4* __restrict__ src, DupRec* __restrict__ dup, DFRec* __restrict__ df) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     vec4 p = pos[i];
-    p.w = i < n_charges ? (real)q[perm[i]] : real(0);
+    const double qi = i < n_charges ? q[perm[i]] : 0.0;
+    p.w = (real)qi;
     src[i] = p;
     if (dup) {
       const float x = (float)p.x, y = (float)p.y, z = (float)p.z, w = (float)p.w;
       dup[i] = DupRec{x, x, y, y, z, z, w, w};
+    }
+    if (df) {
+      const float qh = (float)qi;
+      df[i].qh = qh;
+      df[i].ql = (float)(qi - (double)qh);
     }
   }
 }
@@ -485,6 +493,9 @@ struct P2PArgs {
   const SymRec* rec;
   void* partial;  // float (FP32C) or double (FP64) slot sums
   int stride;
+  // FP64DF: double-float point records and per-entry source frames
+  const DFRec* df_tile;
+  const SymFrame* frame;
   const int32_t* ent_src;
   const int64_t* box_start;
   const int32_t* box_count;
@@ -877,7 +888,10 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
       tz0[k] = p.z;
       tq0[k] = p.w;
     } else {
-      tx0[k] = ty0[k] = tz0[k] = tq0[k] = 0.f;
+      // absent targets far from every source (finite 1/r, zero charge): they
+      // must not add 0 * inf to the sources' sums
+      tx0[k] = 1e18f;
+      ty0[k] = tz0[k] = tq0[k] = 0.f;
     }
   }
   f2 tq[NPH];
@@ -1239,6 +1253,260 @@ __global__ void __launch_bounds__(128) sym_gather_f64_kernel(int64_t n_leaves, c
   }
 }
 
+// ---- E6 (FP64DF, potential, one point set): double-float symmetric near field --
+// FP64 accuracy on the FP32 pipes (GB300 runs FP64 at 1/64 of the FP32 rate).
+// Values are unevaluated sums h + l of two FP32 numbers.  Positions live in
+// the frame of the source leaf (offsets from its centre, FP64, split h + l);
+// differences of hi parts are taken exactly by two-sum (Knuth), so the
+// difference carries about 2^-48 of the larger offset.  r^2 is summed with
+// two-sum error terms, 1/r is the MUFU seed y refined by y (1 + rho / 2) with
+// rho = 1 - r^2 y^2 evaluated from FMA product errors, and the sums are
+// accumulated as renormalised (h, l) pairs.  Lane and slot layout as in
+// p2p_kernel_f64s (lane l holds targets l + 32 k).
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return dfl{s, (a - (s - bb)) + (b - bb)};
+}
+
+// acc += p + pe, renormalised (|l| <= ulp(h) / 2) so that the rounding of
+// later additions to l stays at 2^-48 of the sum
+__device__ __forceinline__ void df_acc(dfl& acc, float p, float pe) {
+  const dfl s = df_two_sum(acc.h, p);
+  const float l = acc.l + s.l + pe;
+  acc.h = s.h + l;
+  acc.l = l - (acc.h - s.h);
+}
+
+// 1/|t - s| as y + yl for target (th, tl) and source (sh, sl) in one frame;
+// zero for coincident points when MASK.
+template <bool MASK>
+__device__ __forceinline__ void df_rinv(const float (&th)[3], const float (&tl)[3], const float4& sh,
+                                        const float4& sl, float& y, float& yl) {
+  const dfl dx = df_two_sum(th[0], -sh.x), dy = df_two_sum(th[1], -sh.y), dz = df_two_sum(th[2], -sh.z);
+  const float ax = dx.h, ay = dy.h, az = dz.h;
+  const float bx = dx.l + (tl[0] - sl.x), by = dy.l + (tl[1] - sl.y), bz = dz.l + (tl[2] - sl.z);
+  const float px = ax * ax, py = ay * ay, pz = az * az;
+  float ex = fmaf(ax, ax, -px), ey = fmaf(ay, ay, -py), ez = fmaf(az, az, -pz);
+  ex = fmaf(bx, bx, fmaf(ax + ax, bx, ex));
+  ey = fmaf(by, by, fmaf(ay + ay, by, ey));
+  ez = fmaf(bz, bz, fmaf(az + az, bz, ez));
+  const dfl s1 = df_two_sum(px, py);
+  const dfl s2 = df_two_sum(s1.h, pz);
+  const float e = ((ex + ey) + ez) + (s1.l + s2.l);
+  const float rh = s2.h + e;
+  const float rl = e - (rh - s2.h);
+  y = rsqrt_mufu(rh);
+  const float w = y * y, we = fmaf(y, y, -w);
+  const float t1 = rh * w;
+  const float t1e = fmaf(rh, we, fmaf(rl, w, fmaf(rh, w, -t1)));
+  const float rho = (1.f - t1) - t1e;
+  yl = y * (0.5f * rho);
+  if (MASK && !(rh > 0.f)) y = yl = 0.f;
+}
+
+template <int TPL>
+__global__ void __launch_bounds__(128) p2p_kernel_dfs(P2PArgs a) {
+  constexpr int CAP = TPL * 32;
+  constexpr int WARPS = 4;
+  extern __shared__ __align__(128) unsigned char p2p_smem[];
+  DFRec (*sbuf)[2][CAP] = reinterpret_cast<DFRec (*)[2][CAP]>(p2p_smem);
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const DFRec* tile = a.df_tile;
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+  if (t >= a.n_leaves) return;
+  const int64_t leaf = a.order[t];
+  const int64_t g = a.leaf_box[leaf];
+  const int64_t tstart = a.box_start[g];
+  const int tcnt = a.box_count[g];
+  // FP64 target positions are re-read per entry (L1/L2 hits) to keep
+  // registers for the double-float state
+  const dvec4* tsrc = reinterpret_cast<const dvec4*>(a.src) + tstart;
+  dfl tq[TPL], u[TPL];
+#pragma unroll
+  for (int k = 0; k < TPL; k++) {
+    const int i = lane + 32 * k;
+    tq[k] = dfl{0.f, 0.f};
+    if (i < tcnt) {
+      const DFRec r = a.df_tile[tstart + i];
+      tq[k] = dfl{r.qh, r.ql};
+    }
+    u[k] = dfl{0.f, 0.f};
+  }
+  const int64_t kb = a.work_off[leaf];
+  const int nwk = (int)(a.work_off[leaf + 1] - kb);
+  SymRec mine{};
+  SymFrame mframe{};
+  auto load_batch = [&](int base) {
+    if (base + lane < nwk) {
+      mine = a.rec[kb + base + lane];
+      mframe = a.frame[kb + base + lane];
+    }
+  };
+  auto issue = [&](int64_t start, int count, int buf) {
+    if (lane == 0) {
+      fence_proxy_async();
+      tma_load_1d(sbuf[warp][buf], tile + start, (uint32_t)(count * sizeof(DFRec)), &bar[buf]);
+    }
+  };
+  uint32_t phase = 0;
+  if (nwk > 0) {
+    load_batch(0);
+    issue(__shfl_sync(0xffffffffu, mine.start, 0), __shfl_sync(0xffffffffu, mine.count, 0), 0);
+  }
+  for (int w = 0; w < nwk; w++) {
+    const int buf = w & 1;
+    if (w > 0 && (w & 31) == 0) load_batch(w);  // warp-uniform
+    const int sl = w & 31;
+    const int scount = __shfl_sync(0xffffffffu, mine.count, sl);
+    const int slot = __shfl_sync(0xffffffffu, mine.slot, sl);
+    const bool mask = __shfl_sync(0xffffffffu, mine.thr, sl) >= 0.f;
+    const double cx = __shfl_sync(0xffffffffu, mframe.cx, sl), cy = __shfl_sync(0xffffffffu, mframe.cy, sl),
+                 cz = __shfl_sync(0xffffffffu, mframe.cz, sl);
+    if (w + 1 < nwk) {
+      int64_t ns;
+      int nc;
+      if ((w + 1) & 31) {
+        ns = __shfl_sync(0xffffffffu, mine.start, (w + 1) & 31);
+        nc = __shfl_sync(0xffffffffu, mine.count, (w + 1) & 31);
+      } else {
+        const SymRec nx = a.rec[kb + w + 1];
+        ns = nx.start;
+        nc = nx.count;
+      }
+      issue(ns, nc, buf ^ 1);
+    }
+    // targets in the source leaf's frame, split as the source records were
+    // (coincident points get identical splits); absent targets far away
+    float th[TPL][3], tl[TPL][3];
+#pragma unroll
+    for (int k = 0; k < TPL; k++) {
+      const int i = lane + 32 * k;
+      const dvec4 p = i < tcnt ? tsrc[i] : dvec4{cx + 1e18, cy, cz, 0.0};
+      const double d[3] = {p.x - cx, p.y - cy, p.z - cz};
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const float h = (float)d[c];
+        th[k][c] = h;
+        tl[k][c] = (float)(d[c] - (double)h);
+      }
+    }
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      // copies still in flight into this warp's buffers must land first
+      mbar_wait(&bar[buf], (phase >> buf) & 1u);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      return;
+    }
+    phase ^= 1u << buf;
+    const float4* sb = reinterpret_cast<const float4*>(sbuf[warp][buf]);
+    if (slot < 0) {
+      // one-sided: the self pair and pairs listed in one direction only
+      for (int j = 0; j < scount; j++) {
+        const float4 sh = sb[2 * j], slo = sb[2 * j + 1];  // (xh, yh, zh, qh), (xl, yl, zl, ql)
+#pragma unroll
+        for (int k = 0; k < TPL; k++) {
+          float y, yl;
+          if (mask) df_rinv<true>(th[k], tl[k], sh, slo, y, yl);
+          else df_rinv<false>(th[k], tl[k], sh, slo, y, yl);
+          const float p = sh.w * y;
+          df_acc(u[k], p, fmaf(sh.w, yl, fmaf(slo.w, y, fmaf(sh.w, y, -p))));
+        }
+      }
+    } else {
+      double* dst = reinterpret_cast<double*>(a.partial) + (int64_t)slot * a.stride;
+      if constexpr (TPL >= 4) {
+        // many targets per lane: one source at a time (compact code), its sum
+        // over the warp by a butterfly all-reduce
+#pragma unroll 1
+        for (int j = 0; j < scount; j++) {
+          const float4 sh = sb[2 * j], slo = sb[2 * j + 1];
+          dfl acc{0.f, 0.f};
+#pragma unroll
+          for (int k = 0; k < TPL; k++) {
+            float y, yl;
+            if (mask) df_rinv<true>(th[k], tl[k], sh, slo, y, yl);
+            else df_rinv<false>(th[k], tl[k], sh, slo, y, yl);
+            const float p = sh.w * y;
+            df_acc(u[k], p, fmaf(sh.w, yl, fmaf(slo.w, y, fmaf(sh.w, y, -p))));
+            const float pq = tq[k].h * y;
+            df_acc(acc, pq, fmaf(tq[k].h, yl, fmaf(tq[k].l, y, fmaf(tq[k].h, y, -pq))));
+          }
+#pragma unroll
+          for (int m = 16; m >= 1; m >>= 1) {
+            const float rh = __shfl_xor_sync(0xffffffffu, acc.h, m);
+            const float rl = __shfl_xor_sync(0xffffffffu, acc.l, m);
+            df_acc(acc, rh, rl);
+          }
+          if (lane == 0) dst[j] = (double)acc.h + (double)acc.l;
+        }
+      } else
+      for (int c0 = 0; c0 < scount; c0 += 16) {
+        dfl P[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; jj++) {
+          const int j = c0 + jj;
+          P[jj] = dfl{0.f, 0.f};
+          if (j < scount) {
+            const float4 sh = sb[2 * j], slo = sb[2 * j + 1];
+#pragma unroll
+            for (int k = 0; k < TPL; k++) {
+              float y, yl;
+              if (mask) df_rinv<true>(th[k], tl[k], sh, slo, y, yl);
+              else df_rinv<false>(th[k], tl[k], sh, slo, y, yl);
+              const float p = sh.w * y;
+              df_acc(u[k], p, fmaf(sh.w, yl, fmaf(slo.w, y, fmaf(sh.w, y, -p))));
+              const float pq = tq[k].h * y;
+              df_acc(P[jj], pq, fmaf(tq[k].h, yl, fmaf(tq[k].l, y, fmaf(tq[k].h, y, -pq))));
+            }
+          }
+        }
+        // reduce-scatter over lane bits 4..1 (lane l ends with P[l >> 1]), then the lane pair
+#pragma unroll
+        for (int m = 16, hh = 8; hh >= 1; m >>= 1, hh >>= 1) {
+          const bool up = (lane & m) != 0;
+#pragma unroll
+          for (int i = 0; i < hh; i++) {
+            const dfl keep = up ? P[i + hh] : P[i];
+            const dfl send = up ? P[i] : P[i + hh];
+            const float rh = __shfl_xor_sync(0xffffffffu, send.h, m);
+            const float rl = __shfl_xor_sync(0xffffffffu, send.l, m);
+            P[i] = keep;
+            df_acc(P[i], rh, rl);
+          }
+        }
+        {
+          const float rh = __shfl_xor_sync(0xffffffffu, P[0].h, 1);
+          const float rl = __shfl_xor_sync(0xffffffffu, P[0].l, 1);
+          df_acc(P[0], rh, rl);
+        }
+        const int j = c0 + (lane >> 1);
+        if ((lane & 1) == 0 && j < scount) dst[j] = (double)P[0].h + (double)P[0].l;
+      }
+    }
+    __syncwarp();
+  }
+  double* near = reinterpret_cast<double*>(a.near_u);
+#pragma unroll
+  for (int k = 0; k < TPL; k++) {
+    const int i = lane + 32 * k;
+    if (i < tcnt) near[tstart + i] = (double)u[k].h + (double)u[k].l;
+  }
+}
+
 // ---- E5 + E7: L2P, near + far combination and inverse sort --------------------
 // u = -1/(4 pi) (far + near);  E = -grad u = 1/(4 pi) (grad far - sum q d / r^3).
 template <int P, bool FIELD>
@@ -1500,6 +1768,28 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
     return;
   }
   if constexpr (!kF32) {
+    if (!field && t->sym && t->prm.precision == FMM_FP64DF) {
+      static bool df_attr = false;
+      if (!df_attr) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_dfs<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        df_attr = true;
+      }
+      a.order = t->leaf_order_sym;
+      a.work_off = t->sym_work_off;
+      a.rec = t->sym_rec;
+      a.frame = t->sym_frame;
+      a.df_tile = t->src_df;
+      a.partial = t->sym_partial;
+      a.stride = t->sym_stride;
+      p2p_kernel_dfs<TPL><<<(unsigned)((t->n_leaves + 3) / 4), 128, smem, st>>>(a);
+      FMM_LAUNCH_CHECK();
+      sym_gather_f64_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
+          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_partial,
+          (int64_t)t->sym_stride, reinterpret_cast<double*>(near_u));
+      FMM_LAUNCH_CHECK();
+      t->launches += 1;
+      return;
+    }
     if (!field && t->sym) {
       static bool sym_attr = false;
       if (!sym_attr) {
@@ -1569,8 +1859,9 @@ void dispatch_p(int p, F&& f) {
 void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
   Ptrs pp = ptrs(t);
   stage_event(t, FMM_STAGE_SORT, false, st);
+  const bool df = !kF32 && t->prm.precision == FMM_FP64DF && t->sym && t->src_df && field == nullptr;
   gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, q, pp.pos, pp.src,
-                                                     kF32 ? t->src_dup : nullptr);
+                                                     kF32 ? t->src_dup : nullptr, df ? t->src_df : nullptr);
   FMM_LAUNCH_CHECK();
   t->launches += 1;
   stage_event(t, FMM_STAGE_SORT, true, st);

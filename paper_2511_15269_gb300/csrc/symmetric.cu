@@ -114,6 +114,50 @@ __global__ void rec_kernel(int64_t n_leaves, const int64_t* __restrict__ work_of
   }
 }
 
+// ---- FP64DF point records and frames ----
+// coordinates of every point in its leaf's frame (offset from the leaf
+// centre in FP64), split h + l
+__global__ void df_points_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
+                                 const int64_t* __restrict__ box_start, const int32_t* __restrict__ box_count,
+                                 const double* __restrict__ center, const dvec4* __restrict__ pos,
+                                 DFRec* __restrict__ rec) {
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; l < n_leaves; l += warps) {
+    const int64_t g = leaf_box[l];
+    const double cx = center[3 * g], cy = center[3 * g + 1], cz = center[3 * g + 2];
+    for (int i = threadIdx.x & 31; i < box_count[g]; i += 32) {
+      const int64_t k = box_start[g] + i;
+      const dvec4 p = pos[k];
+      const double x = p.x - cx, y = p.y - cy, z = p.z - cz;
+      const float hx = (float)x, hy = (float)y, hz = (float)z;
+      DFRec r;
+      r.xh = hx;
+      r.yh = hy;
+      r.zh = hz;
+      r.xl = (float)(x - (double)hx);
+      r.yl = (float)(y - (double)hy);
+      r.zl = (float)(z - (double)hz);
+      r.qh = r.ql = 0.f;
+      rec[k] = r;
+    }
+  }
+}
+
+// source frame of every work entry
+__global__ void frame_rec_kernel(int64_t n_leaves, const int64_t* __restrict__ work_off,
+                                 const int32_t* __restrict__ work, const int32_t* __restrict__ src,
+                                 const int32_t* __restrict__ leaf_box, const double* __restrict__ center,
+                                 SymFrame* __restrict__ frame) {
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; l < n_leaves; l += warps) {
+    for (int64_t k = work_off[l] + (threadIdx.x & 31); k < work_off[l + 1]; k += 32) {
+      const int s = src[work[k]];
+      const int64_t gs = leaf_box[s];
+      frame[k] = SymFrame{center[3 * gs], center[3 * gs + 1], center[3 * gs + 2], 0.f, 0.f};
+    }
+  }
+}
+
 template <class T>
 std::vector<T> host_copy(const T* d, int64_t n, cudaStream_t st) {
   std::vector<T> h((size_t)std::max<int64_t>(n, 0));
@@ -152,6 +196,15 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
   rec_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->sym_work_off, t->sym_work, t->p2p32, t->p2p_thr,
                                                      t->sym_slot, t->src_leaf_box, t->box_start, t->box_count,
                                                      t->sym_rec);
+  FMM_LAUNCH_CHECK();
+  // FP64DF point records and per-entry source frames
+  t->src_df = dev_alloc<DFRec>(t, t->n);
+  df_points_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->leaf_box, t->box_start, t->box_count, t->center,
+                                                           t->pos64, t->src_df);
+  FMM_LAUNCH_CHECK();
+  t->sym_frame = dev_alloc<SymFrame>(t, std::max<int64_t>(nw, 1));
+  frame_rec_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->sym_work_off, t->sym_work, t->p2p_src, t->leaf_box,
+                                                           t->center, t->sym_frame);
   FMM_LAUNCH_CHECK();
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
   cudaFree(mirror), cudaFree(owns), cudaFree(n_work), cudaFree(n_recv);

@@ -15,7 +15,7 @@ _LIB_PATH = os.path.join(_HERE, "libfmm_gb300.so")
 _lib = None
 
 FMM_OK, FMM_ERR_INVALID_ARG, FMM_ERR_CUDA, FMM_ERR_OOM, FMM_ERR_CAPACITY, FMM_ERR_TIMEOUT = range(6)
-FMM_FP64, FMM_FP32C = 0, 1
+FMM_FP64, FMM_FP32C, FMM_FP64DF = 0, 1, 2
 FMM_TIE_TARGET = 1
 FMM_SAME_LEVEL = 2
 FMM_MAX_P = 10

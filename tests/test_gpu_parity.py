@@ -150,6 +150,19 @@ def test_same_level_potential_parity(F, orc):
     F.fmm_tree_status(T)
 
 
+@pytest.mark.parametrize("name,mk,p,leaf,s,theta", POT_CASES, ids=[c[0] for c in POT_CASES])
+def test_fp64df_potential_parity(F, orc, name, mk, p, leaf, s, theta):
+    """FP64 accuracy with the double-float near field: same bar as FP64."""
+    pos, q = mk()
+    T, O = build_both(F, orc, pos, p, leaf, s, theta, F.FMM_FP64DF)
+    u_o = O.eval(q, p)
+    u = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    F.fmm_tree_status(T)
+    e = rel_l2(u, u_o)
+    print("%s: fp64df vs oracle %.3e" % (name, e))
+    assert e <= TOL_FP64
+
+
 @pytest.mark.parametrize("name,mk,p,leaf,s,theta", POT_CASES[:4], ids=[c[0] for c in POT_CASES[:4]])
 def test_field_parity(F, orc, name, mk, p, leaf, s, theta):
     pos, q = mk()
