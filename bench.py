@@ -6,9 +6,11 @@ p = 8, leaf size 128, s = 2, theta = 0.4, FP32-compensated path.  A step is
 one evaluation with the hierarchy prebuilt (sort, P2M, M2M, M2L, L2L, L2P +
 P2P, inverse sort), charges resident in device memory; L2 is flushed (a
 256 MB write) before every timed step.  The JSON line also carries the FP64
-path, the errors against the FP64 direct sum on 4096 sampled targets, the
-backward/forward time ratio, per-stage times, the roofline of the dominant
-kernel and the CPU oracle timed on the host cores.
+and FP64DF paths, the errors against the FP64 direct sum on 4096 sampled
+targets, the backward/forward time ratio, per-stage times, the roofline of
+the dominant kernel against the measured FP32 throughput, the paper's three
+parameter sets (Sec. III.A), the Plummer and batched workloads and the CPU
+oracle timed on the host cores.
 
 --impl reference times the CPU oracle instead (the reference arm), on
 bounded target samples of the same workload.
@@ -327,7 +329,7 @@ def main():
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
-    from paper_2511_15269_gb300 import build, fmm
+    from paper_2511_15269_gb300 import build, fmm, replicas
     if rank == 0:
         build.build()
     if world > 1:
@@ -377,15 +379,11 @@ def main():
     fmm.fmm_tree_profile(T, False)
     launches = fmm.fmm_tree_stats(T)["kernel_launches"] - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    # whole job: points of all ranks over the slowest rank's mean step time
+    value, _, ms = replicas.aggregate_throughput(n, float(np.mean(step_ms)), device=dev)
     stage, calls = fmm.fmm_tree_stage_times(T)
     stage_ms = {k: v / max(calls, 1) for k, v in stage.items()}
     fmm.fmm_tree_status(T)
-    value = world * n / (ms * 1e-3) / 1e6
 
     if rank != 0:
         if world > 1:
