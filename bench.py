@@ -495,7 +495,7 @@ def main():
             "fp64_rel_l2": rel_l2(u64, ud), "fp64_rel_linf": rel_linf(u64, ud),
             "fp32c_vs_fp64_rel_l2": rel_l2(u32, u64)}
         line["backward"] = {"ms": ms_bwd, "bwd_fwd_ratio": ms_bwd / ms,
-                            "what": "dL/dq and dL/dpos (two field evaluations + combine), FP32C"}
+                            "what": "dL/dq and dL/dpos: one near-field sweep for q and dL/du, far field of each, combine; FP32C"}
         line["field"] = {"value": n / (ms_field * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms_field}
         # CPU oracle baseline on bounded samples (rank 0, one GPU)
         O = oracle.Tree(pos, cfg["leaf_size"], cfg["s"], cfg["theta"])

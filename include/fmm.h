@@ -280,7 +280,10 @@ int fmm_eval_potential_static(const fmm_tree* tree, const double* q, double* u, 
  *     grad_q   = K grad_u                               (K is symmetric)
  *     grad_pos = grad_u_k * grad u(r_k) + q_k * grad v(r_k),  v = K grad_u
  * grad_q (n) and grad_pos (n x 3) may each be NULL.  The tree is held fixed
- * (gradients are taken with the hierarchy of the current positions). */
+ * (gradients are taken with the hierarchy of the current positions).  With
+ * FMM_FP32C and leaves of at most 128 points the near field of q and grad_u
+ * is swept once (shared distances and 1/r), followed by the far field of
+ * each; otherwise two field evaluations. */
 int fmm_backward(const fmm_tree* tree, const double* q, const double* grad_u,
                  double* grad_q, double* grad_pos, void* stream);
 

@@ -62,7 +62,7 @@ void free_tree(fmm_tree* t) {
                   t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
                   t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->down_ids,
                   t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr, t->sym_slot, t->sym_work_off,
-                  t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec, t->src_df, t->sym_frame};
+                  t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec, t->src_df, t->sym_frame, t->src_dup2, t->near_u2, t->near_f2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->prof_ev) {
@@ -356,7 +356,14 @@ int fmm_backward(const fmm_tree* t, const double* q, const double* grad_u, doubl
             "fmm_backward needs one point set; for separate source and target trees evaluate the "
             "transposed problem (sources and targets swapped) instead");
     cudaStream_t st = (cudaStream_t)stream;
-    if (grad_pos) {
+    if (grad_pos && t->prm.precision == FMM_FP32C && t->src_dup2 && t->max_leaf <= 128) {
+      // one near-field sweep for both charge vectors, then both far fields
+      // (leaves of more than 128 points: two field evaluations below)
+      backward_fp32(t, q, grad_u, grad_q, t->f_stage, t->g_stage, st);
+      backward_combine_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, q, grad_u, t->f_stage, t->g_stage,
+                                                                   grad_pos);
+      FMM_LAUNCH_CHECK();
+    } else if (grad_pos) {
       eval_any(t, q, nullptr, t->f_stage, st);          // E of the charges
       eval_any(t, grad_u, grad_q, t->g_stage, st);      // v = K grad_u and E of grad_u
       backward_combine_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, q, grad_u, t->f_stage, t->g_stage,

@@ -202,6 +202,11 @@ struct fmm_tree {
   double* Lam64 = nullptr;
   void* near_u = nullptr;        // n x 8 bytes: near-field potential sums
   void* near_f = nullptr;        // 3n x 8 bytes: near-field gradient sums
+  // backward pass (one point set): records of the second charge vector and
+  // its near-field potential (hi, lo) and field sums
+  fmm::DupRec* src_dup2 = nullptr;
+  float* near_u2 = nullptr;      // 2n
+  float* near_f2 = nullptr;      // 3n
   double* q_stage = nullptr;     // n (host-buffer entry points, backward)
   double* u_stage = nullptr;     // n
   double* f_stage = nullptr;     // 3 n (backward)
@@ -250,6 +255,10 @@ void merge_trees(fmm_tree* const* in, int n, cudaStream_t st, fmm_tree* out);
 //   q: device, original order; u / field: device outputs (nullable)
 void eval_fp32(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st);
 void eval_fp64(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st);
+// FP32C backward of one point set: u of g (ug, nullable), fields of q and of
+// g, caller's point order; one near-field sweep for both charge vectors.
+void backward_fp32(const fmm_tree* t, const double* q, const double* g, double* ug, double* fq, double* fg,
+                   cudaStream_t st);
 // Per-precision one-time set-up: constant tables for every order.
 void init_tables_fp32();
 void init_tables_fp64();

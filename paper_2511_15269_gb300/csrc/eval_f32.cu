@@ -17,5 +17,9 @@ Ptrs ptrs(const fmm_tree* t) {
 void eval_fp32(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
   eval_impl(t, q, u, field, st);
 }
+void backward_fp32(const fmm_tree* t, const double* q, const double* g, double* ug, double* fq, double* fg,
+                   cudaStream_t st) {
+  backward_impl(t, q, g, ug, fq, fg, st);
+}
 void init_tables_fp32() { upload_tables(); }
 }  // namespace fmm

@@ -276,6 +276,16 @@ __device__ __forceinline__ void fence_barrier_init() {
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// cp.async.bulk of `bytes` completing on `bar` (the expected transaction
+// count is registered by the caller)
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
@@ -496,6 +506,10 @@ struct P2PArgs {
   // FP64DF: double-float point records and per-entry source frames
   const DFRec* df_tile;
   const SymFrame* frame;
+  // backward pass: records of the second charge vector, its near sums
+  const DupRec* tile_g;
+  float* near_u2;
+  float* near_f2;
   const int32_t* ent_src;
   const int64_t* box_start;
   const int32_t* box_count;
@@ -784,6 +798,186 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : ((TPL >= 8 || 
           a.near_f[3 * pidx + 1] = fy[k];
           a.near_f[3 * pidx + 2] = fz[k];
         }
+      }
+    }
+  }
+}
+
+// ---- E6 for the backward pass (FP32C): both charge vectors in one sweep ------
+// The backward pass needs the field of the charges q and the potential and
+// field of dL/du (g) at every point.  One pass over the near-field list
+// shares the distance and 1/r of every pair between the two: per ordered
+// pair, field of q (w = q_j / r^3), potential and field of g.  Lane layout and
+// staging as in p2p_kernel_f32h, with the q and g records of a source leaf
+// copied side by side.
+template <bool MASK, int NPH>
+__device__ __forceinline__ void bwd_pair(const ulonglong2 a, const ulonglong2 b, const ulonglong2 gb,
+                                         const f2 (&tx)[NPH], const f2 (&ty)[NPH], const f2 (&tz)[NPH],
+                                         f2 (&fqx)[NPH], f2 (&fqy)[NPH], f2 (&fqz)[NPH], f2 (&ug)[NPH],
+                                         f2 (&fgx)[NPH], f2 (&fgy)[NPH], f2 (&fgz)[NPH], float thr) {
+#pragma unroll
+  for (int k = 0; k < NPH; k++) {
+    const f2 dx = f2sub(tx[k], a.x), dy = f2sub(ty[k], a.y), dz = f2sub(tz[k], b.x);
+    const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+    float r0, r1;
+    f2unpack(r2, r0, r1);
+    float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
+    if (MASK) {
+      i0 = (r0 > thr) ? i0 : 0.f;
+      i1 = (r1 > thr) ? i1 : 0.f;
+    }
+    const f2 ri = f2pack(i0, i1);
+    const f2 ri3 = f2mul(f2mul(ri, ri), ri);
+    ug[k] = f2fma(gb.y, ri, ug[k]);
+    const f2 wq = f2mul(b.y, ri3), wg = f2mul(gb.y, ri3);
+    fqx[k] = f2fma(wq, dx, fqx[k]);
+    fqy[k] = f2fma(wq, dy, fqy[k]);
+    fqz[k] = f2fma(wq, dz, fqz[k]);
+    fgx[k] = f2fma(wg, dx, fgx[k]);
+    fgy[k] = f2fma(wg, dy, fgy[k]);
+    fgz[k] = f2fma(wg, dz, fgz[k]);
+  }
+}
+
+template <int TPL>
+__global__ void __launch_bounds__(128, TPL <= 2 ? 4 : 2) p2p_kernel_bwd(P2PArgs a) {  // TPL <= 4
+  constexpr int CAP = TPL * 32;
+  constexpr int WARPS = 4;
+  constexpr int NT = 2 * TPL;
+  constexpr int NPH = TPL;
+  extern __shared__ __align__(128) unsigned char p2p_smem[];
+  DupRec (*sbuf)[2][2][CAP] = reinterpret_cast<DupRec (*)[2][2][CAP]>(p2p_smem);  // [warp][buf][q, g]
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const DupRec* tile = reinterpret_cast<const DupRec*>(a.tile);
+  const DupRec* tile_g = a.tile_g;
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int half = lane >> 4, l16 = lane & 15;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+  if (t >= a.n_leaves) return;
+  const int64_t leaf = a.order[t];
+  const int64_t g = a.leaf_box[leaf];
+  const int64_t tstart = a.box_start[g];
+  const int tcnt = a.box_count[g];
+  float tx0[NT], ty0[NT], tz0[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const int i = l16 + 16 * k;
+    if (i < tcnt) {
+      const float4 p = reinterpret_cast<const float4*>(a.src)[tstart + i];
+      tx0[k] = p.x;
+      ty0[k] = p.y;
+      tz0[k] = p.z;
+    } else {
+      tx0[k] = ty0[k] = tz0[k] = 0.f;
+    }
+  }
+  float uh[NT], ul[NT], qx[NT], qy[NT], qz[NT], gx[NT], gy[NT], gz[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) uh[k] = ul[k] = qx[k] = qy[k] = qz[k] = gx[k] = gy[k] = gz[k] = 0.f;
+  const int64_t eb = a.off[leaf], ee = a.off[leaf + 1];
+  auto issue = [&](int64_t e, int buf) {
+    const int64_t gs = a.src_leaf_box[a.ent32[e].src & 0x7fffffff];
+    if (lane == 0) {
+      const uint32_t bytes = (uint32_t)(a.box_count[gs] * sizeof(DupRec));
+      fence_proxy_async();
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[buf])),
+                   "r"(2 * bytes)
+                   : "memory");
+      bulk_copy(sbuf[warp][buf][0], tile + a.box_start[gs], bytes, &bar[buf]);
+      bulk_copy(sbuf[warp][buf][1], tile_g + a.box_start[gs], bytes, &bar[buf]);
+    }
+  };
+  uint32_t phase = 0;
+  if (eb < ee) issue(eb, 0);
+  for (int64_t e = eb; e < ee; e++) {
+    const int buf = (int)((e - eb) & 1);
+    if (e + 1 < ee) issue(e + 1, buf ^ 1);
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      // copies still in flight into this warp's buffers must land first
+      mbar_wait(&bar[buf], (phase >> buf) & 1u);
+      if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      return;
+    }
+    phase ^= 1u << buf;
+    const P2PEntry en = a.ent32[e];
+    const int ls = en.src & 0x7fffffff;
+    const int scount = a.box_count[a.src_leaf_box[ls]];
+    const bool mask = (en.src < 0) || ls == (int)leaf;
+    const float thr = mask ? a.thr[e] : 0.f;
+    const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
+    f2 tx[NPH], ty[NPH], tz[NPH], fqx[NPH], fqy[NPH], fqz[NPH], ug[NPH], fgx[NPH], fgy[NPH], fgz[NPH];
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      tx[k] = f2add(f2pack(tx0[2 * k], tx0[2 * k + 1]), ddx);
+      ty[k] = f2add(f2pack(ty0[2 * k], ty0[2 * k + 1]), ddy);
+      tz[k] = f2add(f2pack(tz0[2 * k], tz0[2 * k + 1]), ddz);
+      fqx[k] = fqy[k] = fqz[k] = ug[k] = fgx[k] = fgy[k] = fgz[k] = 0ull;
+    }
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sbuf[warp][buf][0]);
+    const ulonglong2* g2 = reinterpret_cast<const ulonglong2*>(sbuf[warp][buf][1]);
+    if (mask) {
+#pragma unroll 2
+      for (int j = half; j < scount; j += 2)
+        bwd_pair<true, NPH>(s2[2 * j], s2[2 * j + 1], g2[2 * j + 1], tx, ty, tz, fqx, fqy, fqz, ug, fgx, fgy, fgz,
+                            thr);
+    } else {
+#pragma unroll 2
+      for (int j = half; j < scount; j += 2)
+        bwd_pair<false, NPH>(s2[2 * j], s2[2 * j + 1], g2[2 * j + 1], tx, ty, tz, fqx, fqy, fqz, ug, fgx, fgy, fgz,
+                             thr);
+    }
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      float a0, a1;
+      f2unpack(ug[k], a0, a1);
+      two_sum(uh[2 * k], ul[2 * k], a0);
+      two_sum(uh[2 * k + 1], ul[2 * k + 1], a1);
+      f2unpack(fqx[k], a0, a1), qx[2 * k] += a0, qx[2 * k + 1] += a1;
+      f2unpack(fqy[k], a0, a1), qy[2 * k] += a0, qy[2 * k + 1] += a1;
+      f2unpack(fqz[k], a0, a1), qz[2 * k] += a0, qz[2 * k + 1] += a1;
+      f2unpack(fgx[k], a0, a1), gx[2 * k] += a0, gx[2 * k + 1] += a1;
+      f2unpack(fgy[k], a0, a1), gy[2 * k] += a0, gy[2 * k + 1] += a1;
+      f2unpack(fgz[k], a0, a1), gz[2 * k] += a0, gz[2 * k + 1] += a1;
+    }
+    __syncwarp();
+  }
+  // combine the two halves
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const float oh = __shfl_xor_sync(0xffffffffu, uh[k], 16);
+    const float ol = __shfl_xor_sync(0xffffffffu, ul[k], 16);
+    two_sum(uh[k], ul[k], oh);
+    ul[k] += ol;
+    qx[k] += __shfl_xor_sync(0xffffffffu, qx[k], 16);
+    qy[k] += __shfl_xor_sync(0xffffffffu, qy[k], 16);
+    qz[k] += __shfl_xor_sync(0xffffffffu, qz[k], 16);
+    gx[k] += __shfl_xor_sync(0xffffffffu, gx[k], 16);
+    gy[k] += __shfl_xor_sync(0xffffffffu, gy[k], 16);
+    gz[k] += __shfl_xor_sync(0xffffffffu, gz[k], 16);
+  }
+  if (half == 0) {
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+      const int i = l16 + 16 * k;
+      if (i < tcnt) {
+        const int64_t pidx = tstart + i;
+        a.near_f[3 * pidx] = qx[k];
+        a.near_f[3 * pidx + 1] = qy[k];
+        a.near_f[3 * pidx + 2] = qz[k];
+        a.near_u2[2 * pidx] = uh[k];
+        a.near_u2[2 * pidx + 1] = ul[k];
+        a.near_f2[3 * pidx] = gx[k];
+        a.near_f2[3 * pidx + 1] = gy[k];
+        a.near_f2[3 * pidx + 2] = gz[k];
       }
     }
   }
@@ -1895,6 +2089,79 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     run_l2p<P>(t, pp, near_u, near_f, u, field, st);
   });
   stage_event(t, FMM_STAGE_L2P, true, st);
+}
+
+// Backward pass (FP32C): near field of both charge vectors in one sweep, then
+// the far field of each, local evaluations into the field of q (fq) and the
+// potential and field of g (ug, fg), all in the caller's point order.
+template <int TPL>
+void run_p2p_bwd_tpl(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+  P2PArgs a{};
+  a.n_leaves = t->n_leaves;
+  a.leaf_box = t->leaf_box;
+  a.src_leaf_box = t->src_leaf_box;
+  a.order = t->leaf_order;
+  a.off = t->p2p_off;
+  a.ent32 = t->p2p32;
+  a.thr = t->p2p_thr;
+  a.box_start = t->box_start;
+  a.box_count = t->box_count;
+  a.src = pp.src;
+  a.tile = t->src_dup;
+  a.tile_g = t->src_dup2;
+  a.near_f = reinterpret_cast<real*>(t->near_f);
+  a.near_u2 = t->near_u2;
+  a.near_f2 = t->near_f2;
+  a.status = t->status;
+  const size_t smem = (size_t)4 * 2 * 2 * TPL * 32 * 32;  // [warp][buf][q, g] 32-byte records
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_bwd<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_bwd<TPL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    attr_set = true;
+  }
+  p2p_kernel_bwd<TPL><<<(unsigned)((t->n_leaves + 3) / 4), 128, smem, st>>>(a);
+  FMM_LAUNCH_CHECK();
+  t->launches += 1;
+}
+
+template <int Unused = 0>
+void backward_impl(const fmm_tree* t, const double* q, const double* g, double* ug, double* fq, double* fg,
+                   cudaStream_t st) {
+  Ptrs pp = ptrs(t);
+  real* near_u = reinterpret_cast<real*>(t->near_u);
+  real* near_f = reinterpret_cast<real*>(t->near_f);
+  // near-field records of g, then of q (src32 ends up holding q)
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, g, pp.pos, pp.src, t->src_dup2,
+                                                     nullptr);
+  FMM_LAUNCH_CHECK();
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, q, pp.pos, pp.src, t->src_dup,
+                                                     nullptr);
+  FMM_LAUNCH_CHECK();
+  t->launches += 2;
+  require(t->max_leaf <= 128, "fused backward sweep needs leaves of at most 128 points");
+  if (t->max_leaf <= 32) run_p2p_bwd_tpl<1>(t, pp, st);
+  else if (t->max_leaf <= 64) run_p2p_bwd_tpl<2>(t, pp, st);
+  else run_p2p_bwd_tpl<4>(t, pp, st);
+  // far field of q and its local evaluation: the field of q
+  dispatch_p(t->prm.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    run_upward<P>(t, pp, st);
+    run_downward<P>(t, pp, st);
+    run_l2p<P>(t, pp, near_u, near_f, nullptr, fq, st);
+  });
+  // far field of g: potential and field
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, g, pp.pos, pp.src, nullptr,
+                                                     nullptr);
+  FMM_LAUNCH_CHECK();
+  t->launches += 1;
+  dispatch_p(t->prm.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    run_upward<P>(t, pp, st);
+    run_downward<P>(t, pp, st);
+    run_l2p<P>(t, pp, reinterpret_cast<real*>(t->near_u2), reinterpret_cast<real*>(t->near_f2), ug, fg, st);
+  });
 }
 
 }  // namespace

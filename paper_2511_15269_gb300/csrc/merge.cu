@@ -225,6 +225,9 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   m->Lam64 = dev_alloc<double>(m, (size_t)NB * NCP);
   m->near_u = dev_alloc<double>(m, N);
   m->near_f = dev_alloc<double>(m, 3 * (size_t)N);
+  m->src_dup2 = dev_alloc<DupRec>(m, N);
+  m->near_u2 = dev_alloc<float>(m, 2 * (size_t)N);
+  m->near_f2 = dev_alloc<float>(m, 3 * (size_t)N);
   m->q_stage = dev_alloc<double>(m, N);
   m->u_stage = dev_alloc<double>(m, N);
   m->f_stage = dev_alloc<double>(m, 3 * (size_t)N);

@@ -1308,6 +1308,11 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
   FMM_CUDA_TRY(cudaMemsetAsync(t->Lam64, 0, sizeof(double) * NB * NCP, st));
   t->near_u = dev_alloc<double>(t, n);
   t->near_f = dev_alloc<double>(t, 3 * (size_t)n);
+  if (!t->two_trees) {
+    t->src_dup2 = dev_alloc<DupRec>(t, n);
+    t->near_u2 = dev_alloc<float>(t, 2 * (size_t)n);
+    t->near_f2 = dev_alloc<float>(t, 3 * (size_t)n);
+  }
   t->q_stage = dev_alloc<double>(t, n);
   t->u_stage = dev_alloc<double>(t, n);
   t->f_stage = dev_alloc<double>(t, 3 * (size_t)n);

@@ -197,6 +197,30 @@ def test_backward_matches_oracle(F, orc):
     assert rel_l2(gp.cpu().numpy(), dp_d) < 1e-3
 
 
+@pytest.mark.parametrize("kind,leaf", [("film", 32), ("cube", 64), ("clusters", 100), ("cube", 200)])
+def test_backward_fp32c_matches_oracle(F, orc, kind, leaf):
+    """FP32C backward (fused near-field sweep for leaves up to 128 points, two
+    field evaluations above) against the oracle FMM's vector-Jacobian product."""
+    if kind == "film":
+        pos, q = workloads.thin_film(24, 1)
+    elif kind == "cube":
+        pos, q = workloads.uniform_cube(9000, 3)
+    else:
+        pos, q = workloads.gaussian_clusters(9000, 4)
+    g = np.random.default_rng(2).normal(size=len(q))
+    p = 8
+    T, O = build_both(F, orc, pos, p, leaf, 2, 0.5, F.FMM_FP32C)
+    _, fq = O.eval(q, p, field=True)
+    v, fg = O.eval(g, p, field=True)
+    dp_o = -(g[:, None] * fq + q[:, None] * fg)
+    gq, gp = F.fmm_backward(T, cuda(q), cuda(g))
+    F.fmm_tree_status(T)
+    e_q, e_p = rel_l2(gq.cpu().numpy(), v), rel_l2(gp.cpu().numpy(), dp_o)
+    print("%s leaf %d: dq %.2e dpos %.2e" % (kind, leaf, e_q, e_p))
+    assert e_q <= TOL_FP32
+    assert e_p <= TOL_FP32_FIELD
+
+
 def test_autograd_function(F, orc):
     pos, q = workloads.uniform_cube(3000, 3)
     T = F.fmm_build_tree(cuda(pos), 8, 32, 2, 0.5, F.FMM_FP64)
