@@ -27,12 +27,14 @@
  *  - Every call returns an fmm_status; on failure fmm_last_error() gives a
  *    thread-local message.  Nothing throws or aborts.
  *  - A tree owns the device workspace its evaluations use (allocated once
- *    by fmm_build_tree).  Evaluations run their stages in order on the
- *    caller's stream (stream capture included); the tree also holds a second,
- *    higher-priority stream on which a build variant overlapping the far
- *    field with the near field forks and joins M2L and L2L.  Evaluations of
- *    one tree must be ordered on one stream; two evaluations of the same tree
- *    in flight at once race.  Distinct trees are independent.
+ *    by fmm_build_tree) and a second, higher-priority CUDA stream: an
+ *    evaluation forks latency- or memory-bound stages onto it (P2M and M2M
+ *    beside the near field, the near-field slot gather beside M2L) from the
+ *    caller's stream and joins them back before the next dependent stage, so
+ *    the caller sees ordinary stream-ordered semantics (stream capture
+ *    included).  Evaluations of one tree must be ordered on one stream; two
+ *    evaluations of the same tree in flight at once race.  Distinct trees are
+ *    independent.
  */
 #ifndef GB300_FMM_H
 #define GB300_FMM_H

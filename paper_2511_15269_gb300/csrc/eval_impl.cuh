@@ -1838,14 +1838,20 @@ void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   stage_event(t, FMM_STAGE_M2M, true, st);
 }
 
-// Far field beside the near field (M2L and L2L on the tree's second stream
-// while P2P runs on the caller's stream) or before it on one stream.  Both
-// are FP32-issue bound: on the 2^20-point cube the serial order took 2.43 ms
-// per evaluation against 2.53-2.70 ms overlapped (M2L at 1-3 blocks per SM
-// beside the symmetric near field), so the stages run in order and M2L gets
-// every SM at full occupancy.  kM2LBlocksPerSM caps the M2L blocks per SM
-// when they overlap.
-constexpr bool kOverlapFarField = false;
+// Order of the stages.  The near field and the far field are independent
+// until the local evaluation.  All heavy stages (near field, M2L) are FP32
+// issue bound, so they run alone at full occupancy; what runs beside the near
+// field (on the tree's second, higher-priority stream) is only latency-bound
+// work that cannot fill the GPU by itself:
+//   kSerial:     P2M, M2M, M2L, L2L, near field, L2P on the caller's stream
+//   kUpwardSide: P2M and M2M rounds beside the near field, then M2L, L2L, L2P
+//   kFarSide:    P2M, M2M, then M2L and L2L beside the near field (M2L capped at
+//                kM2LBlocksPerSM blocks per SM)
+// Measured on the 2^20-point cube beside the symmetric near field: kFarSide
+// 2.53-2.70 ms, kSerial 2.29 ms per evaluation.
+enum { kSerial = 0, kUpwardSide = 1, kFarSide = 2 };
+constexpr int kSchedule = kUpwardSide;
+constexpr bool kOverlapFarField = kSchedule == kFarSide;
 constexpr int kM2LBlocksPerSM = 1;
 
 // Downward pass: M2L over the whole list, then L2L round by round (round r
@@ -1949,11 +1955,6 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       a.stride = t->sym_stride;
       p2p_kernel_f32s<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
-      sym_gather_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off,
-          reinterpret_cast<const float*>(t->sym_partial), (int64_t)t->sym_stride, reinterpret_cast<float*>(near_u));
-      FMM_LAUNCH_CHECK();
-      t->launches += 1;
       return;
     }
     if (field) p2p_kernel_f32h<TPL, true><<<(unsigned)blocks, 128, smem, st>>>(a);
@@ -1977,11 +1978,6 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       a.stride = t->sym_stride;
       p2p_kernel_dfs<TPL><<<(unsigned)((t->n_leaves + 3) / 4), 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
-      sym_gather_f64_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_partial,
-          (int64_t)t->sym_stride, reinterpret_cast<double*>(near_u));
-      FMM_LAUNCH_CHECK();
-      t->launches += 1;
       return;
     }
     if (!field && t->sym) {
@@ -1997,11 +1993,6 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       a.stride = t->sym_stride;
       p2p_kernel_f64s<TPL><<<(unsigned)((t->n_leaves + 3) / 4), 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
-      sym_gather_f64_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-          t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_partial,
-          (int64_t)t->sym_stride, reinterpret_cast<double*>(near_u));
-      FMM_LAUNCH_CHECK();
-      t->launches += 1;
       return;
     }
   }
@@ -2033,6 +2024,25 @@ void run_p2p(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool
   else run_p2p_tpl<8>(t, pp, near_u, near_f, field, st);
 }
 
+// Does this evaluation use the symmetric near field (whose received slots a
+// gather adds before the local evaluation)?
+bool uses_sym(const fmm_tree* t, bool field) { return !field && t->sym; }
+
+// The slot gather of the symmetric near field (after the near-field kernel).
+void run_sym_gather(const fmm_tree* t, real* near_u, cudaStream_t st) {
+  if constexpr (kF32) {
+    sym_gather_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
+        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off,
+        reinterpret_cast<const float*>(t->sym_partial), (int64_t)t->sym_stride, reinterpret_cast<float*>(near_u));
+  } else {
+    sym_gather_f64_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
+        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_partial,
+        (int64_t)t->sym_stride, reinterpret_cast<double*>(near_u));
+  }
+  FMM_LAUNCH_CHECK();
+  t->launches += 1;
+}
+
 template <class F>
 void dispatch_p(int p, F&& f) {
   switch (p) {
@@ -2061,28 +2071,60 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
   stage_event(t, FMM_STAGE_SORT, true, st);
   real* near_u = reinterpret_cast<real*>(t->near_u);
   real* near_f = reinterpret_cast<real*>(t->near_f);
-  // upward pass on the caller's stream; then either fork (M2L and L2L on the
-  // tree's higher-priority stream beside the near field on the caller's
-  // stream, joined before the local evaluation) or all on the caller's stream
-  dispatch_p(t->prm.p, [&](auto pc) {
-    constexpr int P = decltype(pc)::value;
-    run_upward<P>(t, pp, st);
-  });
-  cudaStream_t far = st;
-  if (kOverlapFarField) {
+  auto upward = [&](cudaStream_t ss) {
+    dispatch_p(t->prm.p, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      run_upward<P>(t, pp, ss);
+    });
+  };
+  auto downward = [&](cudaStream_t ss) {
+    dispatch_p(t->prm.p, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      run_downward<P>(t, pp, ss);
+    });
+  };
+  const bool sym = uses_sym(t, field != nullptr);
+  auto near = [&] {
+    stage_event(t, FMM_STAGE_P2P, false, st);
+    run_p2p(t, pp, near_u, near_f, field != nullptr, st);
+    stage_event(t, FMM_STAGE_P2P, true, st);
+  };
+  auto fork = [&] {
     FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
     FMM_CUDA_TRY(cudaStreamWaitEvent(t->far_stream, t->ev_fork, 0));
-    far = t->far_stream;
+  };
+  auto join = [&] {
+    FMM_CUDA_TRY(cudaEventRecord(t->ev_join, t->far_stream));
+    FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+  };
+  if (kSchedule == kUpwardSide) {
+    // P2M, M2M beside the near field; then the slot gather (memory bound)
+    // beside M2L and L2L (compute bound)
+    fork();
+    upward(t->far_stream);
+    near();
+    join();
+    if (sym) {
+      fork();
+      run_sym_gather(t, near_u, t->far_stream);
+      downward(st);
+      join();
+    } else {
+      downward(st);
+    }
+  } else if (kSchedule == kFarSide) {
+    upward(st);
+    fork();
+    downward(t->far_stream);
+    near();
+    if (sym) run_sym_gather(t, near_u, st);
+    join();
+  } else {
+    upward(st);
+    downward(st);
+    near();
+    if (sym) run_sym_gather(t, near_u, st);
   }
-  dispatch_p(t->prm.p, [&](auto pc) {
-    constexpr int P = decltype(pc)::value;
-    run_downward<P>(t, pp, far);
-  });
-  if (kOverlapFarField) FMM_CUDA_TRY(cudaEventRecord(t->ev_join, far));
-  stage_event(t, FMM_STAGE_P2P, false, st);
-  run_p2p(t, pp, near_u, near_f, field != nullptr, st);
-  stage_event(t, FMM_STAGE_P2P, true, st);
-  if (kOverlapFarField) FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
   stage_event(t, FMM_STAGE_L2P, false, st);
   dispatch_p(t->prm.p, [&](auto pc) {
     constexpr int P = decltype(pc)::value;
