@@ -252,14 +252,15 @@ def test_edge_cases(F, orc):
     # coincident points contribute nothing to each other
     pos = np.array([[0.1, 0.2, 0.3]] * 3 + [[0.9, 0.8, 0.7]])
     q = np.array([1.0, 2.0, 3.0, 4.0])
-    for prec in (F.FMM_FP64, F.FMM_FP32C):
+    for prec in (F.FMM_FP64, F.FMM_FP32C, F.FMM_FP64DF):
         T = F.fmm_build_tree(cuda(pos), 4, 4, 2, 0.5, prec)
         u = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
         np.testing.assert_allclose(u, orc.direct(pos, q), rtol=1e-6)
     # all points identical: zero radius everywhere
     pos = np.zeros((40, 3)) + 0.25
-    T = F.fmm_build_tree(cuda(pos), 4, 4, 2, 0.5, F.FMM_FP32C)
-    assert np.all(F.fmm_eval_potential(T, cuda(np.ones(40))).cpu().numpy() == 0.0)
+    for prec in (F.FMM_FP64, F.FMM_FP32C, F.FMM_FP64DF):
+        T = F.fmm_build_tree(cuda(pos), 4, 4, 2, 0.5, prec)
+        assert np.all(F.fmm_eval_potential(T, cuda(np.ones(40))).cpu().numpy() == 0.0)
     # non-finite positions are rejected
     bad = workloads.uniform_cube(100, 0)[0]
     bad[7, 1] = np.nan
