@@ -288,3 +288,81 @@ def test_cube1m_p8_full_size(F, orc):
           % (rel_l2(u32, ud), rel_l2(u64, ud), rel_l2(u64, uo)))
     assert rel_l2(u64, uo) <= TOL_FP64
     assert rel_l2(u32, ud) <= 1e-6
+
+
+def test_plummer4m_p10_full_size(F, orc):
+    """Highly non-uniform N = 2^22 (70% Plummer + 30% sphere surface), p = 10,
+    leaf 64, theta 0.5, in the launch configuration the benchmark times: the
+    balanced box counts of the median split, and FP32C, FP64 and FP64DF
+    potentials against the FP64 direct sum on sampled targets (the FMM
+    truncation at theta 0.5 bounds the error near 1.4e-6)."""
+    c = workloads.CONFIGS["plummer4m_p10"]
+    pos, q = workloads.plummer_sphere(c["n"], seed=0)
+    T = F.fmm_build_tree(cuda(pos), c["p"], c["leaf_size"], c["s"], c["theta"], F.FMM_FP32C)
+    st = F.fmm_tree_stats(T)
+    L, s = st["levels"], c["s"]
+    assert L == orc.num_levels(c["n"], c["leaf_size"], s)
+    counts = F.fmm_tree_export(T)["box_count"]
+    off = 0
+    for l in range(L + 1):
+        nb = 1 << (s * l)
+        lv = counts[off:off + nb]
+        assert lv.sum() == c["n"] and lv.max() - lv.min() <= 1  # ceil / floor of N / 4^l
+        off += nb
+    tg = workloads.sample_targets(c["n"], 1024, seed=1)
+    ud = orc.direct(pos, q, targets=tg)
+    qd = cuda(q)
+    errs = {}
+    for name, prec in (("fp32c", F.FMM_FP32C), ("fp64", F.FMM_FP64), ("fp64df", F.FMM_FP64DF)):
+        F.fmm_tree_set_precision(T, prec)
+        errs[name] = rel_l2(F.fmm_eval_potential(T, qd).cpu().numpy()[tg], ud)
+    F.fmm_tree_status(T)
+    print("plummer4m:", {k: "%.3e" % v for k, v in errs.items()})
+    assert all(v < 3e-6 for v in errs.values())
+    assert abs(errs["fp64df"] - errs["fp64"]) < 1e-9
+
+
+def test_batched64_p6_full_size(F, orc):
+    """64 charge sets of log-uniform size in [1e4, 5e5] (7.9 M points), p = 6,
+    theta 0.6, merged into one batch and replayed from a CUDA graph as the
+    benchmark does: every set's potential against its own direct sum on
+    sampled targets, and the batch equal to the sets evaluated alone."""
+    from paper_2511_15269_gb300 import autotune
+    c = workloads.CONFIGS["batched64_p6"]
+    sets = workloads.batched_sets(64, seed=0)
+    B = autotune.build_batch([p for p, _ in sets], c["p"], 64, c["s"], c["theta"], F.FMM_FP32C)
+    qd = cuda(np.concatenate([q for _, q in sets]))
+    u = torch.empty_like(qd)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        F.fmm_eval_potential(B, qd, u)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        F.fmm_eval_potential(B, qd, u)
+    u.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    uu = u.cpu().numpy()
+    off = F.fmm_tree_point_offsets(B)
+    rng = np.random.default_rng(3)
+    num = den = 0.0
+    for k, (pos, q) in enumerate(sets):
+        tg = np.sort(rng.choice(len(q), 32, replace=False)).astype(np.int64)
+        ud = orc.direct(pos, q, targets=tg)
+        num += float(np.sum((uu[off[k] + tg] - ud) ** 2))
+        den += float(np.sum(ud ** 2))
+        if k % 16 == 0:  # a few sets alone, bit for bit
+            T = F.fmm_build_tree(cuda(pos), c["p"], 64, c["s"], c["theta"], F.FMM_FP32C)
+            np.testing.assert_array_equal(uu[off[k]:off[k + 1]], F.fmm_eval_potential(T, cuda(q)).cpu().numpy())
+    F.fmm_tree_status(B)
+    err = (num / den) ** 0.5
+    print("batched64: rel L2 vs direct %.3e" % err)
+    assert err < 1e-3
+
+
+def test_empty_input_rejected(F):
+    with pytest.raises(F.FmmError) as ei:
+        F.fmm_build_tree(torch.zeros((0, 3), dtype=torch.float64, device="cuda"), 4, 16, 2, 0.5, F.FMM_FP32C)
+    assert ei.value.code == F.FMM_ERR_INVALID_ARG
