@@ -66,7 +66,7 @@ void free_tree(fmm_tree* t) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (t->prof_ev) {
-    for (int i = 0; i < fmm_tree::kProfCalls * FMM_NUM_STAGES * 2; i++) cudaEventDestroy(t->prof_ev[i]);
+    for (int i = 0; i < fmm_tree::kProfCalls * fmm_tree::kProfSlots * 2; i++) cudaEventDestroy(t->prof_ev[i]);
     delete[] t->prof_ev;
   }
   if (t->ev_fork) cudaEventDestroy(t->ev_fork);
@@ -245,7 +245,7 @@ int fmm_tree_profile(fmm_tree* t, int enable) {
   return guarded([&] {
     require(t != nullptr, "tree is NULL");
     if (enable && !t->prof_ev) {
-      const int ne = fmm_tree::kProfCalls * FMM_NUM_STAGES * 2;
+      const int ne = fmm_tree::kProfCalls * fmm_tree::kProfSlots * 2;
       t->prof_ev = new cudaEvent_t[ne];
       for (int i = 0; i < ne; i++) FMM_CUDA_TRY(cudaEventCreate(&t->prof_ev[i]));
     }
@@ -261,12 +261,12 @@ int fmm_tree_stage_times(const fmm_tree* t, double* ms, int64_t* calls) {
     if (calls) *calls = t->prof_ev ? t->prof_used : 0;
     if (!t->prof_ev) return;
     for (int c = 0; c < t->prof_used; c++) {
-      cudaEvent_t* ev = t->prof_ev + c * FMM_NUM_STAGES * 2;
-      for (int s = 0; s < FMM_NUM_STAGES; s++) {
+      cudaEvent_t* ev = t->prof_ev + c * fmm_tree::kProfSlots * 2;
+      for (int s = 0; s < fmm_tree::kProfSlots; s++) {
         FMM_CUDA_TRY(cudaEventSynchronize(ev[2 * s + 1]));
         float x = 0.f;
         FMM_CUDA_TRY(cudaEventElapsedTime(&x, ev[2 * s], ev[2 * s + 1]));
-        ms[s] += x;
+        ms[s == fmm_tree::kStageP2P2 ? FMM_STAGE_P2P : s] += x;
       }
     }
   });

@@ -221,7 +221,11 @@ struct fmm_tree {
 
   // per-stage timing (fmm_tree_profile) and launch accounting
   static constexpr int kProfCalls = 512;
-  cudaEvent_t* prof_ev = nullptr;      // kProfCalls x FMM_NUM_STAGES x {begin, end}
+  // per call and stage {begin, end}; one slot beyond the public stages holds
+  // the second launch of a near field run in two parts (added to P2P)
+  static constexpr int kProfSlots = FMM_NUM_STAGES + 1;
+  static constexpr int kStageP2P2 = FMM_NUM_STAGES;
+  cudaEvent_t* prof_ev = nullptr;      // kProfCalls x kProfSlots x {begin, end}
   mutable int prof_on = 0;
   mutable int prof_used = 0;
   mutable int prof_cur = -1;           // slot of the call being recorded
@@ -237,7 +241,7 @@ inline void stage_event(const fmm_tree* t, int s, bool end, cudaStream_t st) {
   if (s == FMM_STAGE_SORT && !end) {
     t->prof_cur = (t->prof_used < fmm_tree::kProfCalls) ? t->prof_used++ : -1;
   }
-  if (t->prof_cur >= 0) cudaEventRecord(t->prof_ev[(t->prof_cur * FMM_NUM_STAGES + s) * 2 + (end ? 1 : 0)], st);
+  if (t->prof_cur >= 0) cudaEventRecord(t->prof_ev[(t->prof_cur * fmm_tree::kProfSlots + s) * 2 + (end ? 1 : 0)], st);
 }
 
 // tree_build.cu

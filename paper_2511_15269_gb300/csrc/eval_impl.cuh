@@ -1847,9 +1847,14 @@ void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 //   kUpwardSide: P2M and M2M rounds beside the near field, then M2L, L2L, L2P
 //   kFarSide:    P2M, M2M, then M2L and L2L beside the near field (M2L capped at
 //                kM2LBlocksPerSM blocks per SM)
-// Measured on the 2^20-point cube beside the symmetric near field: kFarSide
-// 2.53-2.70 ms, kSerial 2.29 ms per evaluation.
-enum { kSerial = 0, kUpwardSide = 1, kFarSide = 2 };
+// Measured beside the symmetric near field (ms per evaluation, 2^20-point
+// cube / 2^18-point cube / 2^22-point Plummer): kFarSide 2.53-2.70 / - / -,
+// kSerial 2.29 / 0.650 / 54.5, kUpwardSide 2.20 / 0.622 / 46.7,
+// kSplitNear 2.25 / 0.588 / 55.9.
+//   kSplitNear:  the near field in two launches (heaviest leaves first): P2M
+//                and M2M beside the first, M2L alone, L2L beside the second,
+//                then the slot gather and L2P
+enum { kSerial = 0, kUpwardSide = 1, kFarSide = 2, kSplitNear = 3 };
 constexpr int kSchedule = kUpwardSide;
 constexpr bool kOverlapFarField = kSchedule == kFarSide;
 constexpr int kM2LBlocksPerSM = 1;
@@ -1857,7 +1862,7 @@ constexpr int kM2LBlocksPerSM = 1;
 // Downward pass: M2L over the whole list, then L2L round by round (round r
 // holds the boxes at depth r + 1 of every tree in the batch).
 template <int P>
-void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+void run_m2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   const size_t smem = (size_t)4 * ncoef(P) * 32 * sizeof(real);
   static bool attr_set = false;
   if (!attr_set) {
@@ -1878,8 +1883,14 @@ void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   m2l_kernel<P><<<(int)blocks, 128, smem, st>>>(t->n_boxes, t->m2l_order, t->m2l_off, t->m2l_src,
                                                 pp.geo, t->n_m2l, pp.M, pp.Lam, t->counters);
   FMM_LAUNCH_CHECK();
-  t->launches += 1 + t->n_down;
+  t->launches += 1;
   stage_event(t, FMM_STAGE_M2L, true, st);
+}
+
+// L2L round by round (round r holds the boxes at depth r + 1 of every tree)
+template <int P>
+void run_l2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+  t->launches += t->n_down;
   stage_event(t, FMM_STAGE_L2L, false, st);
   for (int r = 0; r < t->n_down; r++) {
     const int64_t nb = t->down_off_h[r + 1] - t->down_off_h[r];
@@ -1888,6 +1899,12 @@ void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
     FMM_LAUNCH_CHECK();
   }
   stage_event(t, FMM_STAGE_L2L, true, st);
+}
+
+template <int P>
+void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+  run_m2l<P>(t, pp, st);
+  run_l2l<P>(t, pp, st);
 }
 
 template <int P>
@@ -1906,14 +1923,14 @@ void run_l2p(const fmm_tree* t, const Ptrs& pp, const real* near_u, const real* 
 }
 
 template <int TPL>
-void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool field,
-                 cudaStream_t st) {
+void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool field, int64_t lb,
+                 int64_t le, cudaStream_t st) {
   P2PArgs a{};
-  a.n_leaves = t->n_leaves;
+  a.n_leaves = le - lb;  // positions lb .. le - 1 of the work order
   a.leaf_box = t->leaf_box;
   a.src_leaf_box = t->src_leaf_box;
   a.self_pairs = t->two_trees ? 0 : 1;
-  a.order = t->leaf_order;
+  a.order = t->leaf_order + lb;
   a.off = t->p2p_off;
   a.ent32 = t->p2p32;
   a.thr = t->p2p_thr;
@@ -1939,7 +1956,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
                                         (int)cudaSharedmemCarveoutMaxShared));
       attr_set = true;
     }
-    const int64_t blocks = (t->n_leaves + 3) / 4;
+    const int64_t blocks = (a.n_leaves + 3) / 4;
     if (!field && t->sym) {
       static bool sym_attr = false;
       if (!sym_attr) {
@@ -1948,7 +1965,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
                                           (int)cudaSharedmemCarveoutMaxShared));
         sym_attr = true;
       }
-      a.order = t->leaf_order_sym;
+      a.order = t->leaf_order_sym + lb;
       a.work_off = t->sym_work_off;
       a.rec = t->sym_rec;
       a.partial = t->sym_partial;
@@ -1969,14 +1986,14 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
         FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_dfs<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         df_attr = true;
       }
-      a.order = t->leaf_order_sym;
+      a.order = t->leaf_order_sym + lb;
       a.work_off = t->sym_work_off;
       a.rec = t->sym_rec;
       a.frame = t->sym_frame;
       a.df_tile = t->src_df;
       a.partial = t->sym_partial;
       a.stride = t->sym_stride;
-      p2p_kernel_dfs<TPL><<<(unsigned)((t->n_leaves + 3) / 4), 128, smem, st>>>(a);
+      p2p_kernel_dfs<TPL><<<(unsigned)((a.n_leaves + 3) / 4), 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
       return;
     }
@@ -1986,12 +2003,12 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
         FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f64s<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         sym_attr = true;
       }
-      a.order = t->leaf_order_sym;
+      a.order = t->leaf_order_sym + lb;
       a.work_off = t->sym_work_off;
       a.rec = t->sym_rec;
       a.partial = t->sym_partial;
       a.stride = t->sym_stride;
-      p2p_kernel_f64s<TPL><<<(unsigned)((t->n_leaves + 3) / 4), 128, smem, st>>>(a);
+      p2p_kernel_f64s<TPL><<<(unsigned)((a.n_leaves + 3) / 4), 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
       return;
     }
@@ -2010,18 +2027,21 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
   else FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_kernel<TPL, false>, 128, smem));
   if (occ < 1) occ = 1;
   int64_t blocks = (int64_t)nsm * occ;
-  const int64_t need = (t->n_leaves + 3) / 4;
+  const int64_t need = (a.n_leaves + 3) / 4;
   if (blocks > need) blocks = need;
   if (field) p2p_kernel<TPL, true><<<(int)blocks, 128, smem, st>>>(a);
   else p2p_kernel<TPL, false><<<(int)blocks, 128, smem, st>>>(a);
   FMM_LAUNCH_CHECK();
 }
 
-void run_p2p(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool field, cudaStream_t st) {
-  if (t->max_leaf <= 32) run_p2p_tpl<1>(t, pp, near_u, near_f, field, st);
-  else if (t->max_leaf <= 64) run_p2p_tpl<2>(t, pp, near_u, near_f, field, st);
-  else if (t->max_leaf <= 128) run_p2p_tpl<4>(t, pp, near_u, near_f, field, st);
-  else run_p2p_tpl<8>(t, pp, near_u, near_f, field, st);
+// Near field of the leaves at positions lb .. le - 1 of the work order.
+void run_p2p(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool field, int64_t lb, int64_t le,
+             cudaStream_t st) {
+  if (le <= lb) return;
+  if (t->max_leaf <= 32) run_p2p_tpl<1>(t, pp, near_u, near_f, field, lb, le, st);
+  else if (t->max_leaf <= 64) run_p2p_tpl<2>(t, pp, near_u, near_f, field, lb, le, st);
+  else if (t->max_leaf <= 128) run_p2p_tpl<4>(t, pp, near_u, near_f, field, lb, le, st);
+  else run_p2p_tpl<8>(t, pp, near_u, near_f, field, lb, le, st);
 }
 
 // Does this evaluation use the symmetric near field (whose received slots a
@@ -2069,6 +2089,9 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
   FMM_LAUNCH_CHECK();
   t->launches += 1;
   stage_event(t, FMM_STAGE_SORT, true, st);
+  // the slot of a second near-field launch is recorded empty unless used
+  stage_event(t, fmm_tree::kStageP2P2, false, st);
+  stage_event(t, fmm_tree::kStageP2P2, true, st);
   real* near_u = reinterpret_cast<real*>(t->near_u);
   real* near_f = reinterpret_cast<real*>(t->near_f);
   auto upward = [&](cudaStream_t ss) {
@@ -2084,10 +2107,23 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     });
   };
   const bool sym = uses_sym(t, field != nullptr);
-  auto near = [&] {
-    stage_event(t, FMM_STAGE_P2P, false, st);
-    run_p2p(t, pp, near_u, near_f, field != nullptr, st);
-    stage_event(t, FMM_STAGE_P2P, true, st);
+  auto near_range = [&](int64_t lb, int64_t le, int stage) {
+    stage_event(t, stage, false, st);
+    run_p2p(t, pp, near_u, near_f, field != nullptr, lb, le, st);
+    stage_event(t, stage, true, st);
+  };
+  auto near = [&] { near_range(0, t->n_leaves, FMM_STAGE_P2P); };
+  auto m2l = [&](cudaStream_t ss) {
+    dispatch_p(t->prm.p, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      run_m2l<P>(t, pp, ss);
+    });
+  };
+  auto l2l = [&](cudaStream_t ss) {
+    dispatch_p(t->prm.p, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      run_l2l<P>(t, pp, ss);
+    });
   };
   auto fork = [&] {
     FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
@@ -2097,7 +2133,19 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     FMM_CUDA_TRY(cudaEventRecord(t->ev_join, t->far_stream));
     FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
   };
-  if (kSchedule == kUpwardSide) {
+  if (kSchedule == kSplitNear) {
+    const int64_t half = t->n_leaves / 2;
+    fork();
+    upward(t->far_stream);
+    near_range(0, half, FMM_STAGE_P2P);
+    join();
+    m2l(st);
+    fork();
+    l2l(t->far_stream);
+    near_range(half, t->n_leaves, fmm_tree::kStageP2P2);
+    if (sym) run_sym_gather(t, near_u, st);
+    join();
+  } else if (kSchedule == kUpwardSide) {
     // P2M, M2M beside the near field; then the slot gather (memory bound)
     // beside M2L and L2L (compute bound)
     fork();
