@@ -58,9 +58,9 @@ void free_tree(fmm_tree* t) {
   void* ptrs[] = {t->perm,     t->box_start, t->box_count, t->center,   t->radius,   t->m2l_off,  t->m2l_src,
                   t->m2l_trg,  t->m2l_order, t->p2p_off,   t->p2p_src,  t->p2p32,    t->leaf_order, t->pos_local,
                   t->pos64,    t->inv_rho32, t->inv_rho64, t->geo32,    t->geo64,    t->m2m32,    t->m2m64,
-                  t->l2l32,    t->l2l64,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
+                  t->l2d32,    t->l2d64,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
                   t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
-                  t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->down_ids,
+                  t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->l2d_off, t->l2d_anc,
                   t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr, t->sym_slot, t->sym_work_off,
                   t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec, t->src_df, t->sym_frame, t->src_dup2, t->near_u2, t->near_f2};
   for (void* p : ptrs)
@@ -74,7 +74,6 @@ void free_tree(fmm_tree* t) {
   if (t->far_stream) cudaStreamDestroy(t->far_stream);
   delete[] t->level_avg_host;
   delete[] t->up_off_h;
-  delete[] t->down_off_h;
   delete[] t->tree_point_off_h;
   delete t;
 }

@@ -155,13 +155,16 @@ struct fmm_tree {
   int32_t* leaf_order = nullptr;   // n_leaves: target leaves, most work first
   int32_t* leaf_box = nullptr;     // n_leaves: global box id of each leaf
   int32_t* box_parent = nullptr;   // n_boxes: parent box id (-1 for a root)
-  // M2M rounds (bottom-up) and L2L rounds (top-down): device lists of box
-  // ids with host offsets; the children of a parent are consecutive
-  int n_up = 0, n_down = 0;
+  // M2M rounds (bottom-up): device lists of box ids with host offsets; the
+  // children of a parent are consecutive
+  int n_up = 0;
   int64_t* up_off_h = nullptr;     // n_up + 1
-  int64_t* down_off_h = nullptr;   // n_down + 1
   int32_t* up_ids = nullptr;
-  int32_t* down_ids = nullptr;
+  // L2L in direct form: per target leaf, its ancestors with a non-empty M2L
+  // list (nearest first), CSR by leaf
+  int64_t n_l2d = 0;
+  int64_t* l2d_off = nullptr;      // n_leaves + 1
+  int32_t* l2d_anc = nullptr;      // n_l2d ancestor boxes
   int n_trees = 1;                 // > 1 for a merged batch of trees
   int64_t* tree_point_off_h = nullptr;  // n_trees + 1 (merged batches)
   // Roles of points and leaves.  One point set: every point carries a charge
@@ -189,8 +192,8 @@ struct fmm_tree {
   double* geo64 = nullptr;
   float* m2m32 = nullptr;        // edge_fields(p) x n_boxes (row = child id)
   double* m2m64 = nullptr;
-  float* l2l32 = nullptr;
-  double* l2l64 = nullptr;
+  float* l2d32 = nullptr;         // edge_fields(p) x n_l2d (row = record)
+  double* l2d64 = nullptr;
 
   // evaluation workspace
   float4* src32 = nullptr;       // n: (x_local, q) in tree order
@@ -250,6 +253,9 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st);
 void build_tree2(fmm_tree* t, const double* src, int64_t n_src, const double* trg, int64_t n_trg, cudaStream_t st);
 // symmetric.cu: symmetric near-field metadata of a one-point-set tree or batch
 void build_symmetric(fmm_tree* t, cudaStream_t st);
+// tree_build.cu: the direct L2L records of a tree with lists, geometry and
+// parents in place
+void build_l2l_direct(fmm_tree* t, cudaStream_t st);
 // api.cu: releases every device array, stream and event of a tree
 void free_tree(fmm_tree* t);
 // merge.cu: a batch of trees as one tree-shaped object

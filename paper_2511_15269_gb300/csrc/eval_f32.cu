@@ -11,7 +11,7 @@ using real = float;
 namespace fmm {
 namespace {
 Ptrs ptrs(const fmm_tree* t) {
-  return Ptrs{t->pos_local, t->src32, t->inv_rho32, t->geo32, t->m2m32, t->l2l32, t->M32, t->Lam32};
+  return Ptrs{t->pos_local, t->src32, t->inv_rho32, t->geo32, t->m2m32, t->l2d32, t->M32, t->Lam32};
 }
 }  // namespace
 void eval_fp32(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {

@@ -8,7 +8,7 @@ using real = double;
 namespace fmm {
 namespace {
 Ptrs ptrs(const fmm_tree* t) {
-  return Ptrs{t->pos64, t->src64, t->inv_rho64, t->geo64, t->m2m64, t->l2l64, t->M64, t->Lam64};
+  return Ptrs{t->pos64, t->src64, t->inv_rho64, t->geo64, t->m2m64, t->l2d64, t->M64, t->Lam64};
 }
 }  // namespace
 void eval_fp64(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {

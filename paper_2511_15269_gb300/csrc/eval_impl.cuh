@@ -95,8 +95,14 @@ __global__ void gather_kernel(int64_t n, int64_t n_charges, const int32_t* __res
   }
 }
 
-// ---- E1: P2M, one warp per leaf ----------------------------------------------
+// ---- E1: P2M, a group of kP2MGroup lanes per leaf ---------------------------
 // M^m_n = sum_i q_i Rt^m_n((x_i - c) / rho)   (Sec. II.C in the scaled basis)
+// Lane j of a group accumulates the points j, j + G, ... of its leaf; the
+// group's sums are combined by an xor butterfly (log2 G shuffle stages per
+// coefficient, against 5 for a whole warp) and lane j stores coefficients
+// c = j (mod G).
+constexpr int kP2MGroup = 4;
+
 template <int P>
 __global__ void __launch_bounds__(128) p2m_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
                                                   const int64_t* __restrict__ box_start,
@@ -105,47 +111,47 @@ __global__ void __launch_bounds__(128) p2m_kernel(int64_t n_leaves, const int32_
                                                   const vec4* __restrict__ src,
                                                   const real* __restrict__ inv_rho,
                                                   real* __restrict__ M) {
+  constexpr int G = kP2MGroup;
   constexpr int NC = ncoef(P);
-  const int lane = lane_id();
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-  for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves;
-       leaf += warps) {
-    const int64_t g = leaf_box[leaf];
-    const int64_t start = box_start[g];
-    const int cnt = box_count[g];
-    const real ir = inv_rho[g];
-    real cx = 0, cy = 0, cz = 0;
-    if (!kF32) {
-      cx = (real)center[3 * g];
-      cy = (real)center[3 * g + 1];
-      cz = (real)center[3 * g + 2];
-    }
-    real acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; c++) acc[c] = real(0);
-    for (int i = lane; i < cnt; i += 32) {
-      const vec4 s = src[start + i];
-      const real x = ((real)s.x - cx) * ir, y = ((real)s.y - cy) * ir, z = ((real)s.z - cz) * ir;
-      const real q = (real)s.w;
-      real R[NC];
-      regular_basis<P>(x, y, z, R, [&](auto nn) {
-        constexpr int n = decltype(nn)::value;
-#pragma unroll
-        for (int c = n * n; c < (n + 1) * (n + 1); c++) acc[c] = fmar(q, R[c], acc[c]);
-      });
-    }
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-      real v = acc[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[c] = v;
-    }
-    real* out = M + g * ncoef_pad(P);
-#pragma unroll
-    for (int c = 0; c < NC; c++)
-      if ((c & 31) == lane) out[c] = acc[c];
+  const int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  if (leaf >= n_leaves) return;  // whole groups leave together
+  const int j = threadIdx.x % G;
+  const unsigned gmask = ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  const int64_t g = leaf_box[leaf];
+  const int64_t start = box_start[g];
+  const int cnt = box_count[g];
+  const real ir = inv_rho[g];
+  real cx = 0, cy = 0, cz = 0;
+  if (!kF32) {
+    cx = (real)center[3 * g];
+    cy = (real)center[3 * g + 1];
+    cz = (real)center[3 * g + 2];
   }
+  real acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c++) acc[c] = real(0);
+  for (int i = j; i < cnt; i += G) {
+    const vec4 s = src[start + i];
+    const real x = ((real)s.x - cx) * ir, y = ((real)s.y - cy) * ir, z = ((real)s.z - cz) * ir;
+    const real q = (real)s.w;
+    real R[NC];
+    regular_basis<P>(x, y, z, R, [&](auto nn) {
+      constexpr int n = decltype(nn)::value;
+#pragma unroll
+      for (int c = n * n; c < (n + 1) * (n + 1); c++) acc[c] = fmar(q, R[c], acc[c]);
+    });
+  }
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    real v = acc[c];
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(gmask, v, o);
+    acc[c] = v;
+  }
+  real* out = M + g * ncoef_pad(P);
+#pragma unroll
+  for (int c = 0; c < NC; c++)
+    if (c % G == j) out[c] = acc[c];
 }
 
 // ---- E2: M2M, one thread per child box of level l+1 -------------------------
@@ -238,27 +244,59 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
   }
 }
 
-// ---- E4: L2L, one thread per box of level l; adds into its own M2L local ----
+// ---- E4: L2L in direct form, a group of kL2LGroup lanes per target leaf ----
+// The local expansion of a leaf is the chain of Sec. II.C: its own M2L sum
+// plus L2L of its parent's complete local.  Unrolled, that is the leaf's M2L
+// sum plus, over every ancestor a, L2L(a -> leaf) of a's own M2L sum: a local
+// expansion of degree p is a polynomial of degree p, which a translation maps
+// exactly onto the same degrees, so translations compose without truncation
+// and the two forms differ by rounding only.  The direct form needs one
+// launch instead of one round per level; only ancestors with a non-empty M2L
+// list have records.  Lanes of a group translate the leaf's records in turn,
+// the group sums the translated expansions by an xor butterfly (the same sum,
+// bit for bit, on every lane) and lane j adds coefficients c = j (mod the
+// group size) to the leaf's own M2L sum.  Internal boxes keep their M2L sums.
+constexpr int kL2LGroup = 8;
+
 template <int P>
-__global__ void __launch_bounds__(128) l2l_kernel(int64_t n_box, const int32_t* __restrict__ box,
-                                                  const int32_t* __restrict__ parent,
-                                                  const real* __restrict__ edge,
-                                                  int64_t edge_stride, real* __restrict__ Lam) {
+__global__ void __launch_bounds__(128) l2l_direct_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
+                                                         const int64_t* __restrict__ off,
+                                                         const int32_t* __restrict__ anc,
+                                                         const real* __restrict__ edge, int64_t n_rec,
+                                                         real* __restrict__ Lam) {
+  constexpr int G = kL2LGroup;
   constexpr int NC = ncoef(P);
   constexpr int NCP = ncoef_pad(P);
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_box) return;
-  const int64_t g = box[t];
-  const int64_t gp = parent[g];
-  real v[NC];
-  load_coef<P>(Lam + gp * NCP, v);
-  const real a = edge[0 * edge_stride + g], b = edge[1 * edge_stride + g];
-  real cp[P], sp[P], ct[P], st[P];
-  load_trig<P>(edge, edge_stride, g, 2, cp, sp, ct, st);
-  translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_l2l<P>(w, a, b); });
-  real* out = Lam + g * NCP;
+  const int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  if (leaf >= n_leaves) return;  // whole groups leave together
+  const int j = threadIdx.x % G;
+  const unsigned gmask = ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  const int64_t b = off[leaf], e = off[leaf + 1];
+  real* out = Lam + (int64_t)leaf_box[leaf] * NCP;
+  for (int64_t r0 = b; r0 < e; r0 += G) {
+    const int64_t i = r0 + j;
+    real v[NC];
+    if (i < e) {
+      load_coef<P>(Lam + (int64_t)anc[i] * NCP, v);
+      const real a = edge[i], bb = edge[n_rec + i];
+      real cp[P], sp[P], ct[P], st[P];
+      load_trig<P>(edge, n_rec, i, 2, cp, sp, ct, st);
+      translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_l2l<P>(w, a, bb); });
+    } else {
 #pragma unroll
-  for (int c = 0; c < NC; c++) out[c] = out[c] + v[c];
+      for (int c = 0; c < NC; c++) v[c] = real(0);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      real x = v[c];
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) x += __shfl_xor_sync(gmask, x, o);
+      v[c] = x;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; c++)
+      if (c % G == j) out[c] += v[c];
+  }
 }
 
 // ---- E6: P2P, persistent; one warp per target leaf ---------------------------
@@ -1810,7 +1848,7 @@ struct Ptrs {
   const real* inv_rho;
   const real* geo;
   const real* m2m;
-  const real* l2l;
+  const real* l2d;  // direct L2L records
   real* M;
   real* Lam;
 };
@@ -1823,7 +1861,7 @@ template <int P>
 void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   const int nch = 1 << t->s;
   stage_event(t, FMM_STAGE_P2M, false, st);
-  p2m_kernel<P><<<grid_for(t->n_src_leaves * 32, 128), 128, 0, st>>>(
+  p2m_kernel<P><<<grid_for(t->n_src_leaves * kP2MGroup, 128, 1 << 30), 128, 0, st>>>(
       t->n_src_leaves, t->src_leaf_box, t->box_start, t->box_count, t->center, pp.src, pp.inv_rho, pp.M);
   FMM_LAUNCH_CHECK();
   t->launches += 1 + t->n_up;
@@ -1887,16 +1925,15 @@ void run_m2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   stage_event(t, FMM_STAGE_M2L, true, st);
 }
 
-// L2L round by round (round r holds the boxes at depth r + 1 of every tree)
+// L2L in direct form: one launch over the target leaves
 template <int P>
 void run_l2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
-  t->launches += t->n_down;
   stage_event(t, FMM_STAGE_L2L, false, st);
-  for (int r = 0; r < t->n_down; r++) {
-    const int64_t nb = t->down_off_h[r + 1] - t->down_off_h[r];
-    l2l_kernel<P><<<grid_for(nb, 128, 1 << 30), 128, 0, st>>>(nb, t->down_ids + t->down_off_h[r], t->box_parent,
-                                                             pp.l2l, t->n_boxes, pp.Lam);
+  if (t->n_l2d > 0) {
+    l2l_direct_kernel<P><<<grid_for(t->n_leaves * kL2LGroup, 128, 1 << 30), 128, 0, st>>>(
+        t->n_leaves, t->leaf_box, t->l2d_off, t->l2d_anc, pp.l2d, t->n_l2d, pp.Lam);
     FMM_LAUNCH_CHECK();
+    t->launches += 1;
   }
   stage_event(t, FMM_STAGE_L2L, true, st);
 }

@@ -115,8 +115,6 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   m->geo64 = dev_alloc<double>(m, (size_t)m2l_fields(p) * std::max<int64_t>(NM, 1));
   m->m2m32 = dev_alloc<float>(m, (size_t)edge_fields(p) * NB);
   m->m2m64 = dev_alloc<double>(m, (size_t)edge_fields(p) * NB);
-  m->l2l32 = dev_alloc<float>(m, (size_t)edge_fields(p) * NB);
-  m->l2l64 = dev_alloc<double>(m, (size_t)edge_fields(p) * NB);
 
   for (int k = 0; k < nt; k++) {
     const fmm_tree& t = *in[k];
@@ -145,8 +143,6 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
     copy_rows(m->geo64, NM, mo[k], t.geo64, t.n_m2l, m2l_fields(p), st);
     copy_rows(m->m2m32, NB, bo[k], t.m2m32, t.n_boxes, edge_fields(p), st);
     copy_rows(m->m2m64, NB, bo[k], t.m2m64, t.n_boxes, edge_fields(p), st);
-    copy_rows(m->l2l32, NB, bo[k], t.l2l32, t.n_boxes, edge_fields(p), st);
-    copy_rows(m->l2l64, NB, bo[k], t.l2l64, t.n_boxes, edge_fields(p), st);
   }
   {
     const int64_t tails[2] = {NM, NP};
@@ -155,36 +151,29 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
   }
 
-  // rounds: M2M round r takes, from every tree with L > r, its level L - r;
-  // L2L round r its level r + 1
+  // rounds: M2M round r takes, from every tree with L > r, its level L - r
   auto loff = [&](int l) {
     int64_t o = 0;
     for (int i = 0; i < l; i++) o += (int64_t)1 << (s * i);
     return o;
   };
-  std::vector<int32_t> up, down;
-  m->n_up = m->n_down = Lmax;
+  std::vector<int32_t> up;
+  m->n_up = Lmax;
   m->up_off_h = new int64_t[Lmax + 1];
-  m->down_off_h = new int64_t[Lmax + 1];
   for (int r = 0; r < Lmax; r++) {
     m->up_off_h[r] = (int64_t)up.size();
-    m->down_off_h[r] = (int64_t)down.size();
     for (int k = 0; k < nt; k++) {
       const int L = in[k]->L;
-      if (L > r) {
+      if (L > r)
         for (int64_t g = loff(L - r); g < loff(L - r + 1); g++) up.push_back((int32_t)(bo[k] + g));
-        for (int64_t g = loff(r + 1); g < loff(r + 2); g++) down.push_back((int32_t)(bo[k] + g));
-      }
     }
   }
   m->up_off_h[Lmax] = (int64_t)up.size();
-  m->down_off_h[Lmax] = (int64_t)down.size();
   m->up_ids = dev_alloc<int32_t>(m, std::max<size_t>(up.size(), 1));
-  m->down_ids = dev_alloc<int32_t>(m, std::max<size_t>(down.size(), 1));
   if (!up.empty())
     FMM_CUDA_TRY(cudaMemcpyAsync(m->up_ids, up.data(), sizeof(int32_t) * up.size(), cudaMemcpyHostToDevice, st));
-  if (!down.empty())
-    FMM_CUDA_TRY(cudaMemcpyAsync(m->down_ids, down.data(), sizeof(int32_t) * down.size(), cudaMemcpyHostToDevice, st));
+  // locals reach the leaves of every tree by direct L2L records
+  build_l2l_direct(m, st);
 
   // work orders over the whole batch: longest M2L lists and heaviest near
   // fields first

@@ -564,14 +564,13 @@ __global__ void box_range_kernel(const int64_t* __restrict__ st, int64_t nb, int
 
 // leaf box ids, parents and per-level box ids of one tree
 __global__ void index_lists_kernel(int64_t nbox, int s, int L, int32_t* __restrict__ leaf_box,
-                                   int32_t* __restrict__ parent, int32_t* __restrict__ ids) {
+                                   int32_t* __restrict__ parent) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nbox) return;
   int l = 0;
   while (level_offset(l + 1, s) <= g) l++;
   const int64_t b = g - level_offset(l, s);
   parent[g] = (l == 0) ? -1 : (int32_t)(level_offset(l - 1, s) + (b >> s));
-  ids[g] = (int32_t)g;
   if (l == L) leaf_box[b] = (int32_t)g;
 }
 
@@ -746,14 +745,14 @@ __global__ void m2l_geo_kernel(const int32_t* __restrict__ mt, const int32_t* __
   }
 }
 
-// M2M (t = c_child - c_parent) and L2L (t = c_parent - c_child) per child box.
+// M2M (t = c_child - c_parent) per child box.
 __global__ void edge_geo_kernel(int64_t nbox, int s, const double* __restrict__ center,
                                 const double* __restrict__ radius, int p, double* __restrict__ m64,
-                                float* __restrict__ m32, double* __restrict__ l64, float* __restrict__ l32) {
+                                float* __restrict__ m32) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nbox) return;
   if (g == 0) {
-    for (int f = 0; f < 2 + 4 * p; f++) m64[f * nbox] = m32[f * nbox] = l64[f * nbox] = l32[f * nbox] = 0;
+    for (int f = 0; f < 2 + 4 * p; f++) m64[f * nbox] = m32[f * nbox] = 0;
     return;
   }
   int l = 0;
@@ -762,16 +761,54 @@ __global__ void edge_geo_kernel(int64_t nbox, int s, const double* __restrict__ 
   const int64_t gp = level_offset(l - 1, s) + (b >> s);
   const double t[3] = {center[3 * g] - center[3 * gp], center[3 * g + 1] - center[3 * gp + 1],
                        center[3 * g + 2] - center[3 * gp + 2]};
-  const double tn[3] = {-t[0], -t[1], -t[2]};
   double r;
   trig_rows(t, p, g, nbox, 2, m64, m32, &r);
-  trig_rows(tn, p, g, nbox, 2, l64, l32, &r);
   const double rp = radius[gp];
   const double a = rp > 0.0 ? r / rp : 0.0, bb = rp > 0.0 ? radius[g] / rp : 0.0;
-  m64[g] = l64[g] = a;
-  m32[g] = l32[g] = (float)a;
-  m64[nbox + g] = l64[nbox + g] = bb;
-  m32[nbox + g] = l32[nbox + g] = (float)bb;
+  m64[g] = a;
+  m32[g] = (float)a;
+  m64[nbox + g] = bb;
+  m32[nbox + g] = (float)bb;
+}
+
+// Direct L2L records (one per target leaf and ancestor with a non-empty M2L
+// list, nearest ancestor first): t = c_ancestor - c_leaf, the axial
+// parameters |t| / rho_a and rho_leaf / rho_a, and the rotation angles.
+__device__ __forceinline__ bool has_m2l(const int64_t* __restrict__ m2l_off, int64_t a) {
+  return m2l_off[a + 1] > m2l_off[a];
+}
+__global__ void l2d_count_kernel(int64_t nl, const int32_t* __restrict__ leaf_box, const int32_t* __restrict__ parent,
+                                 const int64_t* __restrict__ m2l_off, int64_t* __restrict__ cnt) {
+  const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (leaf >= nl) return;
+  int64_t c = 0;
+  for (int64_t a = parent[leaf_box[leaf]]; a >= 0; a = parent[a]) c += has_m2l(m2l_off, a) ? 1 : 0;
+  cnt[leaf] = c;
+}
+__global__ void l2d_fill_kernel(int64_t nl, const int32_t* __restrict__ leaf_box, const int32_t* __restrict__ parent,
+                                const int64_t* __restrict__ m2l_off, const int64_t* __restrict__ off,
+                                const double* __restrict__ center, const double* __restrict__ radius, int p,
+                                int64_t n_rec, int32_t* __restrict__ anc, double* __restrict__ e64,
+                                float* __restrict__ e32) {
+  const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (leaf >= nl) return;
+  const int64_t g = leaf_box[leaf];
+  int64_t e = off[leaf];
+  for (int64_t a = parent[g]; a >= 0; a = parent[a]) {
+    if (!has_m2l(m2l_off, a)) continue;
+    anc[e] = (int32_t)a;
+    const double t[3] = {center[3 * a] - center[3 * g], center[3 * a + 1] - center[3 * g + 1],
+                         center[3 * a + 2] - center[3 * g + 2]};
+    double r;
+    trig_rows(t, p, e, n_rec, 2, e64, e32, &r);
+    const double ra = radius[a];
+    const double va = ra > 0.0 ? r / ra : 0.0, vb = ra > 0.0 ? radius[g] / ra : 0.0;
+    e64[e] = va;
+    e32[e] = (float)va;
+    e64[n_rec + e] = vb;
+    e32[n_rec + e] = (float)vb;
+    e++;
+  }
 }
 
 // Are two distinct points at exactly the same position?  Open-addressing
@@ -1024,27 +1061,23 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   centre_radius_kernel<<<grid_for(NB, 256, 1 << 30), 256, 0, st>>>(NB, blo, bhi, t->center, t->radius, t->inv_rho32,
                                                                    t->inv_rho64);
   FMM_LAUNCH_CHECK();
-  // index lists: a single tree's M2M round r holds level L - r, its L2L
-  // round r level r + 1 (children of a parent consecutive)
+  // index lists: a single tree's M2M round r holds level L - r (children of
+  // a parent consecutive)
   t->leaf_box = dev_alloc<int32_t>(t, NL);
   t->box_parent = dev_alloc<int32_t>(t, NB);
-  t->down_ids = dev_alloc<int32_t>(t, NB);
   t->up_ids = dev_alloc<int32_t>(t, NB);
-  index_lists_kernel<<<grid_for(NB, 256, 1 << 30), 256, 0, st>>>(NB, s, L, t->leaf_box, t->box_parent, t->down_ids);
+  index_lists_kernel<<<grid_for(NB, 256, 1 << 30), 256, 0, st>>>(NB, s, L, t->leaf_box, t->box_parent);
   FMM_LAUNCH_CHECK();
-  t->n_up = t->n_down = L;
+  t->n_up = L;
   t->up_off_h = new int64_t[L + 1];
-  t->down_off_h = new int64_t[L + 1];
   {
     std::vector<int32_t> up;
     up.reserve((size_t)NB);
     for (int r = 0; r < L; r++) {
       t->up_off_h[r] = (int64_t)up.size();
       for (int64_t g = level_offset(L - r, s); g < level_offset(L - r + 1, s); g++) up.push_back((int32_t)g);
-      t->down_off_h[r] = level_offset(r + 1, s);
     }
     t->up_off_h[L] = (int64_t)up.size();
-    t->down_off_h[L] = level_offset(L + 1, s);
     if (!up.empty())
       FMM_CUDA_TRY(cudaMemcpyAsync(t->up_ids, up.data(), sizeof(int32_t) * up.size(), cudaMemcpyHostToDevice, st));
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1074,7 +1107,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
     cudaFree(buf0), cudaFree(buf1);
   }
 
-  // ---- point records and M2M/L2L edge coefficients ----
+  // ---- point records and M2M edge coefficients ----
   const int p = t->prm.p;
   t->pos_local = dev_alloc<float4>(t, n);
   t->pos64 = dev_alloc<dvec4>(t, n);
@@ -1083,10 +1116,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   FMM_LAUNCH_CHECK();
   t->m2m64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
   t->m2m32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
-  t->l2l64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
-  t->l2l32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
-  edge_geo_kernel<<<grid_for(NB, 128, 1 << 30), 128, 0, st>>>(NB, s, t->center, t->radius, p, t->m2m64, t->m2m32,
-                                                              t->l2l64, t->l2l32);
+  edge_geo_kernel<<<grid_for(NB, 128, 1 << 30), 128, 0, st>>>(NB, s, t->center, t->radius, p, t->m2m64, t->m2m32);
   FMM_LAUNCH_CHECK();
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
   t->device_bytes -= sizeof(double) * 6 * NB;  // bounding boxes leave with the caller
@@ -1253,6 +1283,7 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
                                                       t->geo32);
     FMM_LAUNCH_CHECK();
   }
+  build_l2l_direct(t, st);
   {
     unsigned long long* pairs = scratch_alloc<unsigned long long>(1);
     FMM_CUDA_TRY(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), st));
@@ -1368,6 +1399,32 @@ __global__ void offset_i64_kernel(int64_t* __restrict__ dst, const int64_t* __re
 
 }  // namespace
 
+// Direct L2L records of a tree whose lists, geometry and parents are set
+// (single trees, separate hierarchies and merged batches alike).
+void build_l2l_direct(fmm_tree* t, cudaStream_t st) {
+  const int64_t NL = t->n_leaves;
+  const int p = t->prm.p;
+  int64_t* cnt = scratch_alloc<int64_t>(NL + 1);
+  FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (NL + 1), st));
+  if (NL > 0) {
+    l2d_count_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->leaf_box, t->box_parent, t->m2l_off, cnt);
+    FMM_LAUNCH_CHECK();
+  }
+  t->l2d_off = dev_alloc<int64_t>(t, NL + 1);
+  const int64_t nr = exclusive_scan(cnt, t->l2d_off, NL + 1, st);
+  cudaFree(cnt);
+  t->n_l2d = nr;
+  t->l2d_anc = dev_alloc<int32_t>(t, std::max<int64_t>(nr, 1));
+  t->l2d64 = dev_alloc<double>(t, (size_t)edge_fields(p) * std::max<int64_t>(nr, 1));
+  t->l2d32 = dev_alloc<float>(t, (size_t)edge_fields(p) * std::max<int64_t>(nr, 1));
+  if (nr > 0) {
+    l2d_fill_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->leaf_box, t->box_parent, t->m2l_off, t->l2d_off,
+                                                       t->center, t->radius, p, nr, t->l2d_anc, t->l2d64, t->l2d32);
+    FMM_LAUNCH_CHECK();
+  }
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
 void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
   double *blo = nullptr, *bhi = nullptr;
   build_hierarchy(t, pos, st, &blo, &bhi);
@@ -1446,12 +1503,8 @@ void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg,
     m->pos64 = dev_alloc<dvec4>(m, N);
     m->m2m32 = dev_alloc<float>(m, (size_t)edge_fields(p) * NB);
     m->m2m64 = dev_alloc<double>(m, (size_t)edge_fields(p) * NB);
-    m->l2l32 = dev_alloc<float>(m, (size_t)edge_fields(p) * NB);
-    m->l2l64 = dev_alloc<double>(m, (size_t)edge_fields(p) * NB);
     FMM_CUDA_TRY(cudaMemsetAsync(m->m2m32, 0, sizeof(float) * edge_fields(p) * NB, st));
     FMM_CUDA_TRY(cudaMemsetAsync(m->m2m64, 0, sizeof(double) * edge_fields(p) * NB, st));
-    FMM_CUDA_TRY(cudaMemsetAsync(m->l2l32, 0, sizeof(float) * edge_fields(p) * NB, st));
-    FMM_CUDA_TRY(cudaMemsetAsync(m->l2l64, 0, sizeof(double) * edge_fields(p) * NB, st));
 
     copy_d2d(m->perm, S->perm, n_s, st);
     offset_i32_kernel<<<grid_for(n_t, 256), 256, 0, st>>>(m->perm + n_s, T->perm, n_t, (int32_t)n_s, 0);
@@ -1477,24 +1530,15 @@ void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg,
     copy_d2d(m->pos_local + n_s, T->pos_local, n_t, st);
     copy_d2d(m->pos64, S->pos64, n_s, st);
     copy_d2d(m->pos64 + n_s, T->pos64, n_t, st);
-    // multipoles move up the source tree, locals down the target tree
+    // multipoles move up the source tree (M2M rounds); locals reach the
+    // target leaves by the direct L2L records of the target tree
     copy_rows(m->m2m32, NB, 0, S->m2m32, NBs, edge_fields(p), st);
     copy_rows(m->m2m64, NB, 0, S->m2m64, NBs, edge_fields(p), st);
-    copy_rows(m->l2l32, NB, NBs, T->l2l32, NBt, edge_fields(p), st);
-    copy_rows(m->l2l64, NB, NBs, T->l2l64, NBt, edge_fields(p), st);
-
-    // M2M rounds over the source tree, L2L rounds over the target tree
     m->n_up = S->L;
-    m->n_down = T->L;
     m->up_off_h = new int64_t[S->L + 1];
-    m->down_off_h = new int64_t[T->L + 1];
     for (int r = 0; r <= S->L; r++) m->up_off_h[r] = S->up_off_h[r];
-    for (int r = 0; r <= T->L; r++) m->down_off_h[r] = T->down_off_h[r];
     m->up_ids = dev_alloc<int32_t>(m, std::max<int64_t>(NBs, 1));
-    m->down_ids = dev_alloc<int32_t>(m, std::max<int64_t>(NBt, 1));
     copy_d2d(m->up_ids, S->up_ids, NBs, st);
-    offset_i32_kernel<<<grid_for(NBt, 256), 256, 0, st>>>(m->down_ids, T->down_ids, NBt, (int32_t)NBs, 0);
-    FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
 
     // can a target coincide with a source?  (duplicates among the union;
