@@ -153,8 +153,10 @@ int fmm_num_levels(int64_t n, int leaf_size, int splits);
  * to the lower child ordered by (coordinate, original index); leaf points in
  * ascending original index), box centres (bounding-box midpoints) and radii
  * (half diagonals) in FP64, level-march M2L lists and near-field lists, and
- * the rotation coefficients of every M2M, M2L and L2L translation (FP64,
- * also stored rounded to FP32).  -0.0 coordinates are treated as +0.0.
+ * the rotation coefficients of every M2M and M2L translation and of the
+ * L2L translations from each leaf's ancestors with M2L sums straight to the
+ * leaf (the level-by-level L2L chain applied in one step; FP64, also stored
+ * rounded to FP32).  -0.0 coordinates are treated as +0.0.
  *   pos     device, n x 3 doubles, read only during the call
  *   n       >= 1 points (< 2^31)
  *   params  host pointer, copied

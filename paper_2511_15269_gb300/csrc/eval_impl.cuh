@@ -191,6 +191,45 @@ __global__ void __launch_bounds__(128) m2m_kernel(int64_t n_child, const int32_t
 }
 
 // ---- E3: M2L, persistent; one warp per target box, lanes over its list ------
+// Each lane accumulates its interactions in a shared-memory row of m2l_chunks
+// 16-byte chunks (4 FP32 or 2 FP64 values; an odd count, so the 8 lanes of a
+// quarter-warp hit distinct banks); the warp then sums the 32 rows per
+// coefficient in lane order.
+template <int P>
+constexpr int m2l_chunks() {
+  constexpr int per = 16 / (int)sizeof(real);
+  return ((ncoef(P) + per - 1) / per) | 1;
+}
+
+template <int P>
+__device__ __forceinline__ void m2l_acc_add(real* row, const real (&v)[ncoef(P)]) {
+  constexpr int NC = ncoef(P);
+  sfor<0, m2l_chunks<P>()>([&](auto kk) {
+    constexpr int k = decltype(kk)::value;
+    if constexpr (kF32) {
+      constexpr int i = 4 * k;
+      if constexpr (i < NC) {
+        float4* p4 = reinterpret_cast<float4*>(row) + k;
+        float4 a = *p4;
+        a.x += v[i];
+        if constexpr (i + 1 < NC) a.y += v[i + 1];
+        if constexpr (i + 2 < NC) a.z += v[i + 2];
+        if constexpr (i + 3 < NC) a.w += v[i + 3];
+        *p4 = a;
+      }
+    } else {
+      constexpr int i = 2 * k;
+      if constexpr (i < NC) {
+        double2* p2 = reinterpret_cast<double2*>(row) + k;
+        double2 a = *p2;
+        a.x += v[i];
+        if constexpr (i + 1 < NC) a.y += v[i + 1];
+        *p2 = a;
+      }
+    }
+  });
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
                                                   const int32_t* __restrict__ order,
@@ -202,10 +241,12 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
                                                   int* __restrict__ counter) {
   constexpr int NC = ncoef(P);
   constexpr int NCP = ncoef_pad(P);
+  constexpr int ROW = m2l_chunks<P>() * (16 / (int)sizeof(real));  // reals per lane row
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = lane_id();
   const int warp = threadIdx.x >> 5;
-  real* acc = reinterpret_cast<real*>(smem_raw) + (size_t)warp * NC * 32;
+  real* rows = reinterpret_cast<real*>(smem_raw) + (size_t)warp * 32 * ROW;
+  real* mine = rows + lane * ROW;
   for (;;) {
     int t = 0;
     if (lane == 0) t = atomicAdd(counter, 1);
@@ -214,7 +255,7 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
     const int64_t g = order[t];
     const int64_t b = off[g], e = off[g + 1];
 #pragma unroll
-    for (int c = 0; c < NC; c++) acc[c * 32 + lane] = real(0);
+    for (int c = 0; c < ROW; c++) mine[c] = real(0);
     for (int64_t i = b + lane; i < e; i += 32) {
       const int64_t s = src[i];
       real v[NC];
@@ -223,19 +264,17 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
       real cp[P], sp[P], ct[P], st[P];
       load_trig<P>(geo, n_m2l, i, 3, cp, sp, ct, st);
       translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_m2l<P>(w, uS, uT, rinv); });
-#pragma unroll
-      for (int c = 0; c < NC; c++) acc[c * 32 + lane] += v[c];
+      m2l_acc_add<P>(mine, v);
     }
     __syncwarp();
     real* out = Lam + g * NCP;
     for (int c = lane; c < NCP; c += 32) {
       real s = real(0), err = real(0);
       if (c < NC) {
-        const real* row = acc + c * 32;
 #pragma unroll 8
         for (int j = 0; j < 32; j++) {
-          if (kF32) two_sum(s, err, row[(j + lane) & 31]);
-          else s += row[(j + lane) & 31];
+          if (kF32) two_sum(s, err, rows[j * ROW + c]);
+          else s += rows[j * ROW + c];
         }
       }
       out[c] = s + err;
@@ -1885,10 +1924,10 @@ void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 //   kUpwardSide: P2M and M2M rounds beside the near field, then M2L, L2L, L2P
 //   kFarSide:    P2M, M2M, then M2L and L2L beside the near field (M2L capped at
 //                kM2LBlocksPerSM blocks per SM)
-// Measured beside the symmetric near field (ms per evaluation, 2^20-point
-// cube / 2^18-point cube / 2^22-point Plummer): kFarSide 2.53-2.70 / - / -,
-// kSerial 2.29 / 0.650 / 54.5, kUpwardSide 2.20 / 0.622 / 46.7,
-// kSplitNear 2.25 / 0.588 / 55.9.
+// Measured beside the symmetric near field with the level-by-level L2L
+// (ms per evaluation, 2^20-point cube / 2^18-point cube / 2^22-point
+// Plummer): kFarSide 2.53-2.70 / - / -, kSerial 2.29 / 0.650 / 54.5,
+// kUpwardSide 2.20 / 0.622 / 46.7, kSplitNear 2.25 / 0.588 / 55.9.
 //   kSplitNear:  the near field in two launches (heaviest leaves first): P2M
 //                and M2M beside the first, M2L alone, L2L beside the second,
 //                then the slot gather and L2P
@@ -1897,11 +1936,10 @@ constexpr int kSchedule = kUpwardSide;
 constexpr bool kOverlapFarField = kSchedule == kFarSide;
 constexpr int kM2LBlocksPerSM = 1;
 
-// Downward pass: M2L over the whole list, then L2L round by round (round r
-// holds the boxes at depth r + 1 of every tree in the batch).
+// Downward pass: M2L over the whole list, then L2L in direct form.
 template <int P>
 void run_m2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
-  const size_t smem = (size_t)4 * ncoef(P) * 32 * sizeof(real);
+  const size_t smem = (size_t)4 * 32 * m2l_chunks<P>() * 16;
   static bool attr_set = false;
   if (!attr_set) {
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2184,7 +2222,8 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     join();
   } else if (kSchedule == kUpwardSide) {
     // P2M, M2M beside the near field; then the slot gather (memory bound)
-    // beside M2L and L2L (compute bound)
+    // beside M2L and L2L (beside L2L alone: 2.08 / 0.511 / 53.7 ms on the
+    // three workloads below, against 2.08 / 0.503 / 43.1)
     fork();
     upward(t->far_stream);
     near();

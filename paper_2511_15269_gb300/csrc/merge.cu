@@ -1,9 +1,9 @@
 // fmm_tree_merge: one tree-shaped object holding several independent trees
 // (a batch of charge sets), so that every evaluation stage runs as one launch
 // over all of them.  Points, boxes, interaction lists and per-interaction
-// coefficients are concatenated with offsets; leaf boxes and the M2M/L2L
-// rounds become explicit index lists (M2M round r: the boxes r levels above
-// each tree's leaves; L2L round r: each tree's boxes at depth r + 1).
+// coefficients are concatenated with offsets; leaf boxes and the M2M rounds
+// become explicit index lists (M2M round r: the boxes r levels above each
+// tree's leaves), and the direct L2L records are rebuilt over the batch.
 #include <algorithm>
 #include <chrono>
 #include <vector>
