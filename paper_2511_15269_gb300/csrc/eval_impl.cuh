@@ -201,7 +201,8 @@ constexpr int m2l_chunks() {
   return ((ncoef(P) + per - 1) / per) | 1;
 }
 
-template <int P>
+// row += v (ADD) or row = v, in 16-byte chunks
+template <int P, bool ADD = true>
 __device__ __forceinline__ void m2l_acc_add(real* row, const real (&v)[ncoef(P)]) {
   constexpr int NC = ncoef(P);
   sfor<0, m2l_chunks<P>()>([&](auto kk) {
@@ -210,7 +211,7 @@ __device__ __forceinline__ void m2l_acc_add(real* row, const real (&v)[ncoef(P)]
       constexpr int i = 4 * k;
       if constexpr (i < NC) {
         float4* p4 = reinterpret_cast<float4*>(row) + k;
-        float4 a = *p4;
+        float4 a = ADD ? *p4 : make_float4(0.f, 0.f, 0.f, 0.f);
         a.x += v[i];
         if constexpr (i + 1 < NC) a.y += v[i + 1];
         if constexpr (i + 2 < NC) a.z += v[i + 2];
@@ -221,7 +222,7 @@ __device__ __forceinline__ void m2l_acc_add(real* row, const real (&v)[ncoef(P)]
       constexpr int i = 2 * k;
       if constexpr (i < NC) {
         double2* p2 = reinterpret_cast<double2*>(row) + k;
-        double2 a = *p2;
+        double2 a = ADD ? *p2 : make_double2(0.0, 0.0);
         a.x += v[i];
         if constexpr (i + 1 < NC) a.y += v[i + 1];
         *p2 = a;
@@ -291,10 +292,10 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
 // exactly onto the same degrees, so translations compose without truncation
 // and the two forms differ by rounding only.  The direct form needs one
 // launch instead of one round per level; only ancestors with a non-empty M2L
-// list have records.  Lanes of a group translate the leaf's records in turn,
-// the group sums the translated expansions by an xor butterfly (the same sum,
-// bit for bit, on every lane) and lane j adds coefficients c = j (mod the
-// group size) to the leaf's own M2L sum.  Internal boxes keep their M2L sums.
+// list have records.  Lanes of a group translate the leaf's records in turn
+// into shared-memory rows (as M2L), then lane j adds the group's rows, in lane
+// order, to coefficients c = j (mod the group size) of the leaf's own M2L
+// sum.  Internal boxes keep their M2L sums.
 constexpr int kL2LGroup = 8;
 
 template <int P>
@@ -306,35 +307,34 @@ __global__ void __launch_bounds__(128) l2l_direct_kernel(int64_t n_leaves, const
   constexpr int G = kL2LGroup;
   constexpr int NC = ncoef(P);
   constexpr int NCP = ncoef_pad(P);
+  constexpr int ROW = m2l_chunks<P>() * (16 / (int)sizeof(real));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
   if (leaf >= n_leaves) return;  // whole groups leave together
   const int j = threadIdx.x % G;
   const unsigned gmask = ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+  real* rows = reinterpret_cast<real*>(smem_raw) + (size_t)(threadIdx.x - j) * ROW;
   const int64_t b = off[leaf], e = off[leaf + 1];
   real* out = Lam + (int64_t)leaf_box[leaf] * NCP;
   for (int64_t r0 = b; r0 < e; r0 += G) {
     const int64_t i = r0 + j;
-    real v[NC];
     if (i < e) {
+      real v[NC];
       load_coef<P>(Lam + (int64_t)anc[i] * NCP, v);
       const real a = edge[i], bb = edge[n_rec + i];
       real cp[P], sp[P], ct[P], st[P];
       load_trig<P>(edge, n_rec, i, 2, cp, sp, ct, st);
       translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_l2l<P>(w, a, bb); });
-    } else {
-#pragma unroll
-      for (int c = 0; c < NC; c++) v[c] = real(0);
+      m2l_acc_add<P, false>(rows + j * ROW, v);
     }
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-      real x = v[c];
-#pragma unroll
-      for (int o = 1; o < G; o <<= 1) x += __shfl_xor_sync(gmask, x, o);
-      v[c] = x;
+    __syncwarp(gmask);
+    const int nv = (int)((e - r0) < G ? (e - r0) : G);
+    for (int c = j; c < NC; c += G) {
+      real x = out[c];
+      for (int q = 0; q < nv; q++) x += rows[q * ROW + c];
+      out[c] = x;
     }
-#pragma unroll
-    for (int c = 0; c < NC; c++)
-      if (c % G == j) out[c] += v[c];
+    __syncwarp(gmask);
   }
 }
 
@@ -1967,8 +1967,15 @@ void run_m2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 template <int P>
 void run_l2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   stage_event(t, FMM_STAGE_L2L, false, st);
+  const size_t l2l_smem = (size_t)128 * m2l_chunks<P>() * 16;
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(
+        cudaFuncSetAttribute(l2l_direct_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l2l_smem));
+    attr_set = true;
+  }
   if (t->n_l2d > 0) {
-    l2l_direct_kernel<P><<<grid_for(t->n_leaves * kL2LGroup, 128, 1 << 30), 128, 0, st>>>(
+    l2l_direct_kernel<P><<<grid_for(t->n_leaves * kL2LGroup, 128, 1 << 30), 128, l2l_smem, st>>>(
         t->n_leaves, t->leaf_box, t->l2d_off, t->l2d_anc, pp.l2d, t->n_l2d, pp.Lam);
     FMM_LAUNCH_CHECK();
     t->launches += 1;
