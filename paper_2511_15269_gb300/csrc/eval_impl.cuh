@@ -1069,11 +1069,22 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 4 : 2) p2p_kernel_bwd(P2PArgs 
 // local evaluation of leaf B adds its slots in list order.  The self pair and
 // pairs listed in one direction only are evaluated one-sided.  Lane layout
 // and staging as in p2p_kernel_f32h.
+//
+// Source order inside a chunk of 32: lane l16 of half h takes, at step jj,
+// record c0 + 4 (jj mod 8) + h + 2 w with w = (jj >= 8) xor (bit 3 of l16)
+// (records c0 + 4 k + h for steps k, then c0 + 4 k + 2 + h, or the reverse in
+// the upper eight lanes).  A lane's step jj and its partner's (lane xor 8)
+// step jj xor 8 then hold the same source, so the butterfly's first stage
+// needs no selects; at every step a warp reads four records whose
+// 16-byte halves fall in distinct banks.
 template <int NPH>
-__device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* dst, int j0, int jstep, int scount) {
-  // after the stages with masks 8, 4, 2, 1 lane l16 holds the half-warp sum of P[l16]
+__device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* dst, int j, int scount) {
 #pragma unroll
-  for (int m = 8; m >= 1; m >>= 1) {
+  for (int i = 0; i < 8; i++) P[i] += __shfl_xor_sync(0xffffffffu, P[i + 8], 8);
+  // after the stages with masks 4, 2, 1 lane l16 holds the half-warp sum of
+  // its step (l16 mod 8)
+#pragma unroll
+  for (int m = 4; m >= 1; m >>= 1) {
     const bool up = (l16 & m) != 0;
 #pragma unroll
     for (int i = 0; i < m; i++) {
@@ -1082,27 +1093,31 @@ __device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* 
       P[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
     }
   }
-  const int j = j0 + jstep * l16;
   if (j < scount) dst[j] = P[0];
 }
 
-// One chunk of 16 sources per half-warp of a symmetric pair: u of the lane's
-// targets in pu, and per source the lane's share of sum_i q_i / r in P.
-// FULL: all 32 sources of the chunk exist (no bounds checks).
+// One chunk of 32 sources (16 per half-warp): u of the lane's targets in pu,
+// and per source the lane's share of sum_i q_i / r in P (step order above;
+// sw = bit 3 of l16).  FULL: all 32 sources of the chunk exist.
 template <bool MASK, bool FULL, int NPH>
-__device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half, int scount, const f2 (&tx)[NPH],
-                                          const f2 (&ty)[NPH], const f2 (&tz)[NPH], const f2 (&tq)[NPH],
-                                          f2 (&pu)[NPH], float (&P)[16], float thr) {
+__device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half, int sw, int scount,
+                                          const f2 (&tx)[NPH], const f2 (&ty)[NPH], const f2 (&tz)[NPH],
+                                          const f2 (&tq)[NPH], f2 (&pu)[NPH], float (&P)[16], float thr) {
+  const int r_lo = c0 + half + 2 * sw, r_hi = c0 + half + 2 - 2 * sw;
+  const ulonglong2* p_lo = s2 + 2 * r_lo;
+  const ulonglong2* p_hi = s2 + 2 * r_hi;
 #pragma unroll
   for (int jj = 0; jj < 16; jj++) {
-    const int j = c0 + 2 * jj + half;
+    const int k = jj & 7;
+    const int j = (jj < 8 ? r_lo : r_hi) + 4 * k;
     P[jj] = 0.f;
     if (FULL || j < scount) {
-      const ulonglong2 sa = s2[2 * j], sb = s2[2 * j + 1];
+      const ulonglong2* pr = (jj < 8 ? p_lo : p_hi) + 8 * k;
+      const ulonglong2 sa = pr[0], sb = pr[1];
       f2 acc = 0ull;
 #pragma unroll
-      for (int k = 0; k < NPH; k++) {
-        const f2 dx = f2sub(tx[k], sa.x), dy = f2sub(ty[k], sa.y), dz = f2sub(tz[k], sb.x);
+      for (int kk = 0; kk < NPH; kk++) {
+        const f2 dx = f2sub(tx[kk], sa.x), dy = f2sub(ty[kk], sa.y), dz = f2sub(tz[kk], sb.x);
         const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
         float r0, r1;
         f2unpack(r2, r0, r1);
@@ -1112,8 +1127,8 @@ __device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half
           i1 = (r1 > thr) ? i1 : 0.f;
         }
         const f2 ri = f2pack(i0, i1);
-        pu[k] = f2fma(sb.y, ri, pu[k]);
-        acc = f2fma(tq[k], ri, acc);
+        pu[kk] = f2fma(sb.y, ri, pu[kk]);
+        acc = f2fma(tq[kk], ri, acc);
       }
       float a0, a1;
       f2unpack(acc, a0, a1);
@@ -1240,15 +1255,17 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
       float* dst = reinterpret_cast<float*>(a.partial) + (int64_t)slot * a.stride;
       float P[16];
       int c0 = 0;
+      const int sw = (l16 >> 3) & 1;
+      const int jmine = half + 4 * (l16 & 7) + 2 * sw;  // source of this lane after the butterfly
       for (; c0 + 32 <= scount; c0 += 32) {
-        if (mask) sym_chunk<true, true, NPH>(s2, c0, half, scount, tx, ty, tz, tq, pu, P, thr);
-        else sym_chunk<false, true, NPH>(s2, c0, half, scount, tx, ty, tz, tq, pu, P, thr);
-        butterfly_store<NPH>(P, l16, dst, c0 + half, 2, scount);
+        if (mask) sym_chunk<true, true, NPH>(s2, c0, half, sw, scount, tx, ty, tz, tq, pu, P, thr);
+        else sym_chunk<false, true, NPH>(s2, c0, half, sw, scount, tx, ty, tz, tq, pu, P, thr);
+        butterfly_store<NPH>(P, l16, dst, c0 + jmine, scount);
       }
       if (c0 < scount) {
-        if (mask) sym_chunk<true, false, NPH>(s2, c0, half, scount, tx, ty, tz, tq, pu, P, thr);
-        else sym_chunk<false, false, NPH>(s2, c0, half, scount, tx, ty, tz, tq, pu, P, thr);
-        butterfly_store<NPH>(P, l16, dst, c0 + half, 2, scount);
+        if (mask) sym_chunk<true, false, NPH>(s2, c0, half, sw, scount, tx, ty, tz, tq, pu, P, thr);
+        else sym_chunk<false, false, NPH>(s2, c0, half, sw, scount, tx, ty, tz, tq, pu, P, thr);
+        butterfly_store<NPH>(P, l16, dst, c0 + jmine, scount);
       }
     }
 #pragma unroll
