@@ -37,7 +37,7 @@ FP32_FLOPS_PER_PAIR = 10  # potential, per ordered pair: 3 sub, 5 for r^2, 2 for
 # DRAM bytes (read + write) of one launch of the symmetric near-field kernel on
 # this workload, from the ncu capture in profiles/p2p_kernel_f32s_dram_cube1m_p8.md
 # (100.51 MB read + 231.45 MB write); None once the kernel changes.
-P2P_TRAFFIC_BYTES = 331.99e6
+P2P_TRAFFIC_BYTES = 330.96e6
 SMS = 152
 FP32_LANES = 128
 
