@@ -2246,8 +2246,10 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     join();
   } else if (kSchedule == kUpwardSide) {
     // P2M, M2M beside the near field; then the slot gather (memory bound)
-    // beside M2L and L2L (beside L2L alone: 2.08 / 0.511 / 53.7 ms on the
-    // three workloads below, against 2.08 / 0.503 / 43.1)
+    // beside M2L and L2L on the higher-priority stream (beside L2L alone:
+    // 2.08 / 0.511 / 53.7 ms on the three workloads below, against 2.08 /
+    // 0.503 / 43.1; on the caller's stream with M2L and L2L on the
+    // higher-priority one: 2.061 / 0.505 / 52.8, against 2.058 / 0.506 / 42.6)
     fork();
     upward(t->far_stream);
     near();
