@@ -190,14 +190,10 @@ __device__ __forceinline__ void axial_m2l(real (&v)[ncoef(P)], real uS, real uT,
 // Axial M2M (App. B.3), a = r/rho_parent, b = rho_child/rho_parent.
 template <int P>
 __device__ __forceinline__ void axial_m2m(real (&v)[ncoef(P)], real a, real b) {
-  real pA[P + 1], pB[P + 1];
-  pA[0] = real(1);
+  real pB[P + 1];
   pB[0] = real(1);
 #pragma unroll
-  for (int k = 1; k <= P; k++) {
-    pA[k] = pA[k - 1] * a;
-    pB[k] = pB[k - 1] * b;
-  }
+  for (int k = 1; k <= P; k++) pB[k] = pB[k - 1] * b;
   sfor<0, 2 * P + 1>([&](auto mm) {
     constexpr int m = decltype(mm)::value - P;
     constexpr int am = m < 0 ? -m : m;
@@ -206,11 +202,12 @@ __device__ __forceinline__ void axial_m2m(real (&v)[ncoef(P)], real a, real b) {
     for (int k = am; k <= P; k++) in[k] = v[ix(k, m)] * pB[k];
     sfor<am, P + 1>([&](auto nn) {
       constexpr int n = decltype(nn)::value;
+      // sum_k c_nk a^(n-k) in_k in Horner form, lowest k first
       real acc = real(0);
       sfor<am, n + 1>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
         constexpr double c = gen::kAxM2M[ax_id(n, k, am)];
-        acc = fmar(real(c) * pA[n - k], in[k], acc);
+        acc = fmar(acc, a, real(c) * in[k]);
       });
       v[ix(n, m)] = acc;
     });
@@ -220,14 +217,10 @@ __device__ __forceinline__ void axial_m2m(real (&v)[ncoef(P)], real a, real b) {
 // Axial L2L (App. B.3), a = r/rho_parent, b = rho_child/rho_parent.
 template <int P>
 __device__ __forceinline__ void axial_l2l(real (&v)[ncoef(P)], real a, real b) {
-  real pA[P + 1], pB[P + 1];
-  pA[0] = real(1);
+  real pB[P + 1];
   pB[0] = real(1);
 #pragma unroll
-  for (int k = 1; k <= P; k++) {
-    pA[k] = pA[k - 1] * a;
-    pB[k] = pB[k - 1] * b;
-  }
+  for (int k = 1; k <= P; k++) pB[k] = pB[k - 1] * b;
   sfor<0, 2 * P + 1>([&](auto mm) {
     constexpr int m = decltype(mm)::value - P;
     constexpr int am = m < 0 ? -m : m;
@@ -236,11 +229,12 @@ __device__ __forceinline__ void axial_l2l(real (&v)[ncoef(P)], real a, real b) {
     for (int k = am; k <= P; k++) in[k] = v[ix(k, m)];
     sfor<am, P + 1>([&](auto nn) {
       constexpr int n = decltype(nn)::value;
+      // sum_k c_nk a^(k-n) in_k in Horner form, highest k first
       real acc = real(0);
-      sfor<n, P + 1>([&](auto kk) {
-        constexpr int k = decltype(kk)::value;
+      sfor<0, P + 1 - n>([&](auto jj) {
+        constexpr int k = P - decltype(jj)::value;
         constexpr double c = gen::kAxL2L[ax_id(n, k, am)];
-        acc = fmar(real(c) * pA[k - n], in[k], acc);
+        acc = fmar(acc, a, real(c) * in[k]);
       });
       v[ix(n, m)] = acc * pB[n];
     });
