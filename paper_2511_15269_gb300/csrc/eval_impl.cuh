@@ -1795,6 +1795,33 @@ __global__ void __launch_bounds__(128) p2p_kernel_dfs(P2PArgs a) {
   }
 }
 
+// Inputs of one point of the local evaluation (position and charge record,
+// near-field sum, output index, near field), zero beyond the leaf's count.
+struct PointIn {
+  vec4 s;
+  double nearv;
+  real nf[3];
+  int32_t o;
+};
+template <bool FIELD>
+__device__ __forceinline__ PointIn l2p_point_in(const vec4* __restrict__ src, const real* __restrict__ near_u,
+                                                const real* __restrict__ near_f, const int32_t* __restrict__ perm,
+                                                int64_t start, int i, int cnt) {
+  PointIn r{};
+  if (i < cnt) {
+    const int64_t pidx = start + i;
+    r.s = src[pidx];
+    r.nearv = kF32 ? (double)near_u[2 * pidx] + (double)near_u[2 * pidx + 1] : (double)near_u[pidx];
+    r.o = perm[pidx];
+    if (FIELD) {
+      r.nf[0] = near_f[3 * pidx];
+      r.nf[1] = near_f[3 * pidx + 1];
+      r.nf[2] = near_f[3 * pidx + 2];
+    }
+  }
+  return r;
+}
+
 // ---- E5 + E7: L2P, near + far combination and inverse sort --------------------
 // u = -1/(4 pi) (far + near);  E = -grad u = 1/(4 pi) (grad far - sum q d / r^3).
 template <int P, bool FIELD>
@@ -1820,6 +1847,23 @@ __global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, const int32_
   for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves;
        leaf += warps) {
     const int64_t g = leaf_box[leaf];
+    // box data (and in the field variant the lane's first point) are
+    // requested before the shared copy of the local expansion completes
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    const real ir = inv_rho[g];
+    real cx = 0, cy = 0, cz = 0;
+    if (!kF32) {
+      cx = (real)center[3 * g];
+      cy = (real)center[3 * g + 1];
+      cz = (real)center[3 * g + 2];
+    }
+    // the field variant keeps the next point's inputs in flight during the
+    // current one (measured: field 4.92 -> 4.87 ms at 2^20); the potential
+    // variant is register-limited and loads each point when it starts
+    constexpr bool kAhead = FIELD;
+    PointIn nxt{};
+    if (kAhead) nxt = l2p_point_in<FIELD>(src, near_u, near_f, perm, start, lane, cnt);
     const real* L = Lam + g * ncoef_pad(P);
     for (int c = lane; c < NC; c += 32) sL[warp][c] = L[c];
     __syncwarp();
@@ -1852,18 +1896,16 @@ __global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, const int32_
       }
       __syncwarp();
     }
-    const int64_t start = box_start[g];
-    const int cnt = box_count[g];
-    const real ir = inv_rho[g];
-    real cx = 0, cy = 0, cz = 0;
-    if (!kF32) {
-      cx = (real)center[3 * g];
-      cy = (real)center[3 * g + 1];
-      cz = (real)center[3 * g + 2];
-    }
     for (int i = lane; i < cnt; i += 32) {
       const int64_t pidx = start + i;
-      const vec4 s = src[pidx];
+      PointIn cur;
+      if (kAhead) {
+        cur = nxt;
+        nxt = l2p_point_in<FIELD>(src, near_u, near_f, perm, start, i + 32, cnt);  // next point, in flight
+      } else {
+        cur = l2p_point_in<FIELD>(src, near_u, near_f, perm, start, i, cnt);
+      }
+      const vec4 s = cur.s;
       const real x = ((real)s.x - cx) * ir, y = ((real)s.y - cy) * ir, z = ((real)s.z - cz) * ir;
       real u0 = real(0), um = real(0), gx = real(0), gy = real(0), gz = real(0);
       real R[NC];
@@ -1883,14 +1925,13 @@ __global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, const int32_
         }
       });
       const double far = (double)u0 + 2.0 * (double)um;
-      double nearv = kF32 ? (double)near_u[2 * pidx] + (double)near_u[2 * pidx + 1] : (double)near_u[pidx];
-      const int64_t o = perm[pidx] - out_base;
-      if (u_out) u_out[o] = -kInv4Pi * (far + nearv);
+      const int64_t o = cur.o - out_base;
+      if (u_out) u_out[o] = -kInv4Pi * (far + cur.nearv);
       if (FIELD) {
         const double irr = (double)ir;
-        f_out[3 * o] = kInv4Pi * ((double)gx * irr - (double)near_f[3 * pidx]);
-        f_out[3 * o + 1] = kInv4Pi * ((double)gy * irr - (double)near_f[3 * pidx + 1]);
-        f_out[3 * o + 2] = kInv4Pi * ((double)gz * irr - (double)near_f[3 * pidx + 2]);
+        f_out[3 * o] = kInv4Pi * ((double)gx * irr - (double)cur.nf[0]);
+        f_out[3 * o + 1] = kInv4Pi * ((double)gy * irr - (double)cur.nf[1]);
+        f_out[3 * o + 2] = kInv4Pi * ((double)gz * irr - (double)cur.nf[2]);
       }
     }
     __syncwarp();
