@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
 // a two-sum at the end.  Source leaves arrive by double-buffered 1D TMA bulk
 // copies completing on per-warp mbarriers.
 template <int TPL, bool FIELD>
-__global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : ((TPL >= 8 || (FIELD && TPL >= 4)) ? 2 : 4))
+__global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : ((TPL >= 8 || (FIELD && TPL >= 4)) ? 2 : (TPL <= 2 ? 5 : 4)))
     p2p_kernel_f32h(P2PArgs a) {
   constexpr int CAP = TPL * 32;
   constexpr int WARPS = 4;
