@@ -1598,7 +1598,7 @@ __device__ __forceinline__ void df_rinv(const float (&th)[3], const float (&tl)[
 }
 
 template <int TPL>
-__global__ void __launch_bounds__(128) p2p_kernel_dfs(P2PArgs a) {
+__global__ void __launch_bounds__(128, TPL <= 2 ? 5 : 1) p2p_kernel_dfs(P2PArgs a) {
   constexpr int CAP = TPL * 32;
   constexpr int WARPS = 4;
   extern __shared__ __align__(128) unsigned char p2p_smem[];
