@@ -58,6 +58,32 @@ def test_l2l_is_exact(orc, shift):
         assert orc.l2p(p, Dn, c_new, x) == pytest.approx(orc.l2p(p, D, c_old, x), rel=1e-12)
 
 
+def test_l2l_composes_exactly(orc):
+    """Translations of a degree-p local expansion compose without truncation:
+    L2L(A -> leaf) equals L2L(parent -> leaf) after L2L(A -> parent), and the
+    chain over three levels equals the direct translation (the GPU applies the
+    level-by-level L2L of Sec. II.C in this direct form)."""
+    p = 10
+    rng = np.random.default_rng(11)
+    D = rng.normal(size=(p + 1) ** 2)
+    cA = np.array([0.0, 0.0, 0.0])
+    cP = cA + np.array([0.21, -0.13, 0.17])
+    cG = cP + np.array([-0.08, 0.11, 0.06])
+    cL = cG + np.array([0.03, -0.04, -0.05])
+    chain = orc.l2l(p, orc.l2l(p, orc.l2l(p, D, cA, cP), cP, cG), cG, cL)
+    direct = orc.l2l(p, D, cA, cL)
+    np.testing.assert_allclose(chain, direct, rtol=1e-11, atol=1e-12 * np.abs(direct).max())
+    # with M2L sums at every level: the leaf's local is its own sum plus the
+    # direct translations of its ancestors' own sums
+    own = {c: rng.normal(size=(p + 1) ** 2) for c in ("A", "P", "G", "L")}
+    lev = orc.l2l(p, own["A"], cA, cP) + own["P"]
+    lev = orc.l2l(p, lev, cP, cG) + own["G"]
+    lev = orc.l2l(p, lev, cG, cL) + own["L"]
+    direct = (own["L"] + orc.l2l(p, own["G"], cG, cL) + orc.l2l(p, own["P"], cP, cL)
+              + orc.l2l(p, own["A"], cA, cL))
+    np.testing.assert_allclose(lev, direct, rtol=1e-11, atol=1e-12 * np.abs(direct).max())
+
+
 @pytest.mark.parametrize("c_trg", [(2.0, -1.5, 1.2), (0, 0, -3.0), (0, 0, 3.0), (-2.2, 0.1, 0.0)])
 def test_m2l_monopole_is_exact(orc, c_trg):
     p = 10
