@@ -388,6 +388,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// 1/sqrt(r2) in FP64: the hardware's FP64 reciprocal square root
+// approximation (rsqrt.approx.f64; no conversions to and from FP32) with one
+// third-order correction y (1 + rho / 2 + 3 rho^2 / 8), rho = 1 - r2 y^2, the
+// first terms of (1 - rho)^(-1/2).  A seed error e leaves about 2.5 e^3 (e
+// near 4.5e-7, inferred from a one-step Newton refinement: 2e-19, below FP64
+// rounding).  r2 <= 0 (a point paired with itself, or a phantom target on a
+// source) gives 0.
+__device__ __forceinline__ double rsqrt_f64(double r2) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
+  const double rho = fma(-(r2 * y), y, 1.0);
+  y = fma(y * rho, fma(0.375, rho, 0.5), y);
+  return r2 > 0.0 ? y : 0.0;
+}
+
 template <bool MASK, bool FIELD, int TPL>
 __device__ __forceinline__ void p2p_tile(const vec4* sb, int scount, const real (&tx)[TPL],
                                          const real (&ty)[TPL], const real (&tz)[TPL],
@@ -404,13 +419,7 @@ __device__ __forceinline__ void p2p_tile(const vec4* sb, int scount, const real 
       if (kF32) {
         ri = rsqrtf((float)r2);
       } else {
-        // FP32 seed refined by two Newton steps for 1/sqrt in FP64
-        double y0 = (double)rsqrtf((float)r2);
-        const double h = 0.5 * (double)r2;
-        y0 = y0 * fma(-h * y0, y0, 1.5);
-        y0 = y0 * fma(-h * y0, y0, 1.5);
-        if (r2 < 1e-30) y0 = (r2 > 0) ? 1.0 / sqrt((double)r2) : 0.0;
-        ri = (real)y0;
+        ri = (real)rsqrt_f64((double)r2);
       }
       if (MASK) ri = (r2 > real(0)) ? ri : real(0);
       pu[k] = fmar((real)s.w, ri, pu[k]);
@@ -1354,16 +1363,8 @@ __global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_leaves, const
 // As p2p_kernel_f32s, in FP64 on absolute positions: a warp per leaf, lane l
 // holds targets l + 32 k; pairs listed both ways are evaluated once and the
 // sources' sums q_i / r are reduced over the warp in chunks of 16 sources
-// (reduce-scatter butterfly on lane bits 4..1, then the lane pair).  1/r is an
-// FP32 MUFU seed refined by one Newton step, y (3/2 - r^2 y^2 / 2): relative
-// error about 1.5 e^2 with e the seed's error (~2^-23), so near 3e-14.
-__device__ __forceinline__ double rsqrt_f64(double r2) {
-  double y = (double)rsqrt_mufu((float)r2);
-  const double h = 0.5 * r2;
-  y = y * fma(-h * y, y, 1.5);
-  if (!(r2 >= 1e-30 && r2 <= 1e30)) y = (r2 > 0.0) ? 1.0 / sqrt(r2) : 0.0;
-  return y;
-}
+// (reduce-scatter butterfly on lane bits 4..1, then the lane pair); 1/r from
+// rsqrt_f64.
 
 template <int TPL>
 __global__ void __launch_bounds__(128) p2p_kernel_f64s(P2PArgs a) {
