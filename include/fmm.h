@@ -62,11 +62,11 @@ enum {
                     local sums; rotation coefficients generated in FP64; final
                     near + far combination in FP64                             */
   FMM_FP64DF = 2  /* FP64 accuracy: as FMM_FP64, except that the potential
-                    near field of a tree of one point set (or a batch of them)
-                    runs in double-float arithmetic (unevaluated sums of two
-                    FP32 values, error-free transformations) on the FP32 pipes,
-                    with results within a few 1e-14 of FP64; fields, backward
-                    and two-hierarchy trees use the FP64 near field            */
+                    near field and the M2L of a tree of one point set (or a
+                    batch of them) run in double-float arithmetic (unevaluated
+                    sums of two FP32 values, error-free transformations) on the
+                    FP32 pipes, with results within a few 1e-14 of FP64;
+                    fields, backward and two-hierarchy trees use FP64          */
 };
 
 enum {
@@ -210,7 +210,12 @@ int fmm_tree_merge(fmm_tree* const* trees, int n_trees, void* stream, fmm_tree**
  * tree gives {0, n}. */
 int fmm_tree_point_offsets(const fmm_tree* tree, int64_t* offsets);
 
-/* Selects the precision of later evaluation calls (FMM_FP64 or FMM_FP32C). */
+/* Selects the precision of later evaluation calls (FMM_FP64, FMM_FP32C or
+ * FMM_FP64DF).  The first selection of FMM_FP64DF for a tree of one point set
+ * (or a tree built or merged with it) allocates the low parts of the M2L
+ * rotation records (4 m2l_fields(p) = 12 + 16 p bytes per interaction) and a
+ * double-float multipole buffer, synchronously on the default stream.
+ * Errors: FMM_ERR_INVALID_ARG, FMM_ERR_OOM, FMM_ERR_CUDA. */
 int fmm_tree_set_precision(fmm_tree* tree, int precision);
 
 /* Fills *stats (host pointer). */

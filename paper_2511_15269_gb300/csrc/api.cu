@@ -58,7 +58,7 @@ void free_tree(fmm_tree* t) {
   void* ptrs[] = {t->perm,     t->box_start, t->box_count, t->center,   t->radius,   t->m2l_off,  t->m2l_src,
                   t->m2l_trg,  t->m2l_order, t->p2p_off,   t->p2p_src,  t->p2p32,    t->leaf_order, t->pos_local,
                   t->pos64,    t->inv_rho32, t->inv_rho64, t->geo32,    t->geo64,    t->m2m32,    t->m2m64,
-                  t->l2d32,    t->l2d64,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
+                  t->l2d32,    t->l2d64,     t->geo_lo,    t->m_df,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
                   t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
                   t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->l2d_off, t->l2d_anc,
                   t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr, t->sym_slot, t->sym_work_off,
@@ -127,6 +127,7 @@ int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void*
     t->n = n;
     t->L = fmm_num_levels(n, p.leaf_size, p.splits);
     build_tree(t, pos, (cudaStream_t)stream);
+    if (p.precision == FMM_FP64DF) prepare_df_far(t, (cudaStream_t)stream);
     t->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   });
   if (rc != FMM_OK) {
@@ -182,6 +183,7 @@ int fmm_tree_merge(fmm_tree* const* trees, int n_trees, void* stream, fmm_tree**
     auto t0 = std::chrono::steady_clock::now();
     m = new fmm_tree();
     merge_trees(trees, n_trees, (cudaStream_t)stream, m);
+    if (m->prm.precision == FMM_FP64DF) prepare_df_far(m, (cudaStream_t)stream);
     m->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   });
   if (rc != FMM_OK) {
@@ -209,6 +211,7 @@ int fmm_tree_set_precision(fmm_tree* tree, int precision) {
     require(tree != nullptr, "tree is NULL");
     require(precision == FMM_FP64 || precision == FMM_FP32C || precision == FMM_FP64DF,
             "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
+    if (precision == FMM_FP64DF) prepare_df_far(tree, 0);
     tree->prm.precision = precision;
   });
 }

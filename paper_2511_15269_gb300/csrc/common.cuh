@@ -189,6 +189,8 @@ struct fmm_tree {
 
   // rotation / translation coefficients
   float* geo32 = nullptr;        // m2l_fields(p) x n_m2l
+  float* geo_lo = nullptr;       // FP64DF: geo64 - geo32 rounded to FP32 (same layout), or null
+  float2* m_df = nullptr;        // FP64DF: multipoles as double-float pairs, n_boxes x ncoef_pad(p)
   double* geo64 = nullptr;
   float* m2m32 = nullptr;        // edge_fields(p) x n_boxes (row = child id)
   double* m2m64 = nullptr;
@@ -256,6 +258,9 @@ void build_symmetric(fmm_tree* t, cudaStream_t st);
 // tree_build.cu: the direct L2L records of a tree with lists, geometry and
 // parents in place
 void build_l2l_direct(fmm_tree* t, cudaStream_t st);
+// tree_build.cu: the low parts of the rotation records and the double-float
+// multipole buffer of the FP64DF far field (once per tree)
+void prepare_df_far(fmm_tree* t, cudaStream_t st);
 // api.cu: releases every device array, stream and event of a tree
 void free_tree(fmm_tree* t);
 // merge.cu: a batch of trees as one tree-shaped object

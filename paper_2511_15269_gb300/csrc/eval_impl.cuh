@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "expansion.cuh"
+#include "dfloat.cuh"
 
 namespace fmm {
 namespace {
@@ -281,6 +282,86 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
       out[c] = s + err;
     }
     __syncwarp();
+  }
+}
+
+// ---- E3 (FP64DF): M2L in double-float arithmetic -----------------------------
+// The FP64-accurate path's M2L on the FP32 pipes: as m2l_kernel, with the
+// source multipoles, the rotation records and all arithmetic as double-float
+// values (about 48 significant bits; FP64 runs at 1/64 of the FP32 rate on
+// GB300).  Each lane keeps its sums in a shared-memory row of float pairs (an
+// odd row length: conflict-free 8-byte accesses); the warp adds the 32 rows
+// per coefficient in lane order and writes the FP64 locals.
+template <int P>
+__global__ void __launch_bounds__(128) m2l_kernel_df(int64_t n_targets, const int32_t* __restrict__ order,
+                                                     const int64_t* __restrict__ off,
+                                                     const int32_t* __restrict__ src,
+                                                     const float* __restrict__ geo_h,
+                                                     const float* __restrict__ geo_l, int64_t n_m2l,
+                                                     const float2* __restrict__ Mdf, double* __restrict__ Lam,
+                                                     int* __restrict__ counter) {
+  constexpr int NC = ncoef(P);
+  constexpr int NCP = ncoef_pad(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  float2* rows = reinterpret_cast<float2*>(smem_raw) + (size_t)warp * 32 * NC;
+  float2* mine = rows + lane * NC;
+  auto geo = [&](int f, int64_t i) { return dff(geo_h[(int64_t)f * n_m2l + i], geo_l[(int64_t)f * n_m2l + i]); };
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= n_targets) break;
+    const int64_t g = order[t];
+    const int64_t b = off[g], e = off[g + 1];
+    for (int c = 0; c < NC; c++) mine[c] = make_float2(0.f, 0.f);
+    for (int64_t i = b + lane; i < e; i += 32) {
+      const float2* ms = Mdf + (int64_t)src[i] * NCP;
+      dff v[NC];
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        const float2 x = ms[c];
+        v[c] = dff(x.x, x.y);
+      }
+      const dff rinv = geo(0, i), uS = geo(1, i), uT = geo(2, i);
+      dff cp[P], sp[P], ct[P], st[P];
+#pragma unroll
+      for (int m = 0; m < P; m++) {
+        cp[m] = geo(3 + m, i);
+        sp[m] = geo(3 + P + m, i);
+        ct[m] = geo(3 + 2 * P + m, i);
+        st[m] = geo(3 + 3 * P + m, i);
+      }
+      translate_rotated<P>(v, cp, sp, ct, st, [&](dff (&w)[NC]) { axial_m2l<P>(w, uS, uT, rinv); });
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        const float2 a = mine[c];
+        const dff s = dff(a.x, a.y) + v[c];
+        mine[c] = make_float2(s.h, s.l);
+      }
+    }
+    __syncwarp();
+    double* out = Lam + g * NCP;
+    for (int c = lane; c < NCP; c += 32) {
+      dff s(0.f, 0.f);
+      if (c < NC) {
+        for (int j = 0; j < 32; j++) {
+          const float2 a = rows[j * NC + c];
+          s = s + dff(a.x, a.y);
+        }
+      }
+      out[c] = to_double(s);
+    }
+    __syncwarp();
+  }
+}
+
+// FP64 values as double-float pairs (the multipoles before the M2L above)
+__global__ void to_dff_kernel(int64_t n, const double* __restrict__ x, float2* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const dff d(x[i]);
+    y[i] = make_float2(d.h, d.l);
   }
 }
 
@@ -1996,8 +2077,44 @@ constexpr bool kOverlapFarField = kSchedule == kFarSide;
 constexpr int kM2LBlocksPerSM = 1;
 
 // Downward pass: M2L over the whole list, then L2L in direct form.
+// FP64DF: the multipoles as double-float pairs, then the double-float M2L
 template <int P>
-void run_m2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+void run_m2l_df(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
+  const size_t smem = (size_t)4 * 32 * ncoef(P) * sizeof(float2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_kernel_df<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  stage_event(t, FMM_STAGE_M2L, false, st);
+  const int64_t nm = t->n_boxes * (int64_t)ncoef_pad(P);
+  to_dff_kernel<<<grid_for(nm, 256), 256, 0, st>>>(nm, reinterpret_cast<const double*>(pp.M), t->m_df);
+  FMM_LAUNCH_CHECK();
+  FMM_CUDA_TRY(cudaMemsetAsync(t->counters, 0, sizeof(int), st));
+  int dev = 0, nsm = 0, occ = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, m2l_kernel_df<P>, 128, smem));
+  if (occ < 1) occ = 1;
+  int64_t blocks = (int64_t)nsm * occ;
+  const int64_t need = (t->n_boxes + 3) / 4;
+  if (blocks > need) blocks = need;
+  m2l_kernel_df<P><<<(int)blocks, 128, smem, st>>>(t->n_boxes, t->m2l_order, t->m2l_off, t->m2l_src, t->geo32,
+                                                   t->geo_lo, t->n_m2l, t->m_df,
+                                                   reinterpret_cast<double*>(pp.Lam), t->counters);
+  FMM_LAUNCH_CHECK();
+  t->launches += 2;
+  stage_event(t, FMM_STAGE_M2L, true, st);
+}
+
+template <int P>
+void run_m2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st, bool df_far = false) {
+  if constexpr (!kF32) {
+    if (df_far && t->geo_lo && t->m_df) {
+      run_m2l_df<P>(t, pp, st);
+      return;
+    }
+  }
   const size_t smem = (size_t)4 * 32 * m2l_chunks<P>() * 16;
   static bool attr_set = false;
   if (!attr_set) {
@@ -2043,8 +2160,8 @@ void run_l2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 }
 
 template <int P>
-void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
-  run_m2l<P>(t, pp, st);
+void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st, bool df_far = false) {
+  run_m2l<P>(t, pp, st, df_far);
   run_l2l<P>(t, pp, st);
 }
 
@@ -2244,7 +2361,7 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
   auto downward = [&](cudaStream_t ss) {
     dispatch_p(t->prm.p, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
-      run_downward<P>(t, pp, ss);
+      run_downward<P>(t, pp, ss, df);
     });
   };
   const bool sym = uses_sym(t, field != nullptr);
@@ -2257,7 +2374,7 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
   auto m2l = [&](cudaStream_t ss) {
     dispatch_p(t->prm.p, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
-      run_m2l<P>(t, pp, ss);
+      run_m2l<P>(t, pp, ss, df);
     });
   };
   auto l2l = [&](cudaStream_t ss) {

@@ -1,6 +1,7 @@
 // Device-side expansion algebra, compiled once per precision: the including
 // translation unit defines `real` (float or double) before including this
-// header.  Table entries come from tables_gen.h (written by gen_tables.py).
+// header.  The rotations and the axial M2L are templates on the value type,
+// so that the FP64-accurate path can also run them on double-float values.  Table entries come from tables_gen.h (written by gen_tables.py).
 //
 // Coefficient (n, m) of an order-P expansion is v[n*n + n + m].  All loops
 // run over compile-time indices, so the coefficient vector stays in registers
@@ -91,13 +92,13 @@ __device__ __forceinline__ real fmar(real a, real b, real c) { return fma(a, b, 
 
 // Azimuthal rotation (App. B.1 form, identical for multipoles and locals in
 // the internal basis).  INV applies the opposite angle.
-template <int P, bool INV>
-__device__ __forceinline__ void rot_z(real (&v)[ncoef(P)], const real (&c)[P], const real (&s)[P]) {
+template <int P, bool INV, class T>
+__device__ __forceinline__ void rot_z(T (&v)[ncoef(P)], const T (&c)[P], const T (&s)[P]) {
 #pragma unroll
   for (int n = 1; n <= P; n++)
 #pragma unroll
     for (int m = 1; m <= n; m++) {
-      real a = v[ix(n, m)], b = v[ix(n, -m)];
+      T a = v[ix(n, m)], b = v[ix(n, -m)];
       if (!INV) {
         v[ix(n, m)] = fmar(a, c[m - 1], -b * s[m - 1]);
         v[ix(n, -m)] = fmar(b, c[m - 1], a * s[m - 1]);
@@ -110,21 +111,24 @@ __device__ __forceinline__ void rot_z(real (&v)[ncoef(P)], const real (&c)[P], c
 
 // v <- B v (INV = false) or B^-1 v (INV = true), degree by degree, skipping
 // the structural zeros.
-template <int P, bool INV>
-__device__ __forceinline__ void apply_b(real (&v)[ncoef(P)]) {
+template <int P, bool INV, class T>
+__device__ __forceinline__ void apply_b(T (&v)[ncoef(P)]) {
   sfor<1, P + 1>([&](auto nn) {
     constexpr int n = decltype(nn)::value;
     constexpr int w = 2 * n + 1;
-    real out[w];
+    T out[w];
     sfor<0, w>([&](auto ii) {
       constexpr int i = decltype(ii)::value;
-      real acc = real(0);
+      T acc = T(0.0);
       sfor<0, w>([&](auto jj) {
         constexpr int j = decltype(jj)::value;
         constexpr bool nz = INV ? bi_nz(n, i, j) : b_nz(n, i, j);
         if constexpr (nz) {
           constexpr double c = INV ? gen::kBi[b_off(n) + i * w + j] : gen::kB[b_off(n) + i * w + j];
-          if constexpr (c != 0.0) acc = fmar(real(c), v[n * n + j], acc);
+          if constexpr (c != 0.0) {
+            constexpr T cc = T(c);
+            acc = fmar(cc, v[n * n + j], acc);
+          }
         }
       });
       out[i] = acc;
@@ -138,10 +142,10 @@ __device__ __forceinline__ void apply_b(real (&v)[ncoef(P)]) {
 // transform `axial`, rotate back.  Both polar rotations run through one copy
 // of the quarter-turn products (a two-pass loop, the second pass with the
 // opposite angle), which halves the instruction footprint of the kernels.
-template <int P, class Axial>
-__device__ __forceinline__ void translate_rotated(real (&v)[ncoef(P)], const real (&cp)[P], const real (&sp)[P],
-                                                  const real (&ct)[P], const real (&st)[P], Axial&& axial) {
-  real s[P];
+template <int P, class T, class Axial>
+__device__ __forceinline__ void translate_rotated(T (&v)[ncoef(P)], const T (&cp)[P], const T (&sp)[P],
+                                                  const T (&ct)[P], const T (&st)[P], Axial&& axial) {
+  T s[P];
 #pragma unroll
   for (int m = 0; m < P; m++) s[m] = st[m];
   rot_z<P, false>(v, cp, sp);
@@ -158,10 +162,10 @@ __device__ __forceinline__ void translate_rotated(real (&v)[ncoef(P)], const rea
 }
 
 // Axial M2L in the scaled basis (App. B.3), in place: multipole -> local.
-template <int P>
-__device__ __forceinline__ void axial_m2l(real (&v)[ncoef(P)], real uS, real uT, real rinv) {
-  real pS[P + 1], pT[P + 1];
-  pS[0] = real(1);
+template <int P, class T>
+__device__ __forceinline__ void axial_m2l(T (&v)[ncoef(P)], T uS, T uT, T rinv) {
+  T pS[P + 1], pT[P + 1];
+  pS[0] = T(1.0);
   pT[0] = rinv;
 #pragma unroll
   for (int k = 1; k <= P; k++) {
@@ -171,16 +175,17 @@ __device__ __forceinline__ void axial_m2l(real (&v)[ncoef(P)], real uS, real uT,
   sfor<0, 2 * P + 1>([&](auto mm) {
     constexpr int m = decltype(mm)::value - P;
     constexpr int am = m < 0 ? -m : m;
-    real in[P + 1];
+    T in[P + 1];
 #pragma unroll
     for (int k = am; k <= P; k++) in[k] = v[ix(k, m)] * pS[k];
     sfor<am, P + 1>([&](auto nn) {
       constexpr int n = decltype(nn)::value;
-      real acc = real(0);
+      T acc = T(0.0);
       sfor<am, P + 1>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
         constexpr double c = gen::kAxM2L[ax_id(n, k, am)];
-        acc = fmar(real(c), in[k], acc);
+        constexpr T cc = T(c);
+        acc = fmar(cc, in[k], acc);
       });
       v[ix(n, m)] = acc * pT[n];
     });

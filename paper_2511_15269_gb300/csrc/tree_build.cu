@@ -1399,6 +1399,25 @@ __global__ void offset_i64_kernel(int64_t* __restrict__ dst, const int64_t* __re
 
 }  // namespace
 
+namespace {
+__global__ void geo_lo_kernel(int64_t n, const double* __restrict__ g64, const float* __restrict__ g32,
+                              float* __restrict__ lo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    lo[i] = (float)(g64[i] - (double)g32[i]);
+}
+}  // namespace
+
+void prepare_df_far(fmm_tree* t, cudaStream_t st) {
+  if (t->geo_lo || t->two_trees) return;
+  const int p = t->prm.p;
+  const int64_t ng = (int64_t)m2l_fields(p) * std::max<int64_t>(t->n_m2l, 1);
+  t->geo_lo = dev_alloc<float>(t, ng);
+  geo_lo_kernel<<<grid_for(ng, 256), 256, 0, st>>>(ng, t->geo64, t->geo32, t->geo_lo);
+  FMM_LAUNCH_CHECK();
+  t->m_df = dev_alloc<float2>(t, (size_t)t->n_boxes * ncoef_pad(p));
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
 // Direct L2L records of a tree whose lists, geometry and parents are set
 // (single trees, separate hierarchies and merged batches alike).
 void build_l2l_direct(fmm_tree* t, cudaStream_t st) {
