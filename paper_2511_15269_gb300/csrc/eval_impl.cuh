@@ -1823,48 +1823,55 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : 1) p2p_kernel_dfs(P2PArgs 
           }
           if (lane == 0) dst[j] = (double)acc.h + (double)acc.l;
         }
-      } else
-      for (int c0 = 0; c0 < scount; c0 += 16) {
-        dfl P[16];
+      } else {
+        // the mask decided once per entry: each variant's unrolled chunk
+        // loop is one contiguous stretch of code (instruction-cache footprint)
+        auto chunks = [&](auto mk) {
+          constexpr bool MK = decltype(mk)::value;
+          for (int c0 = 0; c0 < scount; c0 += 16) {
+            dfl P[16];
 #pragma unroll
-        for (int jj = 0; jj < 16; jj++) {
-          const int j = c0 + jj;
-          P[jj] = dfl{0.f, 0.f};
-          if (j < scount) {
-            const float4 sh = sb[2 * j], slo = sb[2 * j + 1];
+            for (int jj = 0; jj < 16; jj++) {
+              const int j = c0 + jj;
+              P[jj] = dfl{0.f, 0.f};
+              if (j < scount) {
+                const float4 sh = sb[2 * j], slo = sb[2 * j + 1];
 #pragma unroll
-            for (int k = 0; k < TPL; k++) {
-              float y, yl;
-              if (mask) df_rinv<true>(th[k], tl[k], sh, slo, y, yl);
-              else df_rinv<false>(th[k], tl[k], sh, slo, y, yl);
-              const float p = sh.w * y;
-              df_acc(u[k], p, fmaf(sh.w, yl, fmaf(slo.w, y, fmaf(sh.w, y, -p))));
-              const float pq = tq[k].h * y;
-              df_acc(P[jj], pq, fmaf(tq[k].h, yl, fmaf(tq[k].l, y, fmaf(tq[k].h, y, -pq))));
+                for (int k = 0; k < TPL; k++) {
+                  float y, yl;
+                  df_rinv<MK>(th[k], tl[k], sh, slo, y, yl);
+                  const float p = sh.w * y;
+                  df_acc(u[k], p, fmaf(sh.w, yl, fmaf(slo.w, y, fmaf(sh.w, y, -p))));
+                  const float pq = tq[k].h * y;
+                  df_acc(P[jj], pq, fmaf(tq[k].h, yl, fmaf(tq[k].l, y, fmaf(tq[k].h, y, -pq))));
+                }
+              }
             }
-          }
-        }
-        // reduce-scatter over lane bits 4..1 (lane l ends with P[l >> 1]), then the lane pair
+            // reduce-scatter over lane bits 4..1 (lane l ends with P[l >> 1]), then the lane pair
 #pragma unroll
-        for (int m = 16, hh = 8; hh >= 1; m >>= 1, hh >>= 1) {
-          const bool up = (lane & m) != 0;
+            for (int m = 16, hh = 8; hh >= 1; m >>= 1, hh >>= 1) {
+              const bool up = (lane & m) != 0;
 #pragma unroll
-          for (int i = 0; i < hh; i++) {
-            const dfl keep = up ? P[i + hh] : P[i];
-            const dfl send = up ? P[i] : P[i + hh];
-            const float rh = __shfl_xor_sync(0xffffffffu, send.h, m);
-            const float rl = __shfl_xor_sync(0xffffffffu, send.l, m);
-            P[i] = keep;
-            df_acc(P[i], rh, rl);
+              for (int i = 0; i < hh; i++) {
+                const dfl keep = up ? P[i + hh] : P[i];
+                const dfl send = up ? P[i] : P[i + hh];
+                const float rh = __shfl_xor_sync(0xffffffffu, send.h, m);
+                const float rl = __shfl_xor_sync(0xffffffffu, send.l, m);
+                P[i] = keep;
+                df_acc(P[i], rh, rl);
+              }
+            }
+            {
+              const float rh = __shfl_xor_sync(0xffffffffu, P[0].h, 1);
+              const float rl = __shfl_xor_sync(0xffffffffu, P[0].l, 1);
+              df_acc(P[0], rh, rl);
+            }
+            const int j = c0 + (lane >> 1);
+            if ((lane & 1) == 0 && j < scount) dst[j] = (double)P[0].h + (double)P[0].l;
           }
-        }
-        {
-          const float rh = __shfl_xor_sync(0xffffffffu, P[0].h, 1);
-          const float rl = __shfl_xor_sync(0xffffffffu, P[0].l, 1);
-          df_acc(P[0], rh, rl);
-        }
-        const int j = c0 + (lane >> 1);
-        if ((lane & 1) == 0 && j < scount) dst[j] = (double)P[0].h + (double)P[0].l;
+        };
+        if (mask) chunks(std::true_type{});
+        else chunks(std::false_type{});
       }
     }
     __syncwarp();
