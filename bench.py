@@ -488,7 +488,7 @@ def main():
         line["fp64"] = {"value": n / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
                         "fp32c_speedup": ms64 / ms}
         line["fp64df"] = {"value": n / (ms64df * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64df,
-                          "what": "FP64 far field, double-float near field (FMM_FP64DF)",
+                          "what": "double-float near field and M2L (p <= 8), the other far-field stages in FP64 (FMM_FP64DF)",
                           "rel_l2_vs_fp64": rel_l2(u64df, u64), "rel_l2_vs_direct": rel_l2(u64df, ud)}
         line["errors_vs_direct_4096_targets"] = {
             "fp32c_rel_l2": rel_l2(u32, ud), "fp32c_rel_linf": rel_linf(u32, ud),

@@ -62,8 +62,8 @@ enum {
                     local sums; rotation coefficients generated in FP64; final
                     near + far combination in FP64                             */
   FMM_FP64DF = 2  /* FP64 accuracy: as FMM_FP64, except that the potential
-                    near field and the M2L of a tree of one point set (or a
-                    batch of them) run in double-float arithmetic (unevaluated
+                    near field and (for p <= 8) the M2L of a tree of one point
+                    set (or a batch of them) run in double-float arithmetic (unevaluated
                     sums of two FP32 values, error-free transformations) on the
                     FP32 pipes, with results within a few 1e-14 of FP64;
                     fields, backward and two-hierarchy trees use FP64          */

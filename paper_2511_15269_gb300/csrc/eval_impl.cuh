@@ -2116,7 +2116,10 @@ void run_m2l_df(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 
 template <int P>
 void run_m2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st, bool df_far = false) {
-  if constexpr (!kF32) {
+  // the double-float M2L up to p = 8 (2^20 cube, p = 8: 11.1 ms against
+  // 18.8 ms in FP64); at p = 10 its register spills make it slower (24.7 ms
+  // against 20.1 ms on the paper's set 3), so FP64 from p = 9 on
+  if constexpr (!kF32 && P <= 8) {
     if (df_far && t->geo_lo && t->m_df) {
       run_m2l_df<P>(t, pp, st);
       return;
