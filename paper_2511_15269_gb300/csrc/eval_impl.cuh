@@ -2418,7 +2418,8 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     // beside M2L and L2L on the higher-priority stream (beside L2L alone:
     // 2.08 / 0.511 / 53.7 ms on the three workloads below, against 2.08 /
     // 0.503 / 43.1; on the caller's stream with M2L and L2L on the
-    // higher-priority one: 2.061 / 0.505 / 52.8, against 2.058 / 0.506 / 42.6)
+    // higher-priority one: 2.061 / 0.505 / 52.8, against 2.058 / 0.506 / 42.6;
+    // the gather on a grid of 2 blocks per SM: 2.130 / - / 61.8)
     fork();
     upward(t->far_stream);
     near();
