@@ -199,7 +199,8 @@ void fmm_tree_free(fmm_tree* tree);
  * (same p and splits; leaf sizes may differ), whose points are the
  * concatenation of the trees' points in the given order.  Every evaluation
  * entry point accepts it, with q, u, field, gradients of the concatenated
- * length; each stage then runs as one launch over the whole batch (a whole
+ * length; each stage then runs as one launch over the whole batch (M2M: one
+ * per round; a whole
  * evaluation can be captured as one CUDA graph).  The input trees stay valid
  * and independent; free the batch with fmm_tree_free.  Synchronous.
  * Errors: FMM_ERR_INVALID_ARG (mismatched trees, nested batches), FMM_ERR_OOM,
