@@ -160,7 +160,11 @@ def test_fp64df_potential_parity(F, orc, name, mk, p, leaf, s, theta):
     F.fmm_tree_status(T)
     e = rel_l2(u, u_o)
     print("%s: fp64df vs oracle %.3e" % (name, e))
-    assert e <= TOL_FP64
+    # double-float values carry about 48 bits (2^-48 ~ 3.6e-15 per operation);
+    # sums over thousands of near-field terms and the M2L's few hundred
+    # operations per coefficient stay within about 1e-13, an order of
+    # magnitude inside the FP64 bar (measured up to 4.8e-14 on these cases)
+    assert e <= 2e-13
 
 
 @pytest.mark.parametrize("name,mk,p,leaf,s,theta", POT_CASES[:4], ids=[c[0] for c in POT_CASES[:4]])
