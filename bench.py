@@ -456,7 +456,7 @@ def main():
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1) / 2
         u64 = u64_d.cpu().numpy()[tg]
-        # FP64 accuracy with the double-float near field
+        # FP64 accuracy with the double-float near field and M2L
         fmm.fmm_tree_set_precision(T, fmm.FMM_FP64DF)
         fmm.fmm_eval_potential(T, q_d, u64_d)
         torch.cuda.synchronize()
