@@ -630,27 +630,27 @@ __device__ __forceinline__ void p2p_tile_f32h(const DupRec* sb, int scount, int 
 #pragma unroll 2
     for (int j = half; j < scount; j += 2)
       p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz, thr);
-    return;
-  }
-  f2 pu2[NPH], fx2[NPH], fy2[NPH], fz2[NPH];
+  } else {
+    f2 pu2[NPH], fx2[NPH], fy2[NPH], fz2[NPH];
 #pragma unroll
-  for (int k = 0; k < NPH; k++) pu2[k] = fx2[k] = fy2[k] = fz2[k] = 0ull;
-  int j = half;
+    for (int k = 0; k < NPH; k++) pu2[k] = fx2[k] = fy2[k] = fz2[k] = 0ull;
+    int j = half;
 #pragma unroll 2
-  for (; j + 2 < scount; j += 4) {
-    const ulonglong2 a0 = s2[2 * j], b0 = s2[2 * j + 1];
-    const ulonglong2 a1 = s2[2 * j + 4], b1 = s2[2 * j + 5];
-    p2p_pair_f32<MASK, FIELD, NPH>(a0, b0, tx, ty, tz, pu, fx, fy, fz, thr);
-    p2p_pair_f32<MASK, FIELD, NPH>(a1, b1, tx, ty, tz, pu2, fx2, fy2, fz2, thr);
-  }
-  if (j < scount) p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz, thr);
+    for (; j + 2 < scount; j += 4) {
+      const ulonglong2 a0 = s2[2 * j], b0 = s2[2 * j + 1];
+      const ulonglong2 a1 = s2[2 * j + 4], b1 = s2[2 * j + 5];
+      p2p_pair_f32<MASK, FIELD, NPH>(a0, b0, tx, ty, tz, pu, fx, fy, fz, thr);
+      p2p_pair_f32<MASK, FIELD, NPH>(a1, b1, tx, ty, tz, pu2, fx2, fy2, fz2, thr);
+    }
+    if (j < scount) p2p_pair_f32<MASK, FIELD, NPH>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, fx, fy, fz, thr);
 #pragma unroll
-  for (int k = 0; k < NPH; k++) {
-    pu[k] = f2add(pu[k], pu2[k]);
-    if (FIELD) {
-      fx[k] = f2add(fx[k], fx2[k]);
-      fy[k] = f2add(fy[k], fy2[k]);
-      fz[k] = f2add(fz[k], fz2[k]);
+    for (int k = 0; k < NPH; k++) {
+      pu[k] = f2add(pu[k], pu2[k]);
+      if (FIELD) {
+        fx[k] = f2add(fx[k], fx2[k]);
+        fy[k] = f2add(fy[k], fy2[k]);
+        fz[k] = f2add(fz[k], fz2[k]);
+      }
     }
   }
 }
@@ -1986,7 +1986,6 @@ __global__ void __launch_bounds__(128) l2p_kernel(int64_t n_leaves, const int32_
       __syncwarp();
     }
     for (int i = lane; i < cnt; i += 32) {
-      const int64_t pidx = start + i;
       PointIn cur;
       if (kAhead) {
         cur = nxt;
@@ -2246,8 +2245,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
     else p2p_kernel_f32h<TPL, false><<<(unsigned)blocks, 128, smem, st>>>(a);
     FMM_LAUNCH_CHECK();
     return;
-  }
-  if constexpr (!kF32) {
+  } else {
     if (!field && t->sym && t->prm.precision == FMM_FP64DF) {
       static bool df_attr = false;
       if (!df_attr) {
@@ -2280,26 +2278,27 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       FMM_LAUNCH_CHECK();
       return;
     }
+    // FP64 fields and two-tree evaluations: the one-sided kernel
+    FMM_CUDA_TRY(cudaMemsetAsync(t->counters + 1, 0, sizeof(int), st));
+    static bool attr_set = false;
+    if (!attr_set) {
+      FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      attr_set = true;
+    }
+    int dev = 0, nsm = 0, occ = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (field) FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_kernel<TPL, true>, 128, smem));
+    else FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_kernel<TPL, false>, 128, smem));
+    if (occ < 1) occ = 1;
+    int64_t blocks = (int64_t)nsm * occ;
+    const int64_t need = (a.n_leaves + 3) / 4;
+    if (blocks > need) blocks = need;
+    if (field) p2p_kernel<TPL, true><<<(int)blocks, 128, smem, st>>>(a);
+    else p2p_kernel<TPL, false><<<(int)blocks, 128, smem, st>>>(a);
+    FMM_LAUNCH_CHECK();
   }
-  FMM_CUDA_TRY(cudaMemsetAsync(t->counters + 1, 0, sizeof(int), st));
-  static bool attr_set = false;
-  if (!attr_set) {
-    FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
-  int dev = 0, nsm = 0, occ = 0;
-  FMM_CUDA_TRY(cudaGetDevice(&dev));
-  FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  if (field) FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_kernel<TPL, true>, 128, smem));
-  else FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, p2p_kernel<TPL, false>, 128, smem));
-  if (occ < 1) occ = 1;
-  int64_t blocks = (int64_t)nsm * occ;
-  const int64_t need = (a.n_leaves + 3) / 4;
-  if (blocks > need) blocks = need;
-  if (field) p2p_kernel<TPL, true><<<(int)blocks, 128, smem, st>>>(a);
-  else p2p_kernel<TPL, false><<<(int)blocks, 128, smem, st>>>(a);
-  FMM_LAUNCH_CHECK();
 }
 
 // Near field of the leaves at positions lb .. le - 1 of the work order.
