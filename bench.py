@@ -34,12 +34,42 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpoints/s per FMM eval at 1M pts, FP32 vs FP64 at stated error; bwd/fwd ratio"
 WORKLOAD = "cube1m_p8"
 FP32_FLOPS_PER_PAIR = 10  # potential, per ordered pair: 3 sub, 5 for r^2, 2 for the accumulating FMA
-# DRAM bytes (read + write) of one launch of the symmetric near-field kernel on
-# this workload, from the ncu capture in profiles/p2p_kernel_f32s_dram_cube1m_p8.md
-# (100.51 MB read + 231.45 MB write); None once the kernel changes.
-P2P_TRAFFIC_BYTES = 330.96e6
+# Algorithmic multiply-adds of one M2L interaction (two polar rotations, the
+# axial M2L and two azimuthal rotations) by expansion order; two flops each.
+M2L_MACS = {4: 335, 6: 861, 8: 1755, 10: 3113}
 SMS = 152
 FP32_LANES = 128
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_per_launch.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2511_15269_gb300", "csrc", f)
+                  for f in ("eval_impl.cuh", "expansion.cuh", "common.cuh")]
+
+
+def kernel_source_hash():
+    """Short hash of the evaluation kernels' sources (recorded beside each DRAM
+    traffic figure so that a figure is used only for the kernels it was
+    measured on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM read + write bytes per launch of `kernel` on `workload` from the
+    recorded ncu figures, or None when none was taken with the current kernel
+    sources.  Lines: kernel workload bytes source_hash."""
+    try:
+        lines = open(TRAFFIC_FILE).read().splitlines()
+    except OSError:
+        return None
+    cur = kernel_source_hash()
+    for ln in lines:
+        f = ln.split()
+        if len(f) == 4 and not ln.startswith("#") and f[0] == kernel and f[1] == workload and f[3] == cur:
+            return float(f[2])
+    return None
 
 
 def parse():
@@ -114,14 +144,48 @@ def rel_linf(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-def oracle_sample_eval(O, q, p, leaves, n_leaves):
-    """Oracle FMM at every point of the given target leaves; returns (points, seconds)."""
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def oracle_sample(O, q, p, n_leaves, rng):
+    """One bounded sample of the oracle FMM: the upward pass (P2M, M2M) over
+    every point, then M2L and L2L into the boxes that feed the points of
+    `n_leaves` random target leaves, and L2P + P2P at those points.  The
+    stages restricted to the sample are scaled by the work of a full
+    evaluation (M2L interactions, L2L translations, evaluated points) to the
+    implied time of one evaluation at every point."""
     off = O.level_offset(O.L)
+    leaves = rng.choice(O.n_leaves, n_leaves, replace=False)
     tg = np.concatenate([O.perm[O.box_start[off + l]:O.box_start[off + l] + O.box_count[off + l]]
                          for l in leaves]).astype(np.int64)
     t0 = time.perf_counter()
-    O.eval(q, p, targets=tg)
-    return len(tg), time.perf_counter() - t0
+    _, tm = O.eval_timed(q, p, tg)
+    wall = time.perf_counter() - t0
+    up = tm["sort"] + tm["p2m"] + tm["m2m"]
+    down = (tm["m2l"] * O.n_m2l / max(tm["n_m2l_done"], 1.0)
+            + tm["l2l"] * (O.n_boxes - 1) / max(tm["n_l2l_done"], 1.0)
+            + tm["eval"] * O.n / max(tm["n_eval"], 1.0))
+    return {"implied_s": up + down, "upward_s": up, "downward_implied_s": down,
+            "m2l_s_per_interaction": tm["m2l"] / max(tm["n_m2l_done"], 1.0),
+            "eval_s_per_point": tm["eval"] / max(tm["n_eval"], 1.0),
+            "sample_points": int(tm["n_eval"]), "sample_m2l": int(tm["n_m2l_done"]), "wall_s": wall}
+
+
+def oracle_baseline(O, q, p, threads, n_leaves, rng):
+    """The oracle at `threads` OpenMP threads on one bounded sample."""
+    import oracle
+    oracle.set_num_threads(threads)
+    r = oracle_sample(O, q, p, n_leaves, rng)
+    r["threads"] = oracle.num_threads()
+    return r
 
 
 def run_reference(args, cfg):
@@ -134,27 +198,33 @@ def run_reference(args, cfg):
     pos, q = workloads.uniform_cube(cfg["n"], seed=0)
     O = oracle.Tree(pos, cfg["leaf_size"], cfg["s"], cfg["theta"])
     rng = np.random.default_rng(7)
-    # each step: the oracle FMM at all points of 32 random target leaves, so
-    # that warm-up + steps stay within a few minutes
-    per_step = []
-    pts = 0
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_num_threads(cores)
+    # each step: one bounded sample (full upward pass, downward pass for the
+    # points of 4 random target leaves), scaled to one full evaluation
+    implied, walls, last = [], [], None
     for k in range(args.warmup + args.steps):
-        leaves = rng.choice(O.n_leaves, 32, replace=False)
-        m, dt = oracle_sample_eval(O, q, cfg["p"], leaves, O.n_leaves)
+        r = oracle_sample(O, q, cfg["p"], 4, rng)
         if k >= args.warmup:
-            per_step.append(dt)
-            pts += m
-    secs = sum(per_step)
-    value = pts / secs / 1e6
-    cores = oracle.num_threads()
-    sample = ("oracle FP64 FMM (rotation-based, OpenMP) at every point of 32 random target leaves "
-              "(~2048 points) per step, full P2M/M2M of the 2^20-point tree included; tree prebuilt")
+            implied.append(r["implied_s"])
+            walls.append(r["wall_s"])
+            last = r
+    t_eval = float(np.mean(implied))
+    value = cfg["n"] / t_eval / 1e6
+    sample = ("oracle FP64 FMM (rotation-based, OpenMP, %d threads): per step the upward pass over all "
+              "%d points, then M2L/L2L into the boxes feeding the points of 4 random target leaves and "
+              "L2P + P2P there; the restricted stages scaled by the full evaluation's work (M2L "
+              "interactions, L2L translations, points) to the implied time of one evaluation at every "
+              "point; tree prebuilt" % (oracle.num_threads(), cfg["n"]))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(per_step),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(cfg, "FP64 CPU oracle"),
-        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "implied_ms_per_eval": 1e3 * t_eval,
+        "cpu_baseline": {"value": value, "unit": "Mpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample, "cpu_model": cpu_model(),
+                         "upward_s": last["upward_s"], "downward_implied_s": last["downward_implied_s"]},
         "e2e": {"value": value, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -379,6 +449,12 @@ def main():
     fmm.fmm_tree_profile(T, False)
     launches = fmm.fmm_tree_stats(T)["kernel_launches"] - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    timing = {"protocol": "value: mean of the timed steps (CUDA events around each eager call, L2 flushed "
+                          "before each); min / median of the same steps; graph_*: 100 replays of one "
+                          "evaluation captured in a CUDA graph, L2 not flushed (the paper's minimum of 100 "
+                          "runs, Sec. III.A)",
+              "mean_ms": float(np.mean(step_ms)), "min_ms": float(np.min(step_ms)),
+              "median_ms": float(np.median(step_ms))}
     # whole job: points of all ranks over the slowest rank's mean step time
     value, _, ms = replicas.aggregate_throughput(n, float(np.mean(step_ms)), device=dev)
     stage, calls = fmm.fmm_tree_stage_times(T)
@@ -403,7 +479,10 @@ def main():
     achieved = pairs * FP32_FLOPS_PER_PAIR / p2p_s / 1e12
     roofline = {"bound": "alu", "kernel": "p2p_kernel_f32s (symmetric near field, FP32 + MUFU rsqrt)",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                "traffic": P2P_TRAFFIC_BYTES if n == 1 << 20 else None,
+                "traffic": recorded_traffic("p2p_kernel_f32s", "cube%d_p%d" % (n, cfg["p"])),
+                "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu), "
+                                  "recorded with the hash of the kernel sources it was taken on; null when "
+                                  "the sources changed since",
                 "peak_source": "measured: fmm_device_peaks FP32 FMA probe (scalar %.1f, packed %.1f TFLOP/s); "
                                "derived 152 SMs x 128 lanes x 2 x %.0f MHz = %.1f"
                                % (peaks["fp32_fma_tflops"], peaks["fp32x2_fma_tflops"], clk, derived_tflops),
@@ -412,6 +491,16 @@ def main():
                 "rsqrt_per_launch": rsqrt_count,
                 "mufu_frac": rsqrt_count / p2p_s / (peaks["rsqrt_gops"] * 1e9),
                 "mufu_peak_gops": peaks["rsqrt_gops"]}
+    # M2L (persistent kernel over the interaction list) by the algorithmic
+    # count: two polar and two azimuthal rotations and the axial M2L
+    m2l_flops = 2 * M2L_MACS.get(cfg["p"], 0) * st["n_m2l"]
+    m2l_ach = m2l_flops / (stage_ms["m2l"] * 1e-3) / 1e12 if stage_ms["m2l"] > 0 else 0.0
+    rooflines = {
+        "m2l": {"bound": "alu", "kernel": "m2l_kernel (FP32, rotate - axial - rotate back)",
+                "achieved": m2l_ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": m2l_ach / peak_tflops,
+                "traffic": recorded_traffic("m2l_kernel", "cube%d_p%d" % (n, cfg["p"])),
+                "interactions_per_launch": st["n_m2l"], "flops_per_interaction": 2 * M2L_MACS.get(cfg["p"], 0),
+                "m2l_ms": stage_ms["m2l"]}}
 
     # ---- end to end through the host-buffer entry point ----
     qh = torch.from_numpy(q).pin_memory()
@@ -426,13 +515,36 @@ def main():
     e2e = {"value": n / e2e_s / 1e6, "unit": "Mpoints/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
            "ms_per_step": 1e3 * e2e_s}
 
+    # ---- the paper's protocol: minimum and median of 100 graph replays ----
+    graph_ms = []
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fmm.fmm_eval_potential(T, q_d, u_d)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        fmm.fmm_eval_potential(T, q_d, u_d)
+    graph.replay()
+    torch.cuda.synchronize()
+    for _ in range(100):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        b.synchronize()
+        graph_ms.append(a.elapsed_time(b))
+    del graph
+    timing.update(graph_min_ms=float(np.min(graph_ms)), graph_median_ms=float(np.median(graph_ms)))
+
     line = {
         "metric": METRIC, "value": value, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(cfg, "FP32-compensated path"),
-        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-        "wall_s_timed": wall, "tree_build_ms": build_ms,
+        "roofline": roofline, "rooflines": rooflines, "e2e": e2e, "gpu_launches": launches,
+        "launches_per_eval": launches / max(args.steps, 1), "clocks": clocks,
+        "wall_s_timed": wall, "tree_build_ms": build_ms, "timing": timing,
         "stage_ms": stage_ms,
         "tree": {k: st[k] for k in ("levels", "n_boxes", "n_m2l", "n_p2p", "n_p2p_pairs", "device_bytes")},
         "device_peaks": peaks,
@@ -444,18 +556,35 @@ def main():
         tg = workloads.sample_targets(n, 4096, seed=1)
         ud = oracle.direct(pos, q, targets=tg)
         u32 = u_d.cpu().numpy()[tg]
-        # FP64 path on the same tree
+        # FP64 path on the same tree, with per-stage times for its rooflines
         fmm.fmm_tree_set_precision(T, fmm.FMM_FP64)
         u64_d = fmm.fmm_eval_potential(T, q_d)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fmm.fmm_tree_profile(T, True)
         e0.record()
         for _ in range(2):
             fmm.fmm_eval_potential(T, q_d, u64_d)
         e1.record()
         torch.cuda.synchronize()
+        fmm.fmm_tree_profile(T, False)
         ms64 = e0.elapsed_time(e1) / 2
+        st64, calls64 = fmm.fmm_tree_stage_times(T)
+        st64 = {k: v / max(calls64, 1) for k, v in st64.items()}
         u64 = u64_d.cpu().numpy()[tg]
+        dfma = peaks["fp64_fma_tflops"]
+        p2p64 = pairs * FP32_FLOPS_PER_PAIR / (st64["p2p"] * 1e-3) / 1e12
+        m2l64 = m2l_flops / (st64["m2l"] * 1e-3) / 1e12
+        rooflines["p2p_fp64"] = {"bound": "alu", "kernel": "p2p_kernel_f64s (symmetric near field, FP64)",
+                                 "achieved": p2p64, "peak": dfma, "unit": "TFLOP/s", "frac": p2p64 / dfma,
+                                 "peak_source": "measured FP64 FMA probe (fmm_device_peaks)",
+                                 "p2p_ms": st64["p2p"], "flops_per_pair": FP32_FLOPS_PER_PAIR,
+                                 "note": "algorithmic flops only; 1/r costs an rsqrt approximation and a "
+                                         "third-order correction (about 8 FP64 operations per unordered pair) "
+                                         "that the count leaves out"}
+        rooflines["m2l_fp64"] = {"bound": "alu", "kernel": "m2l_kernel (FP64)", "achieved": m2l64, "peak": dfma,
+                                 "unit": "TFLOP/s", "frac": m2l64 / dfma, "m2l_ms": st64["m2l"],
+                                 "flops_per_interaction": 2 * M2L_MACS.get(cfg["p"], 0)}
         # FP64 accuracy with the double-float near field and M2L
         fmm.fmm_tree_set_precision(T, fmm.FMM_FP64DF)
         fmm.fmm_eval_potential(T, q_d, u64_d)
@@ -486,7 +615,7 @@ def main():
         torch.cuda.synchronize()
         ms_field = e0.elapsed_time(e1) / 3
         line["fp64"] = {"value": n / (ms64 * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64,
-                        "fp32c_speedup": ms64 / ms}
+                        "fp32c_speedup": ms64 / ms, "stage_ms": st64}
         line["fp64df"] = {"value": n / (ms64df * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms64df,
                           "what": "double-float near field and M2L (p <= 8), the other far-field stages in FP64 (FMM_FP64DF)",
                           "rel_l2_vs_fp64": rel_l2(u64df, u64), "rel_l2_vs_direct": rel_l2(u64df, ud)}
@@ -496,22 +625,33 @@ def main():
             "fp32c_vs_fp64_rel_l2": rel_l2(u32, u64)}
         line["backward"] = {"ms": ms_bwd, "bwd_fwd_ratio": ms_bwd / ms,
                             "what": "dL/dq and dL/dpos: one near-field sweep for q and dL/du, far field of each, combine; FP32C"}
-        line["field"] = {"value": n / (ms_field * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms_field}
-        # CPU oracle baseline on bounded samples (rank 0, one GPU)
-        O = oracle.Tree(pos, cfg["leaf_size"], cfg["s"], cfg["theta"])
-        rng = np.random.default_rng(11)
-        pts, secs = 0, 0.0
-        for _ in range(3):
-            m, dt = oracle_sample_eval(O, q, cfg["p"], rng.choice(O.n_leaves, 32, replace=False), O.n_leaves)
-            pts += m
-            secs += dt
+        line["field"] = {"value": n / (ms_field * 1e-3) / 1e6, "unit": "Mpoints/s", "ms_per_step": ms_field,
+                         "field_fwd_ratio": ms_field / ms}
         line["paper_sets_cube1m"] = bench_paper_sets(fmm, dev, pos_d, q_d, tg, ud)
         line["plummer4m_p10"] = bench_plummer(fmm, workloads, oracle, dev)
         line["batched64_p6"] = bench_batched(fmm, workloads, oracle, dev)
+        # CPU oracle baseline (rank 0, one GPU): one bounded sample at all
+        # host cores and one at a single core (the paper's CPU column)
+        O = oracle.Tree(pos, cfg["leaf_size"], cfg["s"], cfg["theta"])
+        rng = np.random.default_rng(11)
+        cores = len(os.sched_getaffinity(0))
+        all_c = oracle_baseline(O, q, cfg["p"], cores, 8, rng)
+        one_c = oracle_baseline(O, q, cfg["p"], 1, 2, rng)
+        oracle.set_num_threads(cores)
         line["cpu_baseline"] = {
-            "value": pts / secs / 1e6, "unit": "Mpoints/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "oracle FP64 FMM at every point of 3 x 32 random target leaves (%d points), "
-                      "full P2M/M2M of the 2^20-point tree included each time; %.1f s" % (pts, secs)}
+            "value": n / all_c["implied_s"] / 1e6, "unit": "Mpoints/s", "cores": all_c["threads"], "kind": "oracle",
+            "sample": "oracle FP64 FMM, one bounded sample: upward pass (P2M, M2M) over all %d points timed "
+                      "in full (%.2f s), M2L/L2L into the boxes feeding the points of 8 random target leaves "
+                      "and L2P + P2P there (%d points, %d M2L interactions), scaled by the full evaluation's "
+                      "work to the implied time of one evaluation at every point (%.1f s); %.1f s of CPU wall"
+                      % (n, all_c["upward_s"], all_c["sample_points"], all_c["sample_m2l"], all_c["implied_s"],
+                         all_c["wall_s"]),
+            "cpu_model": cpu_model(), "upward_s": all_c["upward_s"],
+            "downward_implied_s": all_c["downward_implied_s"], "implied_s_per_eval": all_c["implied_s"],
+            "one_core": {"value": n / one_c["implied_s"] / 1e6, "unit": "Mpoints/s", "cores": one_c["threads"],
+                         "upward_s": one_c["upward_s"], "downward_implied_s": one_c["downward_implied_s"],
+                         "implied_s_per_eval": one_c["implied_s"], "sample_points": one_c["sample_points"],
+                         "wall_s": one_c["wall_s"]}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -144,6 +144,17 @@ int fmm_device_peaks(double* out, void* stream);
 /* Thread-local description of the last failure on this thread. */
 const char* fmm_last_error(void);
 
+/* Caps the device memory the library holds in total (every tree, batch and
+ * build scratch of the process; 0 removes the cap, the default).  A device
+ * allocation that would exceed the cap fails as if cudaMalloc had refused
+ * it: the call returns FMM_ERR_OOM and leaves no tree behind.  Memory
+ * already held is not released.  The paper has no counterpart (a budget for
+ * processes that share a GPU with other allocators).  Always FMM_OK. */
+int fmm_set_device_memory_limit(size_t bytes);
+
+/* Device memory the library holds right now, in bytes (host pointer). */
+int fmm_device_memory_in_use(size_t* bytes);
+
 /* Number of levels L for n points (Sec. II.A step 4): the smallest l with
  * ceil(n / 2^(splits l)) <= leaf_size.  Returns -1 on invalid arguments. */
 int fmm_num_levels(int64_t n, int leaf_size, int splits);
@@ -226,6 +237,16 @@ int fmm_tree_stats(const fmm_tree* tree, fmm_stats* stats);
  * kernels of earlier evaluations of this tree (FMM_OK or FMM_ERR_TIMEOUT). */
 int fmm_tree_status(fmm_tree* tree, void* stream);
 
+/* Limit, in GPU clock cycles, of each near-field warp's wait for a staged
+ * source tile (a bulk copy completing on a shared-memory barrier; Sec. II.B
+ * near field).  A warp whose wait runs out latches FMM_ERR_TIMEOUT in the
+ * tree (read by fmm_tree_status), lets its copies in flight land and stops;
+ * that evaluation's results are then incomplete.  Default about 2e9 cycles
+ * (about a second); 0 gives up before the first poll, which exercises the
+ * timeout path without any fault.  Applies to later evaluations of this
+ * tree.  Errors: FMM_ERR_INVALID_ARG (NULL tree, negative cycles). */
+int fmm_tree_set_wait_limit(fmm_tree* tree, int64_t cycles);
+
 /* Copies the hierarchy to HOST arrays for inspection; every pointer may be
  * NULL.  Sizes: perm n (tree position -> original index); box_start,
  * box_count, radius n_boxes; center 3 n_boxes; level_avg_radius levels+1;
@@ -268,15 +289,24 @@ int fmm_eval_potential_host(const fmm_tree* tree, const double* q_host, double* 
  * evaluation time: code whose device memory budget belongs to another
  * allocator, latency-critical loops that cannot absorb cudaMalloc's implicit
  * synchronisation, plug-ins allowed to allocate only at start-up).
- * Same inputs, outputs and results as fmm_eval_potential, but the per-call
- * scratch (point records, near-field sums, expansions, work counters) lives
- * in one file-scope device array of FMM_STATIC_SCRATCH_BYTES that every GPU
- * loading the library holds until the process exits.  It calls no
+ * Same inputs and outputs as fmm_eval_potential; the per-call scratch (point
+ * records, near-field sums, expansions, work counters) lives in one
+ * file-scope device array of FMM_STATIC_SCRATCH_BYTES that every GPU loading
+ * the library holds until the process exits.  It calls no
  * cudaMalloc/cudaFree and no allocating library routine.
+ *   Results: the near field runs the one-sided kernel (every target leaf
+ *   against its whole list; the symmetric kernel's per-pair slots are tree
+ *   workspace), so FP32C results differ from fmm_eval_potential by rounding
+ *   (within the FP32C tolerance), and a tree set to FMM_FP64DF is evaluated
+ *   in plain FMM_FP64 (within about 1e-13 relative of the double-float
+ *   results).  FMM_FP64 results equal fmm_eval_potential's up to the
+ *   summation order of the near field.
  *   Limits: tree->n <= FMM_STATIC_MAX_POINTS and n_boxes <=
  *   FMM_STATIC_MAX_BOXES, else FMM_ERR_CAPACITY with a message.
  *   The first call on a device looks up the array's device address with
- *   that device current; make that first call before any stream capture.
+ *   that device current and keeps it for later calls; make that first call
+ *   before any stream capture.  The kept address does not survive
+ *   cudaDeviceReset (do not call this entry point after a reset).
  *   All calls share the array and it keeps the last call's contents (the
  *   work counters are cleared by each call before use): calls that overlap
  *   on the GPU, on any streams or trees, race and must be ordered. */

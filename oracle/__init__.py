@@ -71,6 +71,8 @@ def lib():
         L.orc_tree_export.argtypes = [vp] + [vp] * 6
         L.orc_tree_export_lists.argtypes = [vp] * 5
         L.orc_fmm_eval.argtypes = [vp, i, vp, vp, i64, vp, vp]
+        L.orc_fmm_eval_timed.argtypes = [vp, i, vp, vp, i64, vp, vp, vp]
+        L.orc_set_num_threads.argtypes = [i]
         L.orc_direct.argtypes = [vp, vp, i64, vp, i64, vp, vp]
         L.orc_direct_vjp.argtypes = [vp, vp, vp, i64, vp, vp]
         L.orc_tree2_build.argtypes = [vp, i64, vp, i64, i, i, d, i]
@@ -108,6 +110,11 @@ def idx(n, m):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(n):
+    """OpenMP threads of later oracle calls."""
+    lib().orc_set_num_threads(int(n))
 
 
 # ---- basis (App. A) ----
@@ -259,6 +266,19 @@ class Tree:
         lib().orc_fmm_eval(self._h, int(p), _p(q), _p(tg), 0 if tg is None else m,
                            _p(u), _p(f))
         return (u, f) if field else u
+
+
+    def eval_timed(self, q, p, targets):
+        """Potential at `targets` plus the stage wall times (seconds) and the
+        work of the stages restricted to the boxes feeding the targets:
+        dict(sort, p2m, m2m, m2l, l2l, eval, n_m2l_done, n_l2l_done, n_eval)."""
+        q = _f64(q)
+        tg = np.ascontiguousarray(targets, dtype=np.int64)
+        u = np.zeros(len(tg))
+        tm = np.zeros(9)
+        lib().orc_fmm_eval_timed(self._h, int(p), _p(q), _p(tg), len(tg), _p(u), None, _p(tm))
+        keys = ("sort", "p2m", "m2m", "m2l", "l2l", "eval", "n_m2l_done", "n_l2l_done", "n_eval")
+        return u, dict(zip(keys, tm.tolist()))
 
 
 class _Hierarchy:

@@ -10,10 +10,12 @@
  * distance contribute nothing (the self term, and coincident points).  The
  * field is -grad u.
  */
+#define _POSIX_C_SOURCE 199309L
 #include "fmm_oracle.h"
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -67,8 +69,24 @@ static int64_t first_ge(const int32_t* a, int64_t n, int32_t v) {
   return lo;
 }
 
-void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targets,
-                  int64_t n_targets, double* u, double* field) {
+/* Wall clock in seconds (stage timing of orc_fmm_eval_timed only). */
+static double wall_s(void) {
+#ifdef _OPENMP
+  return omp_get_wtime();
+#else
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+#endif
+}
+
+/* The evaluation of orc_fmm_eval; `timing` (nullable) receives the stage
+ * wall times and the work done by the stages that are restricted to the
+ * boxes feeding the evaluated points (see orc_fmm_eval_timed). */
+static void fmm_eval_run(const orc_tree* t, int p, const double* q, const int64_t* targets,
+                         int64_t n_targets, double* u, double* field, double* timing) {
+  double tick = wall_s();
+  int64_t done_m2l = 0, done_l2l = 0;
   const int64_t n = orc__n(t);
   const int L = orc__levels(t), s = orc__splits(t);
   const int64_t nch = (int64_t)1 << s;
@@ -110,6 +128,11 @@ void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targ
 
   double* C = (double*)calloc((size_t)nbox * P, sizeof(double));
   double* D = (double*)calloc((size_t)nbox * P, sizeof(double));
+  if (timing) {
+    double now = wall_s();
+    timing[0] = now - tick;
+    tick = now;
+  }
 
   /* mpls: P2M on every leaf */
 #pragma omp parallel for schedule(dynamic, 16)
@@ -119,6 +142,11 @@ void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targ
     memcpy(pts, X + 3 * bs[g], sizeof(double) * 3 * (size_t)bc[g]);
     orc_p2m(p, pts, qt + bs[g], bc[g], cen + 3 * g, C + (size_t)g * P);
     free(pts);
+  }
+  if (timing) {
+    double now = wall_s();
+    timing[1] = now - tick;
+    tick = now;
   }
   /* M2M: levels L-1 .. 0 */
   for (int l = L - 1; l >= 0; l--) {
@@ -133,27 +161,45 @@ void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targ
       }
     }
   }
+  if (timing) {
+    double now = wall_s();
+    timing[2] = now - tick;
+    tick = now;
+  }
   /* M2L over the whole list, grouped by target */
   const int64_t nm = orc__n_m2l(t);
   const int32_t* mt = orc__m2l_trg(t);
   const int32_t* ms = orc__m2l_src(t);
-#pragma omp parallel for schedule(dynamic, 8)
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : done_m2l)
   for (int64_t g = 0; g < nbox; g++) {
     if (!need[g]) continue;
-    for (int64_t k = first_ge(mt, nm, (int32_t)g); k < nm && mt[k] == g; k++)
+    for (int64_t k = first_ge(mt, nm, (int32_t)g); k < nm && mt[k] == g; k++) {
       orc_m2l(p, C + (size_t)ms[k] * P, cen + 3 * (int64_t)ms[k], cen + 3 * g, D + (size_t)g * P);
+      done_m2l++;
+    }
+  }
+  if (timing) {
+    double now = wall_s();
+    timing[3] = now - tick;
+    tick = now;
   }
   /* L2L: levels 1 .. L */
   for (int l = 1; l <= L; l++) {
     int64_t off = level_off(l, s), offp = level_off(l - 1, s);
     int64_t nb = (int64_t)1 << (s * l);
-#pragma omp parallel for schedule(dynamic, 16)
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : done_l2l)
     for (int64_t b = 0; b < nb; b++) {
       int64_t g = off + b;
       if (!need[g]) continue;
       int64_t gp = offp + b / nch;
       orc_l2l(p, D + (size_t)gp * P, cen + 3 * gp, cen + 3 * g, D + (size_t)g * P);
+      done_l2l++;
     }
+  }
+  if (timing) {
+    double now = wall_s();
+    timing[4] = now - tick;
+    tick = now;
   }
   /* evloc (L2P) and evdir (P2P) for every evaluated point */
   const int64_t np = orc__n_p2p(t);
@@ -191,12 +237,36 @@ void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targ
     if (field)
       for (int a = 0; a < 3; a++) field[3 * k + a] = (grad[a] + gn[a]) / FOUR_PI;
   }
+  if (timing) {
+    timing[5] = wall_s() - tick;
+    timing[6] = (double)done_m2l;
+    timing[7] = (double)done_l2l;
+    timing[8] = (double)n_eval;
+  }
   free(qt);
   free(inv);
   free(tpos);
   free(need);
   free(C);
   free(D);
+}
+
+void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targets,
+                  int64_t n_targets, double* u, double* field) {
+  fmm_eval_run(t, p, q, targets, n_targets, u, field, NULL);
+}
+
+void orc_fmm_eval_timed(const orc_tree* t, int p, const double* q, const int64_t* targets,
+                        int64_t n_targets, double* u, double* field, double* timing) {
+  fmm_eval_run(t, p, q, targets, n_targets, u, field, timing);
+}
+
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }
 
 /* Eq. 1-3 summed directly. */

@@ -88,6 +88,16 @@ void orc_tree2_export_lists(const orc_tree2* t2, int32_t* m2l_trg, int32_t* m2l_
  * written to u[k], field[3k..3k+2] for k = 0..n_targets-1. */
 void orc_fmm_eval(const orc_tree* t, int p, const double* q, const int64_t* targets,
                   int64_t n_targets, double* u, double* field);
+/* As orc_fmm_eval, also reporting the stage wall times in seconds:
+ * timing[0] sort and target bookkeeping, [1] P2M of every leaf, [2] M2M of
+ * every box, [3] M2L into the boxes that feed the evaluated points, [4] L2L
+ * into those boxes, [5] L2P + P2P at the evaluated points; and the work of
+ * the restricted stages: [6] M2L interactions done, [7] L2L translations
+ * done, [8] points evaluated.  (Measurement aid of the CPU baseline.) */
+void orc_fmm_eval_timed(const orc_tree* t, int p, const double* q, const int64_t* targets,
+                        int64_t n_targets, double* u, double* field, double* timing);
+/* Sets the number of OpenMP threads of later calls (no effect without OpenMP). */
+void orc_set_num_threads(int n);
 void orc_direct(const double* pos, const double* q, int64_t n, const int64_t* targets,
                 int64_t n_targets, double* u, double* field);
 /* Potential and field of the charges q at src_pos evaluated at n_trg target

@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -64,7 +65,7 @@ void free_tree(fmm_tree* t) {
                   t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr, t->sym_slot, t->sym_work_off,
                   t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec, t->src_df, t->sym_frame, t->src_dup2, t->near_u2, t->near_f2};
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) dev_free(p);
   if (t->prof_ev) {
     for (int i = 0; i < fmm_tree::kProfCalls * fmm_tree::kProfSlots * 2; i++) cudaEventDestroy(t->prof_ev[i]);
     delete[] t->prof_ev;
@@ -76,6 +77,49 @@ void free_tree(fmm_tree* t) {
   delete[] t->up_off_h;
   delete[] t->tree_point_off_h;
   delete t;
+}
+
+namespace {
+std::mutex g_mem_mu;
+std::unordered_map<void*, size_t> g_live;  // library allocation -> bytes
+size_t g_live_bytes = 0;
+size_t g_mem_limit = 0;  // 0: no cap
+}  // namespace
+
+void* tracked_malloc(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    if (g_mem_limit && g_live_bytes + bytes > g_mem_limit) {
+      set_error("device allocation of %zu bytes refused: the library holds %zu bytes and its limit is %zu "
+                "(fmm_set_device_memory_limit)",
+                bytes, g_live_bytes, g_mem_limit);
+      throw Fail{FMM_ERR_OOM};
+    }
+  }
+  void* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    throw Fail{FMM_ERR_OOM};
+  }
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  g_live[p] = bytes;
+  g_live_bytes += bytes;
+  return p;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    auto it = g_live.find(p);
+    if (it != g_live.end()) {
+      g_live_bytes -= it->second;
+      g_live.erase(it);
+    }
+  }
+  cudaFree(p);
 }
 
 void set_error(const char* fmt, ...) {
@@ -93,6 +137,31 @@ using namespace fmm;
 extern "C" {
 
 const char* fmm_last_error(void) { return fmm::last_error(); }
+
+int fmm_set_device_memory_limit(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  g_mem_limit = bytes;
+  return FMM_OK;
+}
+
+int fmm_device_memory_in_use(size_t* bytes) {
+  if (!bytes) {
+    set_error("invalid argument: bytes is NULL");
+    return FMM_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  *bytes = g_live_bytes;
+  return FMM_OK;
+}
+
+int fmm_tree_set_wait_limit(fmm_tree* tree, int64_t cycles) {
+  if (!tree || cycles < 0) {
+    set_error("invalid argument: %s", !tree ? "tree is NULL" : "cycles must be >= 0");
+    return FMM_ERR_INVALID_ARG;
+  }
+  tree->wait_cycles = (long long)cycles;
+  return FMM_OK;
+}
 
 int fmm_num_levels(int64_t n, int leaf_size, int splits) {
   if (n < 1 || splits < 1 || splits > 3 || leaf_size < (1 << splits)) return -1;

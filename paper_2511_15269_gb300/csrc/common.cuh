@@ -43,8 +43,12 @@ inline void require(bool ok, const char* what) {
 // Device status bits latched by kernels (read by fmm_tree_status).
 enum : int { ST_TIMEOUT = 1 };
 
-// Bounded waits: iterations of mbarrier.try_wait before giving up.
-constexpr long long kWaitLimit = 1ll << 26;
+// Bounded waits: clock cycles a near-field warp waits for a staged source
+// tile before it gives up and latches ST_TIMEOUT (about a second; settable
+// per tree with fmm_tree_set_wait_limit), and the limit of the waits that let
+// copies still in flight land before such a warp leaves.
+constexpr long long kDefaultWaitCycles = 2000000000ll;
+constexpr long long kDrainWaitCycles = 2000000000ll;
 
 // ---- sizes -----------------------------------------------------------------
 constexpr int kMaxP = FMM_MAX_P;
@@ -218,6 +222,7 @@ struct fmm_tree {
   double* g_stage = nullptr;     // 3 n (backward)
   int* counters = nullptr;       // work counters, reset before each launch
   int* status = nullptr;         // latched kernel status bits
+  long long wait_cycles = fmm::kDefaultWaitCycles;  // near-field tile wait limit
 
   // far-field stages run on a second, higher-priority stream forked from
   // and joined back into the caller's stream
@@ -290,15 +295,17 @@ int64_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t 
 void exclusive_scan_async(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
                           cudaStream_t st);
 
+// api.cu: every device allocation of the library goes through these two, so
+// that the bytes it holds are known and can be capped
+// (fmm_set_device_memory_limit): an allocation beyond the cap, or one that
+// cudaMalloc refuses, throws Fail{FMM_ERR_OOM}.
+void* tracked_malloc(size_t bytes);
+void dev_free(void* p);
+
 template <class T>
 T* dev_alloc(fmm_tree* t, size_t count) {
-  T* p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc(&p, sizeof(T) * count);
-  if (e != cudaSuccess) {
-    set_error("cudaMalloc of %zu bytes failed: %s", sizeof(T) * count, cudaGetErrorString(e));
-    throw Fail{FMM_ERR_OOM};
-  }
+  T* p = static_cast<T*>(tracked_malloc(sizeof(T) * count));
   if (t) t->device_bytes += sizeof(T) * count;
   return p;
 }

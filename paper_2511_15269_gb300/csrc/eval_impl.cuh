@@ -453,11 +453,13 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
-// Waits for phase `parity` of the barrier; gives up after about a second of
-// clock cycles and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for phase `parity` of the barrier; gives up and returns false once
+// `limit` clock cycles have passed (limit 0: gives up before the first
+// poll, which is how the timeout path is exercised without a fault).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   for (;;) {
+    if (clock64() - t0 >= limit) return false;
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -465,7 +467,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > 2000000000ll) return false;
   }
 }
 
@@ -687,6 +688,7 @@ struct P2PArgs {
   real* near_f;   // 3 per point (FIELD)
   int* counter;
   int* status;
+  long long wait_cycles;  // limit of a warp's wait for a staged tile (clock cycles)
 };
 
 template <int TPL, bool FIELD>
@@ -751,12 +753,12 @@ __global__ void __launch_bounds__(128) p2p_kernel(P2PArgs a) {
     for (int64_t e = eb; e < ee; e++) {
       const int buf = (int)((e - eb) & 1);
       if (e + 1 < ee) issue(e + 1, buf ^ 1);
-      const bool got = mbar_wait(&bar[buf], (phase >> buf) & 1u);
+      const bool got = mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles);
       if (!got) {
         if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
         // copies still in flight into this warp's buffers must land first
-        mbar_wait(&bar[buf], (phase >> buf) & 1u);
-        if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+        mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+        if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
         ok = false;
         break;
       }
@@ -897,11 +899,11 @@ __global__ void __launch_bounds__(128, (TPL <= 2 && !FIELD) ? 8 : ((TPL >= 8 || 
   for (int64_t e = eb; e < ee; e++) {
     const int buf = (int)((e - eb) & 1);
     if (e + 1 < ee) issue(e + 1, buf ^ 1);
-    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles)) {
       if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
       // copies still in flight into this warp's buffers must land first
-      mbar_wait(&bar[buf], (phase >> buf) & 1u);
-      if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+      if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
       return;
     }
     phase ^= 1u << buf;
@@ -1067,11 +1069,11 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 4 : 2) p2p_kernel_bwd(P2PArgs 
   for (int64_t e = eb; e < ee; e++) {
     const int buf = (int)((e - eb) & 1);
     if (e + 1 < ee) issue(e + 1, buf ^ 1);
-    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles)) {
       if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
       // copies still in flight into this warp's buffers must land first
-      mbar_wait(&bar[buf], (phase >> buf) & 1u);
-      if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+      if (e + 1 < ee) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
       return;
     }
     phase ^= 1u << buf;
@@ -1314,11 +1316,11 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
       const SymRec nx = ((w + 1) & 31) ? bcast((w + 1) & 31) : a.rec[kb + w + 1];
       issue(nx, buf ^ 1);
     }
-    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles)) {
       if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
       // copies still in flight into this warp's buffers must land first
-      mbar_wait(&bar[buf], (phase >> buf) & 1u);
-      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
       return;
     }
     phase ^= 1u << buf;
@@ -1519,11 +1521,11 @@ __global__ void __launch_bounds__(128) p2p_kernel_f64s(P2PArgs a) {
       const SymRec nx = ((w + 1) & 31) ? bcast((w + 1) & 31) : a.rec[kb + w + 1];
       issue(nx, buf ^ 1);
     }
-    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles)) {
       if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
       // copies still in flight into this warp's buffers must land first
-      mbar_wait(&bar[buf], (phase >> buf) & 1u);
-      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
       return;
     }
     phase ^= 1u << buf;
@@ -1774,11 +1776,11 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : 1) p2p_kernel_dfs(P2PArgs 
         tl[k][c] = (float)(d[c] - (double)h);
       }
     }
-    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u)) {
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles)) {
       if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
       // copies still in flight into this warp's buffers must land first
-      mbar_wait(&bar[buf], (phase >> buf) & 1u);
-      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u);
+      mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
       return;
     }
     phase ^= 1u << buf;
@@ -2210,6 +2212,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
   a.near_f = near_f;
   a.counter = t->counters + 1;
   a.status = t->status;
+  a.wait_cycles = t->wait_cycles;
   const size_t smem = (size_t)4 * 2 * TPL * 32 * 32;  // 32-byte records
   t->launches += 1;
   if constexpr (kF32) {
@@ -2474,6 +2477,7 @@ void run_p2p_bwd_tpl(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   a.near_u2 = t->near_u2;
   a.near_f2 = t->near_f2;
   a.status = t->status;
+  a.wait_cycles = t->wait_cycles;
   const size_t smem = (size_t)4 * 2 * 2 * TPL * 32 * 32;  // [warp][buf][q, g] 32-byte records
   static bool attr_set = false;
   if (!attr_set) {

@@ -246,7 +246,8 @@ __device__ __forceinline__ void axial_l2l(real (&v)[ncoef(P)], real a, real b) {
   });
 }
 
-// Normalised regular basis Rt(y) up to degree P (recursions in tables.cu),
+// Normalised regular basis Rt(y) up to degree P (the recursions in the
+// header comment above),
 // evaluated degree by degree; f(n, R) is called after degree n is complete so
 // that callers can consume it before older degrees die.
 template <int P, class F>

@@ -2,7 +2,7 @@
 literal constexpr arrays, so that fully unrolled kernels carry every entry as
 an instruction immediate.
 
-Formulas (see tables.cu for their derivation):
+Formulas (their derivation is in the header comment of expansion.cuh):
   quarter-turn Wigner elements d^n_{m,k}(pi/2) = 2^-n sqrt((n+m)!(n-m)!/((n+k)!(n-k)!))
       * sum_t (-1)^(m-k+t) C(n+k,t) C(n-k,n-m-t)   (exact integer sum),
   B = Y(-pi/2) Z(-pi/2), B^-1 = Z(pi/2) Y(pi/2) in the internal basis,

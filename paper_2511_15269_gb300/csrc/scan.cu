@@ -87,13 +87,13 @@ void scan_rec(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, int64
     add_tile_offsets<<<(unsigned)tiles, kScanThreads, 0, st>>>(out, n, sums);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(dummy);
+    dev_free(dummy);
   }
   write_total<<<1, 1, 0, st>>>(last_in, out + n - 1, total_dev);
   FMM_LAUNCH_CHECK();
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  cudaFree(sums);
-  cudaFree(last_in);
+  dev_free(sums);
+  dev_free(last_in);
 }
 
 }  // namespace
@@ -109,7 +109,7 @@ int64_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t 
   int64_t h = 0;
   FMM_CUDA_TRY(cudaMemcpyAsync(&h, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  cudaFree(tot);
+  dev_free(tot);
   return h;
 }
 

@@ -207,7 +207,7 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
                                                            t->center, t->sym_frame);
   FMM_LAUNCH_CHECK();
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  cudaFree(mirror), cudaFree(owns), cudaFree(n_work), cudaFree(n_recv);
+  dev_free(mirror), dev_free(owns), dev_free(n_work), dev_free(n_recv);
   t->sym_stride = std::max(t->max_leaf, 1);
   // slot sums in FP32 (FP32C path) or FP64 (FP64 path): room for doubles
   t->sym_partial = dev_alloc<double>(t, std::max<int64_t>(t->n_slots, 1) * t->sym_stride);

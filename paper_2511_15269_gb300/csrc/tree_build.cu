@@ -904,7 +904,7 @@ __global__ void point_records_kernel(const double* __restrict__ X, int64_t n, co
 
 template <class T>
 void dfree(T*& p) {
-  if (p) cudaFree(p);
+  if (p) dev_free(p);
   p = nullptr;
 }
 
@@ -945,7 +945,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
   if (hflag) {
-    cudaFree(Xa), cudaFree(Xb), cudaFree(Ia), cudaFree(Ib), cudaFree(flag);
+    dev_free(Xa), dev_free(Xb), dev_free(Ia), dev_free(Ib), dev_free(flag);
     require(false, "positions must be finite");
   }
   int has_dup = 0;
@@ -959,7 +959,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaMemcpyAsync(&has_dup, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(tab);
+    dev_free(tab);
   }
   t->has_duplicates = has_dup;
 
@@ -1019,7 +1019,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
       std::swap(Ia, Ib);
     }
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(bmin), cudaFree(bmax), cudaFree(ctr), cudaFree(hist), cudaFree(sel);
+    dev_free(bmin), dev_free(bmax), dev_free(ctr), dev_free(hist), dev_free(sel);
   }
 
   // ---- remaining rounds and the leaf sort, one CTA per segment ----
@@ -1104,7 +1104,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
       FMM_CUDA_TRY(cudaStreamSynchronize(st));
       t->level_avg_host[l] = sum / (double)((int64_t)1 << (s * l));
     }
-    cudaFree(buf0), cudaFree(buf1);
+    dev_free(buf0), dev_free(buf1);
   }
 
   // ---- point records and M2M edge coefficients ----
@@ -1122,8 +1122,8 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   t->device_bytes -= sizeof(double) * 6 * NB;  // bounding boxes leave with the caller
   *blo_out = blo;
   *bhi_out = bhi;
-  cudaFree(starts);
-  cudaFree(Xa), cudaFree(Xb), cudaFree(Ia), cudaFree(Ib), cudaFree(flag);
+  dev_free(starts);
+  dev_free(Xa), dev_free(Xb), dev_free(Ia), dev_free(Ib), dev_free(flag);
 }
 
 // One side of the list construction: the combined id of the side's root and
@@ -1173,11 +1173,11 @@ void march(const fmm_tree* t, Side S, Side T, cudaStream_t st, std::vector<Step>
     emit_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, fws, pws, pkeep, stp.t, stp.s, kt, ks);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(fws), cudaFree(fkeep), cudaFree(pws), cudaFree(pkeep), cudaFree(ct), cudaFree(cs);
+    dev_free(fws), dev_free(fkeep), dev_free(pws), dev_free(pkeep), dev_free(ct), dev_free(cs);
     if (nws > 0) steps.push_back(stp);
-    else cudaFree(stp.t), cudaFree(stp.s);
+    else dev_free(stp.t), dev_free(stp.s);
     if (nkeep == 0) {
-      cudaFree(kt), cudaFree(ks);
+      dev_free(kt), dev_free(ks);
       ct = cs = nullptr;
       break;
     }
@@ -1204,7 +1204,7 @@ void march(const fmm_tree* t, Side S, Side T, cudaStream_t st, std::vector<Step>
     expand_kernel<<<grid_for(nkeep, 256), 256, 0, st>>>(kt, ks, nkeep, nch, adv, ct, cs);
     FMM_LAUNCH_CHECK();
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(kt), cudaFree(ks);
+    dev_free(kt), dev_free(ks);
     if (adv != 0) ls++;
     if (adv != 1) lt++;
   }
@@ -1248,8 +1248,8 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
       FMM_LAUNCH_CHECK();
     }
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(cnt), cudaFree(fill);
-    for (auto& x : steps) cudaFree(x.t), cudaFree(x.s);
+    dev_free(cnt), dev_free(fill);
+    for (auto& x : steps) dev_free(x.t), dev_free(x.s);
     steps.clear();
   }
 
@@ -1271,8 +1271,8 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
     }
     exclusive_scan(cnt, t->p2p_off, NL + 1, st);
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(cnt);
-    if (p2p_t) cudaFree(p2p_t), cudaFree(p2p_s);
+    dev_free(cnt);
+    if (p2p_t) dev_free(p2p_t), dev_free(p2p_s);
   }
 
   // ---- rotation coefficients and near-field entries ----
@@ -1297,9 +1297,9 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
     FMM_CUDA_TRY(cudaMemcpyAsync(&hp, pairs, sizeof(hp), cudaMemcpyDeviceToHost, st));
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
     t->n_p2p_pairs = (int64_t)hp;
-    cudaFree(pairs);
+    dev_free(pairs);
   }
-  cudaFree(p2p_trg);
+  dev_free(p2p_trg);
 
   // ---- work orders: longest M2L lists and heaviest near fields first ----
   {
@@ -1431,7 +1431,7 @@ void build_l2l_direct(fmm_tree* t, cudaStream_t st) {
   }
   t->l2d_off = dev_alloc<int64_t>(t, NL + 1);
   const int64_t nr = exclusive_scan(cnt, t->l2d_off, NL + 1, st);
-  cudaFree(cnt);
+  dev_free(cnt);
   t->n_l2d = nr;
   t->l2d_anc = dev_alloc<int32_t>(t, std::max<int64_t>(nr, 1));
   t->l2d64 = dev_alloc<double>(t, (size_t)edge_fields(p) * std::max<int64_t>(nr, 1));
@@ -1461,10 +1461,10 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     finish_tree(t, steps, p2p_t, p2p_s, np, leaf_off, leaf_off, blo, bhi, t->has_duplicates, st);
     build_symmetric(t, st);
   } catch (...) {
-    cudaFree(blo), cudaFree(bhi);
+    dev_free(blo), dev_free(bhi);
     throw;
   }
-  cudaFree(blo), cudaFree(bhi);
+  dev_free(blo), dev_free(bhi);
 }
 
 // Two hierarchies (Sec. II.B, final part): the source tree's boxes come first
@@ -1477,7 +1477,7 @@ void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg,
   fmm_tree* T = new fmm_tree();
   double *blo_s = nullptr, *bhi_s = nullptr, *blo_t = nullptr, *bhi_t = nullptr;
   auto cleanup = [&] {
-    cudaFree(blo_s), cudaFree(bhi_s), cudaFree(blo_t), cudaFree(bhi_t);
+    dev_free(blo_s), dev_free(bhi_s), dev_free(blo_t), dev_free(bhi_t);
     S->src_leaf_box = T->src_leaf_box = nullptr;
     free_tree(S);
     free_tree(T);
@@ -1577,7 +1577,7 @@ void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg,
       FMM_LAUNCH_CHECK();
       FMM_CUDA_TRY(cudaMemcpyAsync(&has_dup, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
       FMM_CUDA_TRY(cudaStreamSynchronize(st));
-      cudaFree(X), cudaFree(tab), cudaFree(flag);
+      dev_free(X), dev_free(tab), dev_free(flag);
     }
     m->has_duplicates = has_dup;
     double* blo = scratch_alloc<double>(3 * (size_t)NB);
@@ -1596,10 +1596,10 @@ void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg,
       finish_tree(m, steps, p2p_t, p2p_s, np, NBs + level_offset(T->L, s), level_offset(S->L, s), blo, bhi,
                   has_dup, st);
     } catch (...) {
-      cudaFree(blo), cudaFree(bhi);
+      dev_free(blo), dev_free(bhi);
       throw;
     }
-    cudaFree(blo), cudaFree(bhi);
+    dev_free(blo), dev_free(bhi);
   } catch (...) {
     cleanup();
     throw;

@@ -21,10 +21,12 @@ FMM_SAME_LEVEL = 2
 FMM_MAX_P = 10
 
 # exported entry points, in include/fmm.h order
-ENTRY_POINTS = ["fmm_device_peaks", "fmm_last_error", "fmm_num_levels", "fmm_build_tree", "fmm_build_tree2", "fmm_tree_free",
+ENTRY_POINTS = ["fmm_device_peaks", "fmm_last_error", "fmm_set_device_memory_limit", "fmm_device_memory_in_use",
+                "fmm_num_levels", "fmm_build_tree", "fmm_build_tree2", "fmm_tree_free",
                 "fmm_tree_merge",
                 "fmm_tree_point_offsets",
-                "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_export",
+                "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_set_wait_limit",
+                "fmm_tree_export",
                 "fmm_tree_profile", "fmm_tree_stage_times", "fmm_eval_potential", "fmm_eval_field",
                 "fmm_eval_potential_host", "fmm_eval_potential_static", "fmm_backward"]
 STAGES = ["sort", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p"]
@@ -66,6 +68,9 @@ def lib():
         vp, i64, i = C.c_void_p, C.c_int64, C.c_int
         L.fmm_last_error.restype = C.c_char_p
         L.fmm_device_peaks.argtypes = [vp, vp]
+        L.fmm_set_device_memory_limit.argtypes = [C.c_size_t]
+        L.fmm_device_memory_in_use.argtypes = [C.POINTER(C.c_size_t)]
+        L.fmm_tree_set_wait_limit.argtypes = [vp, i64]
         L.fmm_num_levels.argtypes = [i64, i, i]
         L.fmm_num_levels.restype = i
         L.fmm_build_tree.argtypes = [vp, i64, C.POINTER(fmm_params), vp, C.POINTER(vp)]
@@ -101,9 +106,17 @@ def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _dev(t, shape_last=None):
+def _dev(t, numel=None, what="tensor"):
+    """Device pointer of a contiguous float64 tensor on the current CUDA
+    device; `numel` (if given) is the number of doubles the library reads or
+    writes through it, checked here because the kernels cannot."""
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise TypeError("expected a contiguous float64 CUDA tensor")
+        raise TypeError("%s: expected a contiguous float64 CUDA tensor" % what)
+    if t.device.index != torch.cuda.current_device():
+        raise FmmError(FMM_ERR_INVALID_ARG, "%s is on cuda:%d, the current device is cuda:%d"
+                       % (what, t.device.index, torch.cuda.current_device()))
+    if numel is not None and t.numel() != numel:
+        raise FmmError(FMM_ERR_INVALID_ARG, "%s has %d entries, the tree needs %d" % (what, t.numel(), numel))
     return C.c_void_p(t.data_ptr())
 
 
@@ -118,6 +131,17 @@ def fmm_device_peaks():
 
 def fmm_last_error():
     return lib().fmm_last_error().decode(errors="replace")
+
+
+def fmm_set_device_memory_limit(nbytes):
+    """Caps the device memory the library holds (0: no cap)."""
+    _check(lib().fmm_set_device_memory_limit(int(nbytes)))
+
+
+def fmm_device_memory_in_use():
+    v = C.c_size_t()
+    _check(lib().fmm_device_memory_in_use(C.byref(v)))
+    return v.value
 
 
 def fmm_num_levels(n, leaf_size, splits=2):
@@ -164,7 +188,7 @@ def fmm_build_tree(pos, p, leaf_size, splits=2, theta=0.5, precision=FMM_FP32C, 
     n = pos.shape[0]
     prm = fmm_params(int(p), int(leaf_size), int(splits), float(theta), int(precision), int(flags))
     h = C.c_void_p()
-    _check(lib().fmm_build_tree(_dev(pos), n, C.byref(prm), _stream(), C.byref(h)))
+    _check(lib().fmm_build_tree(_dev(pos, 3 * n, "pos"), n, C.byref(prm), _stream(), C.byref(h)))
     return Tree(h, n, prm)
 
 
@@ -175,7 +199,8 @@ def fmm_build_tree2(src_pos, trg_pos, p, leaf_size, splits=2, theta=0.5, precisi
     ns, nt = src_pos.shape[0], trg_pos.shape[0]
     prm = fmm_params(int(p), int(leaf_size), int(splits), float(theta), int(precision), int(flags))
     h = C.c_void_p()
-    _check(lib().fmm_build_tree2(_dev(src_pos), ns, _dev(trg_pos), nt, C.byref(prm), _stream(), C.byref(h)))
+    _check(lib().fmm_build_tree2(_dev(src_pos, 3 * ns, "src_pos"), ns, _dev(trg_pos, 3 * nt, "trg_pos"), nt,
+                                 C.byref(prm), _stream(), C.byref(h)))
     return Tree(h, ns + nt, prm, n_charges=ns, n_out=nt)
 
 
@@ -215,6 +240,11 @@ def fmm_tree_status(tree):
     _check(lib().fmm_tree_status(tree.handle, _stream()))
 
 
+def fmm_tree_set_wait_limit(tree, cycles):
+    """Cycle limit of the near-field kernels' bounded waits (0: give up at once)."""
+    _check(lib().fmm_tree_set_wait_limit(tree.handle, int(cycles)))
+
+
 def fmm_tree_export(tree):
     """Host copies of the hierarchy (numpy arrays)."""
     import numpy as np
@@ -247,15 +277,17 @@ def fmm_tree_stage_times(tree):
 
 def fmm_eval_potential(tree, q, out=None):
     u = out if out is not None else torch.empty(tree.n_out, dtype=torch.float64, device=q.device)
-    _check(lib().fmm_eval_potential(tree.handle, _dev(q), _dev(u), _stream()))
+    _check(lib().fmm_eval_potential(tree.handle, _dev(q, tree.n_charges, "q"), _dev(u, tree.n_out, "u"),
+                                    _stream()))
     return u
 
 
 def fmm_eval_field(tree, q, potential=True):
     f = torch.empty((tree.n_out, 3), dtype=torch.float64, device=q.device)
     u = torch.empty(tree.n_out, dtype=torch.float64, device=q.device) if potential else None
-    _check(lib().fmm_eval_field(tree.handle, _dev(q), _dev(u) if u is not None else None, _dev(f),
-                                _stream()))
+    _check(lib().fmm_eval_field(tree.handle, _dev(q, tree.n_charges, "q"),
+                                _dev(u, tree.n_out, "u") if u is not None else None,
+                                _dev(f, 3 * tree.n_out, "field"), _stream()))
     return (u, f) if potential else f
 
 
@@ -263,7 +295,9 @@ def fmm_eval_potential_host(tree, q_host, u_host=None):
     """Host-buffer evaluation: q_host, u_host are float64 CPU tensors (pinned is fastest)."""
     if u_host is None:
         u_host = torch.empty(tree.n_out, dtype=torch.float64, pin_memory=True)
-    assert q_host.dtype == torch.float64 and not q_host.is_cuda and q_host.is_contiguous()
+    for t, n, what in ((q_host, tree.n_charges, "q_host"), (u_host, tree.n_out, "u_host")):
+        if t.dtype != torch.float64 or t.is_cuda or not t.is_contiguous() or t.numel() != n:
+            raise FmmError(FMM_ERR_INVALID_ARG, "%s: expected %d contiguous float64 host values" % (what, n))
     _check(lib().fmm_eval_potential_host(tree.handle, C.c_void_p(q_host.data_ptr()),
                                          C.c_void_p(u_host.data_ptr()), _stream()))
     return u_host
@@ -274,16 +308,16 @@ def fmm_eval_potential_static(tree, q, out=None):
     per-call scratch is the library's static device array (see fmm.h).
     `out` lets the caller pass a preallocated output."""
     u = out if out is not None else torch.empty(tree.n, dtype=torch.float64, device=q.device)
-    _check(lib().fmm_eval_potential_static(tree.handle, _dev(q), _dev(u), _stream()))
+    _check(lib().fmm_eval_potential_static(tree.handle, _dev(q, tree.n, "q"), _dev(u, tree.n, "u"), _stream()))
     return u
 
 
 def fmm_backward(tree, q, grad_u, need_q=True, need_pos=True):
     gq = torch.empty(tree.n, dtype=torch.float64, device=q.device) if need_q else None
     gp = torch.empty((tree.n, 3), dtype=torch.float64, device=q.device) if need_pos else None
-    _check(lib().fmm_backward(tree.handle, _dev(q), _dev(grad_u.contiguous()),
-                              _dev(gq) if gq is not None else None,
-                              _dev(gp) if gp is not None else None, _stream()))
+    _check(lib().fmm_backward(tree.handle, _dev(q, tree.n, "q"), _dev(grad_u.contiguous(), tree.n, "grad_u"),
+                              _dev(gq, tree.n, "grad_q") if gq is not None else None,
+                              _dev(gp, 3 * tree.n, "grad_pos") if gp is not None else None, _stream()))
     return gq, gp
 
 

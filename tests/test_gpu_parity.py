@@ -15,12 +15,23 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-# FP32 budget: unit roundoff 6e-8, about ten rounded operations deep per
-# translation chain plus FP32 position offsets; fields lose one more digit.
+# FP32C budget against the FP64 oracle FMM (same tree, same p): the unit
+# roundoff u = 2^-24 = 6e-8 enters (i) the near field through FP32 offsets
+# from the leaf centres (a pair at distance r in a leaf of radius R carries
+# about 2u R / r) with compensated sums, and (ii) the far field through
+# about ten rounded operations per coefficient and translation along an
+# M2M - M2L - L2L chain whose depth grows with the level count L, in a basis
+# scaled by the box radii so that no coefficient over- or underflows.  A
+# random-walk estimate u sqrt(10 (2L + 1)) gives 1.2e-6 at L = 8, the errors
+# of different coefficients partly cancel in the potential (measured 1e-7 to
+# 3e-7), so the bars below sit at 3-10x the measured errors: 1e-6 for trees
+# up to L = 7, 2e-6 for the depth-8 Plummer tree.  Fields are one derivative
+# of the same sums (about one more digit).
 TOL_FP64 = 1e-12
 TOL_FP64_FIELD = 1e-11
-TOL_FP32 = 3e-6
-TOL_FP32_FIELD = 3e-5
+TOL_FP32 = 1e-6
+TOL_FP32_FIELD = 1e-5
+TOL_FP32_CFG = {"cube4k_p4": 5e-7, "cube1m_p8": 1e-6, "plummer4m_p10": 2e-6}
 
 
 @pytest.fixture(scope="module")
@@ -63,8 +74,8 @@ def assert_same_tree(F, T, O):
     np.testing.assert_array_equal(ex["m2l_src"], O.m2l_src)
     np.testing.assert_array_equal(ex["p2p_trg"], O.p2p_trg)
     np.testing.assert_array_equal(ex["p2p_src"], O.p2p_src)
-    pairs = sum(int(O.box_count[O.level_offset(O.L) + t]) * int(O.box_count[O.level_offset(O.L) + s])
-                for t, s in zip(O.p2p_trg, O.p2p_src))
+    leaf_counts = O.box_count[O.level_offset(O.L):].astype(np.int64)
+    pairs = int(np.sum(leaf_counts[O.p2p_trg] * leaf_counts[O.p2p_src]))
     assert st["n_p2p_pairs"] == pairs
 
 
@@ -137,7 +148,7 @@ def test_potential_parity(F, orc, name, mk, p, leaf, s, theta):
     F.fmm_tree_status(T)
     print("%s: fp64 vs oracle %.3e, fp32c vs oracle %.3e" % (name, e64, e32))
     assert e64 <= TOL_FP64
-    assert e32 <= TOL_FP32
+    assert e32 <= TOL_FP32_CFG.get(name, TOL_FP32)
 
 
 def test_same_level_potential_parity(F, orc):
@@ -288,42 +299,53 @@ def test_cube1m_p8_full_size(F, orc):
     u64 = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()[tg]
     uo = O.eval(q, c["p"], targets=tg)
     F.fmm_tree_status(T)
-    print("cube1m: fp32c vs direct %.3e, fp64 vs direct %.3e, fp64 vs oracle fmm %.3e"
-          % (rel_l2(u32, ud), rel_l2(u64, ud), rel_l2(u64, uo)))
+    print("cube1m: fp32c vs direct %.3e, fp64 vs direct %.3e, fp64 vs oracle fmm %.3e, fp32c vs oracle fmm %.3e"
+          % (rel_l2(u32, ud), rel_l2(u64, ud), rel_l2(u64, uo), rel_l2(u32, uo)))
     assert rel_l2(u64, uo) <= TOL_FP64
+    assert rel_l2(u32, uo) <= TOL_FP32_CFG["cube1m_p8"]
     assert rel_l2(u32, ud) <= 1e-6
+
+
+def leaf_targets(O, n_leaves, seed):
+    """Every point of `n_leaves` random leaves of the oracle tree (original
+    indices, sorted): the oracle FMM then needs M2L and L2L only for those
+    leaves and their ancestors."""
+    rng = np.random.default_rng(seed)
+    off = O.level_offset(O.L)
+    leaves = rng.choice(O.n_leaves, n_leaves, replace=False)
+    tg = np.concatenate([O.perm[O.box_start[off + l]:O.box_start[off + l] + O.box_count[off + l]] for l in leaves])
+    return np.sort(tg.astype(np.int64))
 
 
 def test_plummer4m_p10_full_size(F, orc):
     """Highly non-uniform N = 2^22 (70% Plummer + 30% sphere surface), p = 10,
-    leaf 64, theta 0.5, in the launch configuration the benchmark times: the
-    balanced box counts of the median split, and FP32C, FP64 and FP64DF
-    potentials against the FP64 direct sum on sampled targets (the FMM
-    truncation at theta 0.5 bounds the error near 1.4e-6)."""
+    leaf 64, theta 0.5, depth 8, in the launch configuration the benchmark
+    times: the hierarchy bit for bit against the oracle, and FP64, FP64DF and
+    FP32C potentials against the oracle FMM at every point of 12 random leaves
+    (the deepest tree the benchmark evaluates, where the FP32 radius scaling
+    is stressed most), plus FP32C against the FP64 direct sum."""
     c = workloads.CONFIGS["plummer4m_p10"]
     pos, q = workloads.plummer_sphere(c["n"], seed=0)
-    T = F.fmm_build_tree(cuda(pos), c["p"], c["leaf_size"], c["s"], c["theta"], F.FMM_FP32C)
-    st = F.fmm_tree_stats(T)
-    L, s = st["levels"], c["s"]
-    assert L == orc.num_levels(c["n"], c["leaf_size"], s)
-    counts = F.fmm_tree_export(T)["box_count"]
-    off = 0
-    for l in range(L + 1):
-        nb = 1 << (s * l)
-        lv = counts[off:off + nb]
-        assert lv.sum() == c["n"] and lv.max() - lv.min() <= 1  # ceil / floor of N / 4^l
-        off += nb
-    tg = workloads.sample_targets(c["n"], 1024, seed=1)
+    T, O = build_both(F, orc, pos, c["p"], c["leaf_size"], c["s"], c["theta"], F.FMM_FP32C)
+    assert O.L == 8
+    assert_same_tree(F, T, O)
+    tg = leaf_targets(O, 12, seed=1)
+    uo = O.eval(q, c["p"], targets=tg)
     ud = orc.direct(pos, q, targets=tg)
     qd = cuda(q)
     errs = {}
     for name, prec in (("fp32c", F.FMM_FP32C), ("fp64", F.FMM_FP64), ("fp64df", F.FMM_FP64DF)):
         F.fmm_tree_set_precision(T, prec)
-        errs[name] = rel_l2(F.fmm_eval_potential(T, qd).cpu().numpy()[tg], ud)
+        errs[name] = rel_l2(F.fmm_eval_potential(T, qd).cpu().numpy()[tg], uo)
+    F.fmm_tree_set_precision(T, F.FMM_FP32C)
+    e32d = rel_l2(F.fmm_eval_potential(T, qd).cpu().numpy()[tg], ud)
     F.fmm_tree_status(T)
-    print("plummer4m:", {k: "%.3e" % v for k, v in errs.items()})
-    assert all(v < 3e-6 for v in errs.values())
-    assert abs(errs["fp64df"] - errs["fp64"]) < 1e-9
+    print("plummer4m vs oracle fmm (%d targets):" % len(tg), {k: "%.3e" % v for k, v in errs.items()},
+          "fp32c vs direct %.3e, oracle fmm vs direct %.3e" % (e32d, rel_l2(uo, ud)))
+    assert errs["fp64"] <= TOL_FP64
+    assert errs["fp64df"] <= 2e-13
+    assert errs["fp32c"] <= TOL_FP32_CFG["plummer4m_p10"]
+    assert e32d <= 3e-6  # truncation (about 1.4e-6 at theta 0.5) plus the FP32 budget
 
 
 def test_batched64_p6_full_size(F, orc):
