@@ -223,11 +223,16 @@ int fmm_tree_merge(fmm_tree* const* trees, int n_trees, void* stream, fmm_tree**
 int fmm_tree_point_offsets(const fmm_tree* tree, int64_t* offsets);
 
 /* Selects the precision of later evaluation calls (FMM_FP64, FMM_FP32C or
- * FMM_FP64DF).  The first selection of FMM_FP64DF for a tree of one point set
- * (or a tree built or merged with it) allocates the low parts of the M2L
- * rotation records (4 m2l_fields(p) = 12 + 16 p bytes per interaction) and a
- * double-float multipole buffer, synchronously on the default stream.
- * Errors: FMM_ERR_INVALID_ARG, FMM_ERR_OOM, FMM_ERR_CUDA. */
+ * FMM_FP64DF).  A tree keeps only the data of the precisions selected so
+ * far: the first selection of FMM_FP64 or FMM_FP64DF (at build or here)
+ * computes the FP64 rotation records of every M2L, M2M and direct L2L
+ * translation (4 m2l_fields(p) = 12 + 16 p more bytes per M2L interaction
+ * than FP32C alone), FP64 expansion and point buffers and double-width
+ * near-field slots; the first selection of FMM_FP64DF for a tree of one point
+ * set (or a tree built or merged with it) also makes the low parts of the M2L
+ * rotation records, a double-float multipole buffer and the double-float
+ * near-field records.  These calls allocate and run synchronously on the
+ * default stream.  Errors: FMM_ERR_INVALID_ARG, FMM_ERR_OOM, FMM_ERR_CUDA. */
 int fmm_tree_set_precision(fmm_tree* tree, int precision);
 
 /* Fills *stats (host pointer). */

@@ -77,14 +77,73 @@ void free_tree(fmm_tree* t) {
   delete[] t->up_off_h;
   delete[] t->tree_point_off_h;
   delete t;
+  trim_pool();
 }
 
 namespace {
+struct LiveAlloc {
+  size_t bytes;
+  bool pooled;  // from the library's stream-ordered pool (cudaMallocFromPoolAsync)
+};
 std::mutex g_mem_mu;
-std::unordered_map<void*, size_t> g_live;  // library allocation -> bytes
+std::unordered_map<void*, LiveAlloc> g_live;  // library allocation -> size, origin
 size_t g_live_bytes = 0;
 size_t g_mem_limit = 0;  // 0: no cap
+cudaMemPool_t g_pool[64] = {};
+
+// The library's memory pool on the current device, created on first use;
+// it keeps freed memory for reuse until the end of the build that freed it
+// (AllocScope trims it then), so the many short-lived scratch buffers of a
+// build cost neither cudaMalloc nor an implicit synchronisation of cudaFree.
+cudaMemPool_t pool_for_device() {
+  int dev = 0;
+  FMM_CUDA_TRY(cudaGetDevice(&dev));
+  require(dev >= 0 && dev < 64, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    FMM_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = UINT64_MAX;
+    FMM_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
 }  // namespace
+
+void trim_pool() {
+  if (tl_alloc_pool) return;  // inside a build: its scope trims at the end
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    pool = g_pool[dev];
+  }
+  if (pool) {
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
+  }
+}
+
+AllocScope::AllocScope(cudaStream_t s)
+    : prev(tl_alloc_stream), prev_pool(tl_alloc_pool), pool(pool_for_device()) {
+  tl_alloc_stream = s;
+  tl_alloc_pool = pool;
+}
+AllocScope::~AllocScope() {
+  tl_alloc_stream = prev;
+  tl_alloc_pool = prev_pool;
+  if (!prev_pool) {
+    // the outermost scope gives the memory freed during the build back
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
+  }
+}
 
 void* tracked_malloc(size_t bytes) {
   {
@@ -97,29 +156,36 @@ void* tracked_malloc(size_t bytes) {
     }
   }
   void* p = nullptr;
-  const cudaError_t e = cudaMalloc(&p, bytes);
+  const bool pooled = tl_alloc_pool != nullptr;
+  const cudaError_t e = pooled ? cudaMallocFromPoolAsync(&p, bytes, tl_alloc_pool, tl_alloc_stream)
+                               : cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
-    cudaGetLastError();  // clear the sticky-free allocation error
-    set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    cudaGetLastError();  // clear the allocation error
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     throw Fail{FMM_ERR_OOM};
   }
   std::lock_guard<std::mutex> lk(g_mem_mu);
-  g_live[p] = bytes;
+  g_live[p] = LiveAlloc{bytes, pooled};
   g_live_bytes += bytes;
   return p;
 }
 
 void dev_free(void* p) {
   if (!p) return;
+  bool pooled = false;
   {
     std::lock_guard<std::mutex> lk(g_mem_mu);
     auto it = g_live.find(p);
     if (it != g_live.end()) {
-      g_live_bytes -= it->second;
+      g_live_bytes -= it->second.bytes;
+      pooled = it->second.pooled;
       g_live.erase(it);
     }
   }
-  cudaFree(p);
+  // stream-ordered inside a build (the memory is reused once the work queued
+  // before the free has run); otherwise after the device is idle
+  if (pooled) cudaFreeAsync(p, tl_alloc_pool ? tl_alloc_stream : nullptr);
+  else cudaFree(p);
 }
 
 void set_error(const char* fmt, ...) {
@@ -190,12 +256,16 @@ int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void*
             "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
     require((p.flags & ~(FMM_TIE_TARGET | FMM_SAME_LEVEL)) == 0, "unknown flags");
     auto t0 = std::chrono::steady_clock::now();
+    TraceScope trace((cudaStream_t)stream);
+    AllocScope scratch((cudaStream_t)stream);
     ensure_tables();
     t = new fmm_tree();
     t->prm = p;
     t->n = n;
     t->L = fmm_num_levels(n, p.leaf_size, p.splits);
+    trace_mark("set-up");
     build_tree(t, pos, (cudaStream_t)stream);
+    if (p.precision != FMM_FP32C) ensure_fp64(t, (cudaStream_t)stream);
     if (p.precision == FMM_FP64DF) prepare_df_far(t, (cudaStream_t)stream);
     t->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   });
@@ -225,10 +295,13 @@ int fmm_build_tree2(const double* src_pos, int64_t n_src, const double* trg_pos,
             "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
     require((p.flags & ~FMM_TIE_TARGET) == 0, "flags must be 0 or FMM_TIE_TARGET for two hierarchies");
     auto t0 = std::chrono::steady_clock::now();
+    TraceScope trace((cudaStream_t)stream);
+    AllocScope scratch((cudaStream_t)stream);
     ensure_tables();
     t = new fmm_tree();
     t->prm = p;
     build_tree2(t, src_pos, n_src, trg_pos, n_trg, (cudaStream_t)stream);
+    if (p.precision != FMM_FP32C) ensure_fp64(t, (cudaStream_t)stream);
     t->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   });
   if (rc != FMM_OK) {
@@ -250,8 +323,10 @@ int fmm_tree_merge(fmm_tree* const* trees, int n_trees, void* stream, fmm_tree**
     for (int k = 0; k < n_trees; k++)
       require(trees[k] == nullptr || !trees[k]->two_trees, "trees with separate source and target sets cannot be merged");
     auto t0 = std::chrono::steady_clock::now();
+    AllocScope scratch((cudaStream_t)stream);
     m = new fmm_tree();
     merge_trees(trees, n_trees, (cudaStream_t)stream, m);
+    if (m->prm.precision != FMM_FP32C) ensure_fp64(m, (cudaStream_t)stream);
     if (m->prm.precision == FMM_FP64DF) prepare_df_far(m, (cudaStream_t)stream);
     m->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   });
@@ -280,6 +355,9 @@ int fmm_tree_set_precision(fmm_tree* tree, int precision) {
     require(tree != nullptr, "tree is NULL");
     require(precision == FMM_FP64 || precision == FMM_FP32C || precision == FMM_FP64DF,
             "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
+    // FP64 rotation records, expansions and wide slots are made on the first
+    // FP64 or FP64DF selection (on the legacy default stream, synchronously)
+    if (precision != FMM_FP32C) ensure_fp64(tree, 0);
     if (precision == FMM_FP64DF) prepare_df_far(tree, 0);
     tree->prm.precision = precision;
   });

@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <string>
 
 #include "../../include/fmm.h"
@@ -60,11 +62,12 @@ __host__ __device__ constexpr int ncoef(int p) { return (p + 1) * (p + 1); }
 __host__ __device__ constexpr int ncoef_pad(int p) { return (ncoef(p) + 3) & ~3; }
 
 // Per-interaction geometry fields (structure of arrays, field-major):
-//   M2L: [0] 1/r  [1] rho_S/r  [2] rho_T/r  then cos(m phi), sin(m phi),
-//        cos(m theta), sin(m theta) for m = 1..p
+//   M2L: [0] 1/r  [1] rho_S/r  [2] rho_T/r  [3] cos phi  [4] sin phi
+//        [5] cos theta  [6] sin theta  (the M2L kernels make the multiples
+//        m phi, m theta, m = 2..p, by angle addition in their own precision)
 //   edges (per child box, M2M and L2L each): [0] r/rho_P  [1] rho_C/rho_P
-//        then the same 4p trigonometric rows
-__host__ __device__ constexpr int m2l_fields(int p) { return 3 + 4 * p; }
+//        then cos(m phi), sin(m phi), cos(m theta), sin(m theta) for m = 1..p
+__host__ __device__ constexpr int m2l_fields(int /*p*/) { return 7; }
 __host__ __device__ constexpr int edge_fields(int p) { return 2 + 4 * p; }
 
 // Near-field entry for the FP32 path: source leaf (bit 31 set when the tree
@@ -148,7 +151,9 @@ struct fmm_tree {
   int64_t* sym_work_off = nullptr;    // n_leaves + 1
   int32_t* sym_work = nullptr;        // entries each leaf's warp evaluates, list order
   int64_t* sym_recv_off = nullptr;    // n_leaves + 1: the slots each leaf receives (contiguous)
-  double* sym_partial = nullptr;      // n_slots x sym_stride (read as float by the FP32C path)
+  double* sym_partial = nullptr;      // n_slots x sym_stride floats (FP32C), doubles once
+                                      // sym_partial_f64 is set (an FP64 precision was selected)
+  int sym_partial_f64 = 0;
   fmm::SymRec* sym_rec = nullptr;     // per work entry, in work-list order
   // FP64DF near field: per-point double-float records (coordinates set at
   // build, charges by every evaluation's gather) and the source frame of
@@ -263,9 +268,16 @@ void build_symmetric(fmm_tree* t, cudaStream_t st);
 // tree_build.cu: the direct L2L records of a tree with lists, geometry and
 // parents in place
 void build_l2l_direct(fmm_tree* t, cudaStream_t st);
+// tree_build.cu: the FP64 data of a tree (FP64 rotation records, FP64
+// expansions and point records, double-width near-field slots), made the
+// first time a tree's precision is FMM_FP64 or FMM_FP64DF; synchronous
+void ensure_fp64(fmm_tree* t, cudaStream_t st);
 // tree_build.cu: the low parts of the rotation records and the double-float
-// multipole buffer of the FP64DF far field (once per tree)
+// multipole buffer of the FP64DF far field, and (symmetric.cu,
+// build_df_near) the double-float point records and per-entry source frames
+// of its near field (once per tree)
 void prepare_df_far(fmm_tree* t, cudaStream_t st);
+void build_df_near(fmm_tree* t, cudaStream_t st);
 // api.cu: releases every device array, stream and event of a tree
 void free_tree(fmm_tree* t);
 // merge.cu: a batch of trees as one tree-shaped object
@@ -289,6 +301,13 @@ __host__ __device__ constexpr int b_off(int n) {
   return n * (4 * n * n - 1) / 3;
 }
 
+// sort.cu: perm = 0 .. n - 1 ordered by descending key (keys clamped to
+// [0, 2^32)), equal keys in ascending index order; asynchronous on st.
+void order_desc(const int64_t* key, int64_t n, int32_t* perm, cudaStream_t st);
+// tree_build.cu: work orders of a tree whose lists are set (m2l_order,
+// leaf_order), on the device.
+void build_work_orders(fmm_tree* t, cudaStream_t st);
+
 // scan.cu: exclusive prefix sum of n int64 values (in place allowed);
 // returns the total (synchronises the stream).
 int64_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
@@ -302,6 +321,23 @@ void exclusive_scan_async(const int64_t* in, int64_t* out, int64_t n, int64_t* t
 void* tracked_malloc(size_t bytes);
 void dev_free(void* p);
 
+// Stream-ordered allocation for the duration of a build: while an AllocScope
+// is alive on this thread, tracked_malloc takes memory from the library's
+// pool on the scope's stream and dev_free returns it on that stream (no
+// cudaMalloc, no implicit device synchronisation of cudaFree).  Pointers
+// that outlive the scope (the tree's arrays) are freed later like any other.
+inline thread_local cudaStream_t tl_alloc_stream = nullptr;
+inline thread_local cudaMemPool_t tl_alloc_pool = nullptr;
+// Returns the pool's unused memory to the device (outside a build).
+void trim_pool();
+struct AllocScope {
+  cudaStream_t prev;
+  cudaMemPool_t prev_pool;
+  cudaMemPool_t pool;
+  explicit AllocScope(cudaStream_t s);
+  ~AllocScope();
+};
+
 template <class T>
 T* dev_alloc(fmm_tree* t, size_t count) {
   if (count == 0) count = 1;
@@ -309,6 +345,39 @@ T* dev_alloc(fmm_tree* t, size_t count) {
   if (t) t->device_bytes += sizeof(T) * count;
   return p;
 }
+
+// Build-phase trace, on when the environment holds FMM_BUILD_TRACE=1: every
+// trace_mark synchronises the build stream and prints the wall time since the
+// previous mark to stderr (a diagnostic of where a build spends its time; the
+// marks cost nothing when the trace is off).
+struct BuildTrace {
+  cudaStream_t st = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  explicit BuildTrace(cudaStream_t s) : st(s), t0(std::chrono::steady_clock::now()) {}
+  void mark(const char* what) {
+    cudaStreamSynchronize(st);
+    const auto t1 = std::chrono::steady_clock::now();
+    fprintf(stderr, "fmm build: %-28s %8.3f ms\n", what, std::chrono::duration<double, std::milli>(t1 - t0).count());
+    t0 = t1;
+  }
+};
+inline thread_local BuildTrace* tl_trace = nullptr;
+inline bool build_trace_enabled() {
+  const char* e = std::getenv("FMM_BUILD_TRACE");
+  return e && e[0] == '1';
+}
+inline void trace_mark(const char* what) {
+  if (tl_trace) tl_trace->mark(what);
+}
+// Installs a trace for the current thread's build when the environment asks
+// for one, and removes it when the build returns.
+struct TraceScope {
+  BuildTrace tr;
+  explicit TraceScope(cudaStream_t s) : tr(s) {
+    if (build_trace_enabled()) tl_trace = &tr;
+  }
+  ~TraceScope() { tl_trace = nullptr; }
+};
 
 template <class T>
 T* scratch_alloc(size_t count) {

@@ -12,6 +12,9 @@ Ptrs ptrs(const fmm_tree* t) {
 }
 }  // namespace
 void eval_fp64(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
+  // the FP64 data are made when an FP64 precision is selected (ensure_fp64)
+  require(t->geo64 && t->m2m64 && t->l2d64 && t->M64 && t->Lam64 && t->src64 && (!t->sym || t->sym_partial_f64),
+          "the tree's FP64 data are missing (select FMM_FP64 or FMM_FP64DF with fmm_tree_set_precision)");
   eval_impl(t, q, u, field, st);
 }
 void init_tables_fp64() { upload_tables(); }

@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
       load_coef<P>(M + s * NCP, v);
       const real rinv = geo[i], uS = geo[n_m2l + i], uT = geo[2 * n_m2l + i];
       real cp[P], sp[P], ct[P], st[P];
-      load_trig<P>(geo, n_m2l, i, 3, cp, sp, ct, st);
+      trig_multiples<P>(geo[3 * n_m2l + i], geo[4 * n_m2l + i], cp, sp);
+      trig_multiples<P>(geo[5 * n_m2l + i], geo[6 * n_m2l + i], ct, st);
       translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_m2l<P>(w, uS, uT, rinv); });
       m2l_acc_add<P>(mine, v);
     }
@@ -326,13 +327,8 @@ __global__ void __launch_bounds__(128) m2l_kernel_df(int64_t n_targets, const in
       }
       const dff rinv = geo(0, i), uS = geo(1, i), uT = geo(2, i);
       dff cp[P], sp[P], ct[P], st[P];
-#pragma unroll
-      for (int m = 0; m < P; m++) {
-        cp[m] = geo(3 + m, i);
-        sp[m] = geo(3 + P + m, i);
-        ct[m] = geo(3 + 2 * P + m, i);
-        st[m] = geo(3 + 3 * P + m, i);
-      }
+      trig_multiples<P>(geo(3, i), geo(4, i), cp, sp);
+      trig_multiples<P>(geo(5, i), geo(6, i), ct, st);
       translate_rotated<P>(v, cp, sp, ct, st, [&](dff (&w)[NC]) { axial_m2l<P>(w, uS, uT, rinv); });
 #pragma unroll
       for (int c = 0; c < NC; c++) {

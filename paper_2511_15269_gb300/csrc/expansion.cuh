@@ -138,6 +138,21 @@ __device__ __forceinline__ void apply_b(T (&v)[ncoef(P)]) {
   });
 }
 
+// cos(m a), sin(m a) for m = 1..P from cos a, sin a by angle addition, in
+// the arithmetic of T (FP32: the error grows by about one rounding per step,
+// and the degree-m coefficients it touches carry the factor (rho/r)^m of the
+// expansion, so the potential sees a few roundings at most).
+template <int P, class T>
+__device__ __forceinline__ void trig_multiples(T c1, T s1, T (&c)[P], T (&s)[P]) {
+  c[0] = c1;
+  s[0] = s1;
+#pragma unroll
+  for (int m = 1; m < P; m++) {
+    c[m] = fmar(c[m - 1], c1, -(s[m - 1] * s1));
+    s[m] = fmar(s[m - 1], c1, c[m - 1] * s1);
+  }
+}
+
 // Rotate so that the translation vector lies on +z, apply the axial
 // transform `axial`, rotate back.  Both polar rotations run through one copy
 // of the quarter-turn products (a two-pass loop, the second pass with the

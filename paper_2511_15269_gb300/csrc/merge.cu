@@ -112,9 +112,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   m->pos_local = dev_alloc<float4>(m, N);
   m->pos64 = dev_alloc<dvec4>(m, N);
   m->geo32 = dev_alloc<float>(m, (size_t)m2l_fields(p) * std::max<int64_t>(NM, 1));
-  m->geo64 = dev_alloc<double>(m, (size_t)m2l_fields(p) * std::max<int64_t>(NM, 1));
   m->m2m32 = dev_alloc<float>(m, (size_t)edge_fields(p) * NB);
-  m->m2m64 = dev_alloc<double>(m, (size_t)edge_fields(p) * NB);
 
   for (int k = 0; k < nt; k++) {
     const fmm_tree& t = *in[k];
@@ -140,9 +138,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
     copy_d2d(m->pos_local + po[k], t.pos_local, t.n, st);
     copy_d2d(m->pos64 + po[k], t.pos64, t.n, st);
     copy_rows(m->geo32, NM, mo[k], t.geo32, t.n_m2l, m2l_fields(p), st);
-    copy_rows(m->geo64, NM, mo[k], t.geo64, t.n_m2l, m2l_fields(p), st);
     copy_rows(m->m2m32, NB, bo[k], t.m2m32, t.n_boxes, edge_fields(p), st);
-    copy_rows(m->m2m64, NB, bo[k], t.m2m64, t.n_boxes, edge_fields(p), st);
   }
   {
     const int64_t tails[2] = {NM, NP};
@@ -177,41 +173,15 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
 
   // work orders over the whole batch: longest M2L lists and heaviest near
   // fields first
-  {
-    std::vector<int64_t> off(NB + 1), poff(NL + 1);
-    std::vector<int32_t> cnt(NB), psrc(NP), lbox(NL);
-    FMM_CUDA_TRY(cudaMemcpyAsync(off.data(), m->m2l_off, sizeof(int64_t) * (NB + 1), cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(poff.data(), m->p2p_off, sizeof(int64_t) * (NL + 1), cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(cnt.data(), m->box_count, sizeof(int32_t) * NB, cudaMemcpyDeviceToHost, st));
-    if (NP) FMM_CUDA_TRY(cudaMemcpyAsync(psrc.data(), m->p2p_src, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(lbox.data(), m->leaf_box, sizeof(int32_t) * NL, cudaMemcpyDeviceToHost, st));
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    std::vector<int32_t> ord(NB);
-    for (int64_t g = 0; g < NB; g++) ord[g] = (int32_t)g;
-    std::stable_sort(ord.begin(), ord.end(),
-                     [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
-    std::vector<int64_t> work(NL, 0);
-    for (int64_t l = 0; l < NL; l++)
-      for (int64_t e = poff[l]; e < poff[l + 1]; e++) work[l] += (int64_t)cnt[lbox[psrc[e]]] * cnt[lbox[l]];
-    std::vector<int32_t> lord(NL);
-    for (int64_t l = 0; l < NL; l++) lord[l] = (int32_t)l;
-    std::stable_sort(lord.begin(), lord.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
-    m->m2l_order = dev_alloc<int32_t>(m, NB);
-    m->leaf_order = dev_alloc<int32_t>(m, NL);
-    FMM_CUDA_TRY(cudaMemcpyAsync(m->m2l_order, ord.data(), sizeof(int32_t) * NB, cudaMemcpyHostToDevice, st));
-    FMM_CUDA_TRY(cudaMemcpyAsync(m->leaf_order, lord.data(), sizeof(int32_t) * NL, cudaMemcpyHostToDevice, st));
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  }
+  m->src_leaf_box = m->leaf_box;
+  build_work_orders(m, st);
 
   // evaluation workspace
   const int NCP = ncoef_pad(p);
   m->src32 = dev_alloc<float4>(m, N);
   m->src_dup = dev_alloc<DupRec>(m, N);
-  m->src64 = dev_alloc<dvec4>(m, N);
   m->M32 = dev_alloc<float>(m, (size_t)NB * NCP);
   m->Lam32 = dev_alloc<float>(m, (size_t)NB * NCP);
-  m->M64 = dev_alloc<double>(m, (size_t)NB * NCP);
-  m->Lam64 = dev_alloc<double>(m, (size_t)NB * NCP);
   m->near_u = dev_alloc<double>(m, N);
   m->near_f = dev_alloc<double>(m, 3 * (size_t)N);
   m->src_dup2 = dev_alloc<DupRec>(m, N);

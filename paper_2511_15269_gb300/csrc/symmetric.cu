@@ -57,40 +57,60 @@ __global__ void mirror_kernel(int64_t n_leaves, const int64_t* __restrict__ off,
 
 // per leaf: entries its warp evaluates (owned pairs and one-sided entries)
 // and entries it receives (pairs owned by the partner)
+// One warp per leaf (lanes over its entries): a received entry (the
+// partner owns the pair) or an entry the leaf's warp evaluates.
+__device__ __forceinline__ bool is_received(const int64_t* __restrict__ mirror, const int64_t* __restrict__ owns,
+                                            int64_t e) {
+  return !owns[e] && mirror[e] >= 0;
+}
+
 __global__ void count_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int64_t* __restrict__ mirror,
                              const int64_t* __restrict__ owns, int64_t* __restrict__ n_work,
                              int64_t* __restrict__ n_recv) {
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n_leaves;
-       l += (int64_t)gridDim.x * blockDim.x) {
-    int64_t w = 0, r = 0;
-    for (int64_t e = off[l]; e < off[l + 1]; e++) {
-      if (!owns[e] && mirror[e] >= 0) r++;
-      else w++;
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  const int lane = threadIdx.x & 31;
+  for (int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; l < n_leaves; l += warps) {
+    int64_t r = 0;
+    for (int64_t e = off[l] + lane; e < off[l + 1]; e += 32) r += is_received(mirror, owns, e) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) {
+      n_work[l] = (off[l + 1] - off[l]) - r;
+      n_recv[l] = r;
     }
-    n_work[l] = w;
-    n_recv[l] = r;
   }
 }
 
 // Work entries in list order, and slots: a received entry's slot is its
 // position in the receivers' concatenated lists, so the slots a leaf adds are
-// contiguous; the owning entry (its mirror) writes to the same slot.
+// contiguous; the owning entry (its mirror) writes to the same slot.  The
+// warp walks its leaf's list in chunks of 32 entries, in order, ranking
+// each kind of entry by ballot.
 __global__ void fill_kernel(int64_t n_leaves, const int64_t* __restrict__ off, const int64_t* __restrict__ mirror,
                             const int64_t* __restrict__ owns, const int64_t* __restrict__ work_off,
                             const int64_t* __restrict__ recv_off, int32_t* __restrict__ work,
                             int32_t* __restrict__ slot) {
-  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n_leaves;
-       l += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  for (int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; l < n_leaves; l += warps) {
     int64_t w = work_off[l], r = recv_off[l];
-    for (int64_t e = off[l]; e < off[l + 1]; e++) {
-      if (!owns[e] && mirror[e] >= 0) {
-        slot[e] = (int32_t)r;
-        slot[mirror[e]] = (int32_t)r;
-        r++;
-      } else {
+    for (int64_t e0 = off[l]; e0 < off[l + 1]; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool valid = e < off[l + 1];
+      const bool recv = valid && is_received(mirror, owns, e);
+      const unsigned br = __ballot_sync(0xffffffffu, recv);
+      const unsigned bw = __ballot_sync(0xffffffffu, valid && !recv);
+      if (recv) {
+        const int32_t sl = (int32_t)(r + __popc(br & below));
+        slot[e] = sl;
+        slot[mirror[e]] = sl;
+      } else if (valid) {
         if (!owns[e]) slot[e] = -1;
-        work[w++] = (int32_t)e;
+        work[w + __popc(bw & below)] = (int32_t)e;
       }
+      r += __popc(br);
+      w += __popc(bw);
     }
   }
 }
@@ -158,12 +178,20 @@ __global__ void frame_rec_kernel(int64_t n_leaves, const int64_t* __restrict__ w
   }
 }
 
-template <class T>
-std::vector<T> host_copy(const T* d, int64_t n, cudaStream_t st) {
-  std::vector<T> h((size_t)std::max<int64_t>(n, 0));
-  if (n > 0) FMM_CUDA_TRY(cudaMemcpyAsync(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost, st));
-  FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  return h;
+// points of the source leaves a leaf's warp evaluates (its work list)
+__global__ void sym_cost_kernel(int64_t n_leaves, const int64_t* __restrict__ work_off,
+                                const int32_t* __restrict__ work, const int32_t* __restrict__ src,
+                                const int32_t* __restrict__ src_leaf_box, const int32_t* __restrict__ box_count,
+                                int64_t* __restrict__ cost) {
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; l < n_leaves; l += warps) {
+    int64_t c = 0;
+    for (int64_t k = work_off[l] + (threadIdx.x & 31); k < work_off[l + 1]; k += 32)
+      c += box_count[src_leaf_box[src[work[k]]]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) cost[l] = c;
+  }
 }
 
 }  // namespace
@@ -178,26 +206,59 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
   int64_t* n_recv = scratch_alloc<int64_t>(NL + 1);
   FMM_CUDA_TRY(cudaMemsetAsync(n_work + NL, 0, sizeof(int64_t), st));
   FMM_CUDA_TRY(cudaMemsetAsync(n_recv + NL, 0, sizeof(int64_t), st));
+  trace_mark("  sym: scratch");
   mirror_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->p2p_off, t->p2p_src, mirror, owns);
   FMM_LAUNCH_CHECK();
-  count_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->p2p_off, mirror, owns, n_work, n_recv);
+  trace_mark("  sym: mirror");
+  count_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->p2p_off, mirror, owns, n_work, n_recv);
   FMM_LAUNCH_CHECK();
   t->sym_work_off = dev_alloc<int64_t>(t, NL + 1);
   t->sym_recv_off = dev_alloc<int64_t>(t, NL + 1);
   const int64_t nw = exclusive_scan(n_work, t->sym_work_off, NL + 1, st);
   t->n_slots = exclusive_scan(n_recv, t->sym_recv_off, NL + 1, st);
   require(t->n_slots < ((int64_t)1 << 31), "too many symmetric pairs");
+  trace_mark("  sym: count + scans");
   t->sym_slot = dev_alloc<int32_t>(t, NE1);
   t->sym_work = dev_alloc<int32_t>(t, std::max<int64_t>(nw, 1));
-  fill_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->p2p_off, mirror, owns, t->sym_work_off, t->sym_recv_off,
-                                                 t->sym_work, t->sym_slot);
+  fill_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->p2p_off, mirror, owns, t->sym_work_off,
+                                                       t->sym_recv_off, t->sym_work, t->sym_slot);
   FMM_LAUNCH_CHECK();
+  trace_mark("  sym: fill");
   t->sym_rec = dev_alloc<SymRec>(t, std::max<int64_t>(nw, 1));
   rec_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->sym_work_off, t->sym_work, t->p2p32, t->p2p_thr,
                                                      t->sym_slot, t->src_leaf_box, t->box_start, t->box_count,
                                                      t->sym_rec);
   FMM_LAUNCH_CHECK();
-  // FP64DF point records and per-entry source frames
+  trace_mark("  sym: records");
+  dev_free(mirror), dev_free(owns), dev_free(n_work), dev_free(n_recv);
+  t->sym_stride = std::max(t->max_leaf, 1);
+  // slot sums in FP32 for the FP32C path; ensure_fp64 widens them to doubles
+  // when an FP64 precision is selected
+  t->sym_partial = reinterpret_cast<double*>(
+      dev_alloc<float>(t, (size_t)std::max<int64_t>(t->n_slots, 1) * t->sym_stride));
+  t->sym_partial_f64 = 0;
+  trace_mark("  sym: slots");
+
+  // work order of the symmetric kernel: heaviest work list first
+  int64_t* cost = scratch_alloc<int64_t>(std::max<int64_t>(NL, 1));
+  sym_cost_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->sym_work_off, t->sym_work, t->p2p_src,
+                                                          t->src_leaf_box, t->box_count, cost);
+  FMM_LAUNCH_CHECK();
+  t->leaf_order_sym = dev_alloc<int32_t>(t, NL);
+  order_desc(cost, NL, t->leaf_order_sym, st);
+  dev_free(cost);
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  t->sym = 1;
+}
+
+// FP64DF near field: double-float point records and the source frame of
+// every work entry (made once, when FMM_FP64DF is first selected)
+void build_df_near(fmm_tree* t, cudaStream_t st) {
+  if (t->src_df || !t->sym) return;
+  const int64_t NL = t->n_leaves;
+  int64_t nw = 0;
+  FMM_CUDA_TRY(cudaMemcpyAsync(&nw, t->sym_work_off + NL, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
   t->src_df = dev_alloc<DFRec>(t, t->n);
   df_points_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->leaf_box, t->box_start, t->box_count, t->center,
                                                            t->pos64, t->src_df);
@@ -207,27 +268,6 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
                                                            t->center, t->sym_frame);
   FMM_LAUNCH_CHECK();
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  dev_free(mirror), dev_free(owns), dev_free(n_work), dev_free(n_recv);
-  t->sym_stride = std::max(t->max_leaf, 1);
-  // slot sums in FP32 (FP32C path) or FP64 (FP64 path): room for doubles
-  t->sym_partial = dev_alloc<double>(t, std::max<int64_t>(t->n_slots, 1) * t->sym_stride);
-
-  // work order of the symmetric kernel: heaviest work list first
-  std::vector<int64_t> woff = host_copy(t->sym_work_off, NL + 1, st);
-  std::vector<int32_t> work = host_copy(t->sym_work, nw, st);
-  std::vector<int32_t> src = host_copy(t->p2p_src, NE, st);
-  std::vector<int32_t> lbox = host_copy(t->leaf_box, NL, st);
-  std::vector<int32_t> cnt = host_copy(t->box_count, t->n_boxes, st);
-  std::vector<int64_t> cost(NL, 0);
-  for (int64_t l = 0; l < NL; l++)
-    for (int64_t k = woff[l]; k < woff[l + 1]; k++) cost[l] += cnt[lbox[src[work[k]]]];
-  std::vector<int32_t> ord(NL);
-  for (int64_t l = 0; l < NL; l++) ord[l] = (int32_t)l;
-  std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
-  t->leaf_order_sym = dev_alloc<int32_t>(t, NL);
-  FMM_CUDA_TRY(cudaMemcpyAsync(t->leaf_order_sym, ord.data(), sizeof(int32_t) * NL, cudaMemcpyHostToDevice, st));
-  FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  t->sym = 1;
 }
 
 }  // namespace fmm

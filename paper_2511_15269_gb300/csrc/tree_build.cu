@@ -228,33 +228,62 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const double* __re
   }
 }
 
+// One warp per segment: lane j holds bins 8j .. 8j + 7 of the segment's
+// histogram; a warp prefix sum over the lanes' totals finds the bin holding
+// the pivot (the first bin whose cumulative count exceeds its rank), and the
+// bins are cleared for the next digit.
 __global__ void radix_select_kernel(Sel* __restrict__ sel, int nseg, int d, unsigned* __restrict__ hist,
                                     int* __restrict__ unresolved) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nseg) return;
+  const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= nseg) return;  // whole warps leave together
+  unsigned* h = hist + (size_t)j * 256 + 8 * lane;
   Sel s = sel[j];
-  unsigned* h = hist + (size_t)j * 256;
   if (!s.resolved) {
-    long long cum = 0;
-    int dig = 255;
-    unsigned cnt = 0;
-    for (int b = 0; b < 256; b++) {
-      if (cum + h[b] > s.krem) {
-        dig = b;
-        cnt = h[b];
-        break;
-      }
-      cum += h[b];
+    unsigned b[8];
+    unsigned tot = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      b[k] = h[k];
+      tot += b[k];
     }
-    s.krem -= cum;
-    if (d < 8) s.phi |= (unsigned long long)dig << (56 - 8 * d);
-    else s.plo |= (unsigned)dig << (24 - 8 * (d - 8));
-    s.bits += 8;
-    if (cnt <= 1) s.resolved = 1;
-    else atomicOr(unresolved, 1);
-    sel[j] = s;
+    // exclusive prefix of the lanes' totals
+    unsigned inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const long long before = (long long)(inc - tot);
+    // the lane whose range holds rank krem
+    bool mine = before <= s.krem && s.krem < before + (long long)tot;
+    // no bin holds the rank (cannot happen for a segment with points left):
+    // the last bin, as a resolved prefix
+    if (__ballot_sync(0xffffffffu, mine) == 0u && lane == 31) mine = true;
+    if (mine) {
+      long long cum = before;
+      int dig = 8 * lane + 7;
+      unsigned cnt = 0;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        if (cnt == 0 && cum + (long long)b[k] > s.krem) {
+          dig = 8 * lane + k;
+          cnt = b[k];
+        } else if (cnt == 0) {
+          cum += b[k];
+        }
+      }
+      s.krem -= cum;
+      if (d < 8) s.phi |= (unsigned long long)dig << (56 - 8 * d);
+      else s.plo |= (unsigned)dig << (24 - 8 * (d - 8));
+      s.bits += 8;
+      if (cnt <= 1) s.resolved = 1;
+      else atomicOr(unresolved, 1);
+      sel[j] = s;
+    }
   }
-  for (int b = 0; b < 256; b++) h[b] = 0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) h[k] = 0;
 }
 
 // Points with key prefix <= the pivot's go to the lower child.
@@ -575,9 +604,50 @@ __global__ void index_lists_kernel(int64_t nbox, int s, int L, int32_t* __restri
 }
 
 // adjacent-pair sums, one stage
-__global__ void pair_sum_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t m) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < m) out[i] = __dadd_rn(in[2 * i], in[2 * i + 1]);
+// Sum of the radii of every level (block l: level l, 2^(s l) boxes from
+// offset level_offset(l, s)), as adjacent-pair sums repeated down to one
+// value: each thread first sums a contiguous power-of-two chunk with the same
+// pairing (a binary counter: a partial sum is combined with its left
+// neighbour of equal size as soon as one exists), then the block pairs the
+// threads' partials in shared memory.
+constexpr int kLevelSumThreads = 256;
+__global__ void __launch_bounds__(kLevelSumThreads) level_sum_kernel(const double* __restrict__ radius, int s,
+                                                                    double* __restrict__ out) {
+  const int l = blockIdx.x;
+  const int64_t m = (int64_t)1 << (s * l);
+  int64_t off = 0;
+  for (int i = 0; i < l; i++) off += (int64_t)1 << (s * i);
+  const int nt = m < kLevelSumThreads ? (int)m : kLevelSumThreads;  // a power of two
+  const int64_t chunk = m / nt;
+  __shared__ double part[kLevelSumThreads];
+  if (threadIdx.x < nt) {
+    double stack[64];
+    int64_t size[64];
+    int top = 0;
+    const double* v = radius + off + (int64_t)threadIdx.x * chunk;
+    for (int64_t k = 0; k < chunk; k++) {
+      double x = v[k];
+      int64_t sz = 1;
+      while (top > 0 && size[top - 1] == sz) {
+        x = __dadd_rn(stack[top - 1], x);
+        sz *= 2;
+        top--;
+      }
+      stack[top] = x;
+      size[top] = sz;
+      top++;
+    }
+    part[threadIdx.x] = stack[0];
+  }
+  __syncthreads();
+  for (int w = nt / 2; w >= 1; w /= 2) {
+    double x = 0.0;
+    if (threadIdx.x < w) x = __dadd_rn(part[2 * threadIdx.x], part[2 * threadIdx.x + 1]);
+    __syncthreads();
+    if (threadIdx.x < w) part[threadIdx.x] = x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[l] = part[0];
 }
 
 // ---- lists -----------------------------------------------------------------------
@@ -597,29 +667,32 @@ __device__ __forceinline__ bool well_separated(const double* __restrict__ c, con
   return d > 0.0 && lhs <= rhs;
 }
 
+// Eq. 4 on every candidate pair; the two flags (well separated, kept) are
+// packed as ws + (keep << 32) so that one scan yields both prefix counts
+// (each stays below 2^32).
 __global__ void ws_kernel(const int32_t* __restrict__ ct, const int32_t* __restrict__ cs, int64_t nc,
                           int64_t offt, int64_t offs, const double* __restrict__ center,
-                          const double* __restrict__ radius, double theta, int64_t* __restrict__ fws,
-                          int64_t* __restrict__ fkeep) {
+                          const double* __restrict__ radius, double theta, int64_t* __restrict__ flags) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
     const bool w = well_separated(center, radius, offs + cs[e], offt + ct[e], theta);
-    fws[e] = w ? 1 : 0;
-    fkeep[e] = w ? 0 : 1;
+    flags[e] = w ? 1 : ((int64_t)1 << 32);
   }
 }
 
 __global__ void emit_kernel(const int32_t* __restrict__ ct, const int32_t* __restrict__ cs, int64_t nc,
-                            int64_t offt, int64_t offs, const int64_t* __restrict__ fws,
-                            const int64_t* __restrict__ pws, const int64_t* __restrict__ pkeep,
-                            int32_t* __restrict__ mt, int32_t* __restrict__ ms, int32_t* __restrict__ kt,
-                            int32_t* __restrict__ ks) {
+                            int64_t offt, int64_t offs, const int64_t* __restrict__ flags,
+                            const int64_t* __restrict__ pref, int32_t* __restrict__ mt, int32_t* __restrict__ ms,
+                            int32_t* __restrict__ kt, int32_t* __restrict__ ks) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
-    if (fws[e]) {
-      mt[pws[e]] = (int32_t)(offt + ct[e]);
-      ms[pws[e]] = (int32_t)(offs + cs[e]);
+    const int64_t p = pref[e];
+    if (flags[e] & 1) {
+      const int64_t o = p & 0xffffffffll;
+      mt[o] = (int32_t)(offt + ct[e]);
+      ms[o] = (int32_t)(offs + cs[e]);
     } else {
-      kt[pkeep[e]] = ct[e];
-      ks[pkeep[e]] = cs[e];
+      const int64_t o = p >> 32;
+      kt[o] = ct[e];
+      ks[o] = cs[e];
     }
   }
 }
@@ -668,18 +741,26 @@ __global__ void expand_kernel(const int32_t* __restrict__ kt, const int32_t* __r
   }
 }
 
-__global__ void count_kernel(const int32_t* __restrict__ key, int64_t n, int64_t* __restrict__ cnt) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[key[e]]), 1ull);
+
+// Lists of one march step are sorted by target, so each target forms one run
+// of consecutive entries.  run_start_kernel records where each target's run
+// begins; m2l_scatter_kernel places entry e of the run of g at off[g] +
+// fill[g] + (e - start of the run); m2l_fill_kernel adds each run's length to
+// fill[g] (also used to count the entries per target).
+__global__ void run_start_kernel(const int32_t* __restrict__ mt, int64_t nm, int64_t* __restrict__ rs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nm; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = mt[e];
+    if (e == 0 || mt[e - 1] != g) rs[g] = e;
+  }
 }
 
 __global__ void m2l_scatter_kernel(const int32_t* __restrict__ mt, const int32_t* __restrict__ ms, int64_t nm,
                                    const int64_t* __restrict__ off, const int64_t* __restrict__ fill,
-                                   int32_t* __restrict__ out_t, int32_t* __restrict__ out_s) {
+                                   const int64_t* __restrict__ rs, int32_t* __restrict__ out_t,
+                                   int32_t* __restrict__ out_s) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nm; e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t g = mt[e];
-    const int64_t first = lower_bound32(mt, nm, g);
-    const int64_t pos = off[g] + fill[g] + (e - first);
+    const int64_t pos = off[g] + fill[g] + (e - rs[g]);
     out_t[pos] = g;
     out_s[pos] = ms[e];
   }
@@ -694,8 +775,9 @@ __global__ void m2l_fill_kernel(const int32_t* __restrict__ mt, int64_t nm, int6
 
 // ---- rotation coefficients -----------------------------------------------------------
 // For t = c_old - c_new: 1/r and cos/sin of the multiples of the polar angle
-// theta and azimuth phi of t, in FP64 by angle addition, stored in FP64 and
-// rounded to FP32.
+// theta and azimuth phi of t, in FP64 by angle addition, stored in FP64
+// (g64) and rounded to FP32 (g32); either may be NULL (the FP64 copies are
+// made only once a tree's precision needs them).
 __device__ void trig_rows(const double t[3], int p, int64_t e, int64_t stride, int f0, double* g64, float* g32,
                           double* rout) {
   const double rxy = sqrt(t[0] * t[0] + t[1] * t[1]);
@@ -721,13 +803,16 @@ __device__ void trig_rows(const double t[3], int p, int64_t e, int64_t stride, i
     const int64_t rows[4] = {f0 + m - 1, f0 + p + m - 1, f0 + 2 * p + m - 1, f0 + 3 * p + m - 1};
     const double vals[4] = {cpm, spm, ctm, stm};
     for (int k = 0; k < 4; k++) {
-      g64[rows[k] * stride + e] = vals[k];
-      g32[rows[k] * stride + e] = (float)vals[k];
+      if (g64) g64[rows[k] * stride + e] = vals[k];
+      if (g32) g32[rows[k] * stride + e] = (float)vals[k];
     }
   }
   *rout = r;
 }
 
+// M2L records: 1/r, rho_S/r, rho_T/r and the cosines and sines of the polar
+// angle theta and azimuth phi of t = c_S - c_T, in FP64 (g64) and rounded to
+// FP32 (g32); either may be NULL.
 __global__ void m2l_geo_kernel(const int32_t* __restrict__ mt, const int32_t* __restrict__ ms, int64_t nm,
                                const double* __restrict__ center, const double* __restrict__ radius, int p,
                                double* __restrict__ g64, float* __restrict__ g32) {
@@ -735,40 +820,55 @@ __global__ void m2l_geo_kernel(const int32_t* __restrict__ mt, const int32_t* __
     const int64_t gt = mt[e], gs = ms[e];
     const double t[3] = {center[3 * gs] - center[3 * gt], center[3 * gs + 1] - center[3 * gt + 1],
                          center[3 * gs + 2] - center[3 * gt + 2]};
-    double r;
-    trig_rows(t, p, e, nm, 3, g64, g32, &r);
-    const double vals[3] = {1.0 / r, radius[gs] / r, radius[gt] / r};
-    for (int k = 0; k < 3; k++) {
-      g64[k * nm + e] = vals[k];
-      g32[k * nm + e] = (float)vals[k];
+    const double rxy = sqrt(t[0] * t[0] + t[1] * t[1]);
+    const double r = sqrt(rxy * rxy + t[2] * t[2]);
+    double ct = 1.0, st = 0.0, cp = 1.0, sp = 0.0;
+    if (r > 0.0) {
+      ct = t[2] / r;
+      st = rxy / r;
+    }
+    if (rxy > 0.0) {
+      cp = t[0] / rxy;
+      sp = t[1] / rxy;
+    }
+    const double vals[7] = {1.0 / r, radius[gs] / r, radius[gt] / r, cp, sp, ct, st};
+    for (int k = 0; k < 7; k++) {
+      if (g64) g64[k * nm + e] = vals[k];
+      if (g32) g32[k * nm + e] = (float)vals[k];
     }
   }
+  (void)p;
 }
 
-// M2M (t = c_child - c_parent) per child box.
-__global__ void edge_geo_kernel(int64_t nbox, int s, const double* __restrict__ center,
+// M2M (t = c_child - c_parent) per child box; boxes without a parent (the
+// roots) get zero rows.  m64 / m32 may be NULL.
+__global__ void edge_geo_kernel(int64_t nbox, const int32_t* __restrict__ parent, const double* __restrict__ center,
                                 const double* __restrict__ radius, int p, double* __restrict__ m64,
                                 float* __restrict__ m32) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nbox) return;
-  if (g == 0) {
-    for (int f = 0; f < 2 + 4 * p; f++) m64[f * nbox] = m32[f * nbox] = 0;
+  const int64_t gp = parent[g];
+  if (gp < 0) {
+    for (int f = 0; f < 2 + 4 * p; f++) {
+      if (m64) m64[f * nbox + g] = 0;
+      if (m32) m32[f * nbox + g] = 0;
+    }
     return;
   }
-  int l = 0;
-  while (level_offset(l + 1, s) <= g) l++;
-  const int64_t b = g - level_offset(l, s);
-  const int64_t gp = level_offset(l - 1, s) + (b >> s);
   const double t[3] = {center[3 * g] - center[3 * gp], center[3 * g + 1] - center[3 * gp + 1],
                        center[3 * g + 2] - center[3 * gp + 2]};
   double r;
   trig_rows(t, p, g, nbox, 2, m64, m32, &r);
   const double rp = radius[gp];
   const double a = rp > 0.0 ? r / rp : 0.0, bb = rp > 0.0 ? radius[g] / rp : 0.0;
-  m64[g] = a;
-  m32[g] = (float)a;
-  m64[nbox + g] = bb;
-  m32[nbox + g] = (float)bb;
+  if (m64) {
+    m64[g] = a;
+    m64[nbox + g] = bb;
+  }
+  if (m32) {
+    m32[g] = (float)a;
+    m32[nbox + g] = (float)bb;
+  }
 }
 
 // Direct L2L records (one per target leaf and ancestor with a non-empty M2L
@@ -796,17 +896,21 @@ __global__ void l2d_fill_kernel(int64_t nl, const int32_t* __restrict__ leaf_box
   int64_t e = off[leaf];
   for (int64_t a = parent[g]; a >= 0; a = parent[a]) {
     if (!has_m2l(m2l_off, a)) continue;
-    anc[e] = (int32_t)a;
+    if (anc) anc[e] = (int32_t)a;
     const double t[3] = {center[3 * a] - center[3 * g], center[3 * a + 1] - center[3 * g + 1],
                          center[3 * a + 2] - center[3 * g + 2]};
     double r;
     trig_rows(t, p, e, n_rec, 2, e64, e32, &r);
     const double ra = radius[a];
     const double va = ra > 0.0 ? r / ra : 0.0, vb = ra > 0.0 ? radius[g] / ra : 0.0;
-    e64[e] = va;
-    e32[e] = (float)va;
-    e64[n_rec + e] = vb;
-    e32[n_rec + e] = (float)vb;
+    if (e64) {
+      e64[e] = va;
+      e64[n_rec + e] = vb;
+    }
+    if (e32) {
+      e32[e] = (float)va;
+      e32[n_rec + e] = (float)vb;
+    }
     e++;
   }
 }
@@ -962,6 +1066,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
     dev_free(tab);
   }
   t->has_duplicates = has_dup;
+  trace_mark("canon + duplicates");
 
   // ---- segment boundaries of every round (closed form) ----
   std::vector<int64_t> round_off(R + 2);
@@ -1002,15 +1107,21 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
       FMM_LAUNCH_CHECK();
       seg_axis_kernel<<<(ns + 255) / 256, 256, 0, st>>>(bmin, bmax, stt, ns, sel);
       FMM_LAUNCH_CHECK();
+      // 8-bit digits of the 96-bit key; a resolved segment skips the later
+      // passes on the device, and the host looks at the flag only from the
+      // third digit on (random 64-bit keys of up to ~2^24 points are
+      // resolved by then), one synchronisation per round in the usual case
       for (int d = 0; d < 12; d++) {
         FMM_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
         radix_hist_kernel<<<nblk, kThreads, 0, st>>>(Xa, Ia, n, stt, ns, sel, d, hist);
         FMM_LAUNCH_CHECK();
-        radix_select_kernel<<<(ns + 255) / 256, 256, 0, st>>>(sel, ns, d, hist, flag);
+        radix_select_kernel<<<(ns + 3) / 4, 128, 0, st>>>(sel, ns, d, hist, flag);
         FMM_LAUNCH_CHECK();
-        FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-        FMM_CUDA_TRY(cudaStreamSynchronize(st));
-        if (!hflag) break;
+        if (d >= 2) {
+          FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+          FMM_CUDA_TRY(cudaStreamSynchronize(st));
+          if (!hflag) break;
+        }
       }
       FMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 2 * ns, st));
       partition_kernel<<<nblk, kThreads, 0, st>>>(Xa, Ia, n, stt, ns, sel, ctr, Xb, Ib);
@@ -1021,6 +1132,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
     dev_free(bmin), dev_free(bmax), dev_free(ctr), dev_free(hist), dev_free(sel);
   }
+  trace_mark("large bisection rounds");
 
   // ---- remaining rounds and the leaf sort, one CTA per segment ----
   t->perm = dev_alloc<int32_t>(t, n);
@@ -1033,6 +1145,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
     FMM_LAUNCH_CHECK();
     std::swap(Xa, Xb);  // Xa: positions in tree order
   }
+  trace_mark("small segments + leaf order");
 
   // ---- box ranges and geometry ----
   t->box_start = dev_alloc<int64_t>(t, NB);
@@ -1061,6 +1174,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   centre_radius_kernel<<<grid_for(NB, 256, 1 << 30), 256, 0, st>>>(NB, blo, bhi, t->center, t->radius, t->inv_rho32,
                                                                    t->inv_rho64);
   FMM_LAUNCH_CHECK();
+  trace_mark("box ranges + geometry");
   // index lists: a single tree's M2M round r holds level L - r (children of
   // a parent consecutive)
   t->leaf_box = dev_alloc<int32_t>(t, NL);
@@ -1086,26 +1200,16 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   // ---- average radius per level ----
   t->level_avg_host = new double[L + 1];
   {
-    double* buf0 = scratch_alloc<double>(std::max<int64_t>(NL, 1));
-    double* buf1 = scratch_alloc<double>(std::max<int64_t>(NL, 1));
-    for (int l = 0; l <= L; l++) {
-      double* pa = buf0;
-      double* pb = buf1;
-      int64_t m = (int64_t)1 << (s * l);
-      FMM_CUDA_TRY(cudaMemcpyAsync(pa, t->radius + level_offset(l, s), sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-      while (m > 1) {
-        pair_sum_kernel<<<grid_for(m / 2, 256, 1 << 30), 256, 0, st>>>(pa, pb, m / 2);
-        FMM_LAUNCH_CHECK();
-        std::swap(pa, pb);
-        m /= 2;
-      }
-      double sum = 0;
-      FMM_CUDA_TRY(cudaMemcpyAsync(&sum, pa, sizeof(double), cudaMemcpyDeviceToHost, st));
-      FMM_CUDA_TRY(cudaStreamSynchronize(st));
-      t->level_avg_host[l] = sum / (double)((int64_t)1 << (s * l));
-    }
-    dev_free(buf0), dev_free(buf1);
+    double* sums = scratch_alloc<double>(L + 1);
+    level_sum_kernel<<<L + 1, kLevelSumThreads, 0, st>>>(t->radius, s, sums);
+    FMM_LAUNCH_CHECK();
+    std::vector<double> h(L + 1);
+    FMM_CUDA_TRY(cudaMemcpyAsync(h.data(), sums, sizeof(double) * (L + 1), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaStreamSynchronize(st));
+    dev_free(sums);
+    for (int l = 0; l <= L; l++) t->level_avg_host[l] = h[l] / (double)((int64_t)1 << (s * l));
   }
+  trace_mark("index lists + level averages");
 
   // ---- point records and M2M edge coefficients ----
   const int p = t->prm.p;
@@ -1114,9 +1218,9 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   point_records_kernel<<<grid_for(NL * 32, 256, 1 << 30), 256, 0, st>>>(Xa, n, t->box_start, t->box_count, leaf_off,
                                                                         NL, t->center, t->pos_local, t->pos64);
   FMM_LAUNCH_CHECK();
-  t->m2m64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
   t->m2m32 = dev_alloc<float>(t, (size_t)edge_fields(p) * NB);
-  edge_geo_kernel<<<grid_for(NB, 128, 1 << 30), 128, 0, st>>>(NB, s, t->center, t->radius, p, t->m2m64, t->m2m32);
+  edge_geo_kernel<<<grid_for(NB, 128, 1 << 30), 128, 0, st>>>(NB, t->box_parent, t->center, t->radius, p, nullptr,
+                                                              t->m2m32);
   FMM_LAUNCH_CHECK();
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
   t->device_bytes -= sizeof(double) * 6 * NB;  // bounding boxes leave with the caller
@@ -1124,6 +1228,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   *bhi_out = bhi;
   dev_free(starts);
   dev_free(Xa), dev_free(Xb), dev_free(Ia), dev_free(Ib), dev_free(flag);
+  trace_mark("point records + edges");
 }
 
 // One side of the list construction: the combined id of the side's root and
@@ -1157,23 +1262,20 @@ void march(const fmm_tree* t, Side S, Side T, cudaStream_t st, std::vector<Step>
   const bool tie_target = (t->prm.flags & FMM_TIE_TARGET) != 0;
   const bool same_level = (t->prm.flags & FMM_SAME_LEVEL) != 0;
   for (;;) {
-    int64_t* fws = scratch_alloc<int64_t>(nc);
-    int64_t* fkeep = scratch_alloc<int64_t>(nc);
-    int64_t* pws = scratch_alloc<int64_t>(nc);
-    int64_t* pkeep = scratch_alloc<int64_t>(nc);
+    require(nc < ((int64_t)1 << 32), "too many candidate pairs in one level-march step");
+    int64_t* flags = scratch_alloc<int64_t>(nc);
+    int64_t* pref = scratch_alloc<int64_t>(nc);
     const int64_t offt = T.base + level_offset(lt, s), offs = S.base + level_offset(ls, s);
-    ws_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, t->center, t->radius, t->prm.theta, fws,
-                                                 fkeep);
+    ws_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, t->center, t->radius, t->prm.theta, flags);
     FMM_LAUNCH_CHECK();
-    const int64_t nws = exclusive_scan(fws, pws, nc, st);
-    const int64_t nkeep = exclusive_scan(fkeep, pkeep, nc, st);
+    const int64_t both = exclusive_scan(flags, pref, nc, st);
+    const int64_t nws = both & 0xffffffffll, nkeep = both >> 32;
     Step stp{dev_alloc<int32_t>(nullptr, nws), dev_alloc<int32_t>(nullptr, nws), nws};
     int32_t* kt = dev_alloc<int32_t>(nullptr, nkeep);
     int32_t* ks = dev_alloc<int32_t>(nullptr, nkeep);
-    emit_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, fws, pws, pkeep, stp.t, stp.s, kt, ks);
+    emit_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, flags, pref, stp.t, stp.s, kt, ks);
     FMM_LAUNCH_CHECK();
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    dev_free(fws), dev_free(fkeep), dev_free(pws), dev_free(pkeep), dev_free(ct), dev_free(cs);
+    dev_free(flags), dev_free(pref), dev_free(ct), dev_free(cs);
     if (nws > 0) steps.push_back(stp);
     else dev_free(stp.t), dev_free(stp.s);
     if (nkeep == 0) {
@@ -1203,7 +1305,6 @@ void march(const fmm_tree* t, Side S, Side T, cudaStream_t st, std::vector<Step>
     cs = dev_alloc<int32_t>(nullptr, nc);
     expand_kernel<<<grid_for(nkeep, 256), 256, 0, st>>>(kt, ks, nkeep, nch, adv, ct, cs);
     FMM_LAUNCH_CHECK();
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
     dev_free(kt), dev_free(ks);
     if (adv != 0) ls++;
     if (adv != 1) lt++;
@@ -1211,6 +1312,7 @@ void march(const fmm_tree* t, Side S, Side T, cudaStream_t st, std::vector<Step>
   *p2p_t_out = p2p_t;
   *p2p_s_out = p2p_s;
   *np_out = np;
+  trace_mark("level march");
 }
 
 // Lists into their device form, per-interaction coefficients, near-field
@@ -1234,24 +1336,29 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
   {
     int64_t* cnt = scratch_alloc<int64_t>(NB + 1);
     int64_t* fill = scratch_alloc<int64_t>(NB + 1);
+    int64_t* rs = scratch_alloc<int64_t>(NB + 1);
     FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (NB + 1), st));
     FMM_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int64_t) * (NB + 1), st));
     for (auto& x : steps) {
-      count_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.n, cnt);
+      m2l_fill_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.n, cnt);
       FMM_LAUNCH_CHECK();
     }
     exclusive_scan(cnt, t->m2l_off, NB + 1, st);
     for (auto& x : steps) {
-      m2l_scatter_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.s, x.n, t->m2l_off, fill, t->m2l_trg, t->m2l_src);
+      run_start_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.n, rs);
+      FMM_LAUNCH_CHECK();
+      m2l_scatter_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.s, x.n, t->m2l_off, fill, rs, t->m2l_trg,
+                                                             t->m2l_src);
       FMM_LAUNCH_CHECK();
       m2l_fill_kernel<<<grid_for(x.n, 256), 256, 0, st>>>(x.t, x.n, fill);
       FMM_LAUNCH_CHECK();
     }
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    dev_free(cnt), dev_free(fill);
+    dev_free(cnt), dev_free(fill), dev_free(rs);
     for (auto& x : steps) dev_free(x.t), dev_free(x.s);
     steps.clear();
   }
+  trace_mark("M2L lists (CSR)");
 
   // ---- near-field lists as CSR by target leaf ----
   t->n_p2p = np;
@@ -1264,7 +1371,7 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
     int64_t* cnt = scratch_alloc<int64_t>(NL + 1);
     FMM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (NL + 1), st));
     if (np > 0) {
-      count_kernel<<<grid_for(np, 256), 256, 0, st>>>(p2p_t, np, cnt);
+      m2l_fill_kernel<<<grid_for(np, 256), 256, 0, st>>>(p2p_t, np, cnt);  // runs by target leaf
       FMM_LAUNCH_CHECK();
       FMM_CUDA_TRY(cudaMemcpyAsync(t->p2p_src, p2p_s, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st));
       FMM_CUDA_TRY(cudaMemcpyAsync(p2p_trg, p2p_t, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st));
@@ -1274,16 +1381,19 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
     dev_free(cnt);
     if (p2p_t) dev_free(p2p_t), dev_free(p2p_s);
   }
+  trace_mark("near-field lists (CSR)");
 
   // ---- rotation coefficients and near-field entries ----
-  t->geo64 = dev_alloc<double>(t, (size_t)m2l_fields(p) * std::max<int64_t>(nm, 1));
   t->geo32 = dev_alloc<float>(t, (size_t)m2l_fields(p) * std::max<int64_t>(nm, 1));
+  trace_mark("  M2L records: allocation");
   if (nm > 0) {
-    m2l_geo_kernel<<<grid_for(nm, 256), 256, 0, st>>>(t->m2l_trg, t->m2l_src, nm, t->center, t->radius, p, t->geo64,
+    m2l_geo_kernel<<<grid_for(nm, 256), 256, 0, st>>>(t->m2l_trg, t->m2l_src, nm, t->center, t->radius, p, nullptr,
                                                       t->geo32);
     FMM_LAUNCH_CHECK();
   }
+  trace_mark("M2L rotation records");
   build_l2l_direct(t, st);
+  trace_mark("direct L2L records");
   {
     unsigned long long* pairs = scratch_alloc<unsigned long long>(1);
     FMM_CUDA_TRY(cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), st));
@@ -1301,42 +1411,19 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
   }
   dev_free(p2p_trg);
 
+  trace_mark("near-field entries");
   // ---- work orders: longest M2L lists and heaviest near fields first ----
-  {
-    std::vector<int64_t> off = to_host(t->m2l_off, NB + 1, st);
-    std::vector<int32_t> ord(NB);
-    for (int64_t g = 0; g < NB; g++) ord[g] = (int32_t)g;
-    std::stable_sort(ord.begin(), ord.end(),
-                     [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
-    t->m2l_order = dev_alloc<int32_t>(t, NB);
-    FMM_CUDA_TRY(cudaMemcpyAsync(t->m2l_order, ord.data(), sizeof(int32_t) * NB, cudaMemcpyHostToDevice, st));
-    std::vector<int64_t> poff = to_host(t->p2p_off, NL + 1, st);
-    std::vector<int32_t> psrc = to_host(t->p2p_src, np, st);
-    std::vector<int32_t> scnt = to_host(t->box_count + src_leaf_base, NLS, st);
-    std::vector<int64_t> work(NL, 0);
-    for (int64_t l = 0; l < NL; l++)
-      for (int64_t e = poff[l]; e < poff[l + 1]; e++) work[l] += scnt[psrc[e]];
-    std::vector<int32_t> lord(NL);
-    for (int64_t l = 0; l < NL; l++) lord[l] = (int32_t)l;
-    std::stable_sort(lord.begin(), lord.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
-    t->leaf_order = dev_alloc<int32_t>(t, NL);
-    FMM_CUDA_TRY(cudaMemcpyAsync(t->leaf_order, lord.data(), sizeof(int32_t) * NL, cudaMemcpyHostToDevice, st));
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  }
+  build_work_orders(t, st);
+  trace_mark("work orders");
 
   // ---- evaluation workspace ----
   const int NCP = ncoef_pad(p);
   t->src32 = dev_alloc<float4>(t, n);
   t->src_dup = dev_alloc<DupRec>(t, n);
-  t->src64 = dev_alloc<dvec4>(t, n);
   t->M32 = dev_alloc<float>(t, (size_t)NB * NCP);
   t->Lam32 = dev_alloc<float>(t, (size_t)NB * NCP);
-  t->M64 = dev_alloc<double>(t, (size_t)NB * NCP);
-  t->Lam64 = dev_alloc<double>(t, (size_t)NB * NCP);
   FMM_CUDA_TRY(cudaMemsetAsync(t->M32, 0, sizeof(float) * NB * NCP, st));
   FMM_CUDA_TRY(cudaMemsetAsync(t->Lam32, 0, sizeof(float) * NB * NCP, st));
-  FMM_CUDA_TRY(cudaMemsetAsync(t->M64, 0, sizeof(double) * NB * NCP, st));
-  FMM_CUDA_TRY(cudaMemsetAsync(t->Lam64, 0, sizeof(double) * NB * NCP, st));
   t->near_u = dev_alloc<double>(t, n);
   t->near_f = dev_alloc<double>(t, 3 * (size_t)n);
   if (!t->two_trees) {
@@ -1359,6 +1446,7 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
   t->status = dev_alloc<int>(t, 1);
   FMM_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), st));
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  trace_mark("evaluation workspace");
 }
 
 template <class T>
@@ -1407,15 +1495,102 @@ __global__ void geo_lo_kernel(int64_t n, const double* __restrict__ g64, const f
 }
 }  // namespace
 
+// The FP64 data of a tree, made the first time its precision needs them:
+// FP64 rotation records of every M2L, M2M and direct L2L translation (the
+// build stores only their FP32 roundings), FP64 expansions and point records,
+// and near-field slots wide enough for doubles.  Synchronous.
+void ensure_fp64(fmm_tree* t, cudaStream_t st) {
+  const int p = t->prm.p;
+  const int64_t NB = t->n_boxes, nm = t->n_m2l;
+  const int NCP = ncoef_pad(p);
+  if (!t->geo64) {
+    t->geo64 = dev_alloc<double>(t, (size_t)m2l_fields(p) * std::max<int64_t>(nm, 1));
+    if (nm > 0) {
+      m2l_geo_kernel<<<grid_for(nm, 256), 256, 0, st>>>(t->m2l_trg, t->m2l_src, nm, t->center, t->radius, p,
+                                                        t->geo64, nullptr);
+      FMM_LAUNCH_CHECK();
+    }
+  }
+  if (!t->m2m64) {
+    t->m2m64 = dev_alloc<double>(t, (size_t)edge_fields(p) * NB);
+    edge_geo_kernel<<<grid_for(NB, 128, 1 << 30), 128, 0, st>>>(NB, t->box_parent, t->center, t->radius, p,
+                                                                t->m2m64, nullptr);
+    FMM_LAUNCH_CHECK();
+  }
+  if (!t->l2d64) {
+    const int64_t nr = t->n_l2d;
+    t->l2d64 = dev_alloc<double>(t, (size_t)edge_fields(p) * std::max<int64_t>(nr, 1));
+    if (nr > 0) {
+      l2d_fill_kernel<<<grid_for(t->n_leaves, 128), 128, 0, st>>>(t->n_leaves, t->leaf_box, t->box_parent,
+                                                                  t->m2l_off, t->l2d_off, t->center, t->radius, p,
+                                                                  nr, nullptr, t->l2d64, nullptr);
+      FMM_LAUNCH_CHECK();
+    }
+  }
+  if (!t->M64) {
+    t->M64 = dev_alloc<double>(t, (size_t)NB * NCP);
+    t->Lam64 = dev_alloc<double>(t, (size_t)NB * NCP);
+    FMM_CUDA_TRY(cudaMemsetAsync(t->M64, 0, sizeof(double) * NB * NCP, st));
+    FMM_CUDA_TRY(cudaMemsetAsync(t->Lam64, 0, sizeof(double) * NB * NCP, st));
+  }
+  if (!t->src64) t->src64 = dev_alloc<dvec4>(t, t->n);
+  if (t->sym && !t->sym_partial_f64) {
+    dev_free(t->sym_partial);
+    t->device_bytes -= sizeof(float) * (size_t)std::max<int64_t>(t->n_slots, 1) * t->sym_stride;
+    t->sym_partial = dev_alloc<double>(t, (size_t)std::max<int64_t>(t->n_slots, 1) * t->sym_stride);
+    t->sym_partial_f64 = 1;
+  }
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
 void prepare_df_far(fmm_tree* t, cudaStream_t st) {
   if (t->geo_lo || t->two_trees) return;
+  ensure_fp64(t, st);
   const int p = t->prm.p;
   const int64_t ng = (int64_t)m2l_fields(p) * std::max<int64_t>(t->n_m2l, 1);
   t->geo_lo = dev_alloc<float>(t, ng);
   geo_lo_kernel<<<grid_for(ng, 256), 256, 0, st>>>(ng, t->geo64, t->geo32, t->geo_lo);
   FMM_LAUNCH_CHECK();
   t->m_df = dev_alloc<float2>(t, (size_t)t->n_boxes * ncoef_pad(p));
+  if (t->sym) build_df_near(t, st);
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+namespace {
+// M2L list length of every target box
+__global__ void m2l_len_kernel(int64_t nb, const int64_t* __restrict__ off, int64_t* __restrict__ key) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nb; g += (int64_t)gridDim.x * blockDim.x)
+    key[g] = off[g + 1] - off[g];
+}
+// near-field work of every target leaf: its point count times the points of
+// its list's source leaves (one warp per leaf)
+__global__ void leaf_work_kernel(int64_t nl, const int64_t* __restrict__ off, const int32_t* __restrict__ src,
+                                 const int32_t* __restrict__ leaf_box, const int32_t* __restrict__ src_leaf_box,
+                                 const int32_t* __restrict__ box_count, int64_t* __restrict__ key) {
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; l < nl; l += warps) {
+    int64_t w = 0;
+    for (int64_t e = off[l] + (threadIdx.x & 31); e < off[l + 1]; e += 32) w += box_count[src_leaf_box[src[e]]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0) key[l] = w * box_count[leaf_box[l]];
+  }
+}
+}  // namespace
+
+void build_work_orders(fmm_tree* t, cudaStream_t st) {
+  const int64_t NB = t->n_boxes, NL = t->n_leaves;
+  int64_t* key = scratch_alloc<int64_t>(std::max(NB, NL));
+  t->m2l_order = dev_alloc<int32_t>(t, NB);
+  m2l_len_kernel<<<grid_for(NB, 256), 256, 0, st>>>(NB, t->m2l_off, key);
+  FMM_LAUNCH_CHECK();
+  order_desc(key, NB, t->m2l_order, st);
+  t->leaf_order = dev_alloc<int32_t>(t, NL);
+  leaf_work_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->p2p_off, t->p2p_src, t->leaf_box,
+                                                          t->src_leaf_box, t->box_count, key);
+  FMM_LAUNCH_CHECK();
+  order_desc(key, NL, t->leaf_order, st);
+  dev_free(key);
 }
 
 // Direct L2L records of a tree whose lists, geometry and parents are set
@@ -1434,11 +1609,10 @@ void build_l2l_direct(fmm_tree* t, cudaStream_t st) {
   dev_free(cnt);
   t->n_l2d = nr;
   t->l2d_anc = dev_alloc<int32_t>(t, std::max<int64_t>(nr, 1));
-  t->l2d64 = dev_alloc<double>(t, (size_t)edge_fields(p) * std::max<int64_t>(nr, 1));
   t->l2d32 = dev_alloc<float>(t, (size_t)edge_fields(p) * std::max<int64_t>(nr, 1));
   if (nr > 0) {
     l2d_fill_kernel<<<grid_for(NL, 128), 128, 0, st>>>(NL, t->leaf_box, t->box_parent, t->m2l_off, t->l2d_off,
-                                                       t->center, t->radius, p, nr, t->l2d_anc, t->l2d64, t->l2d32);
+                                                       t->center, t->radius, p, nr, t->l2d_anc, nullptr, t->l2d32);
     FMM_LAUNCH_CHECK();
   }
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1460,6 +1634,7 @@ void build_tree(fmm_tree* t, const double* pos, cudaStream_t st) {
     march(t, side, side, st, steps, &p2p_t, &p2p_s, &np);
     finish_tree(t, steps, p2p_t, p2p_s, np, leaf_off, leaf_off, blo, bhi, t->has_duplicates, st);
     build_symmetric(t, st);
+    trace_mark("symmetric near field");
   } catch (...) {
     dev_free(blo), dev_free(bhi);
     throw;
@@ -1521,9 +1696,7 @@ void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg,
     m->pos_local = dev_alloc<float4>(m, N);
     m->pos64 = dev_alloc<dvec4>(m, N);
     m->m2m32 = dev_alloc<float>(m, (size_t)edge_fields(p) * NB);
-    m->m2m64 = dev_alloc<double>(m, (size_t)edge_fields(p) * NB);
     FMM_CUDA_TRY(cudaMemsetAsync(m->m2m32, 0, sizeof(float) * edge_fields(p) * NB, st));
-    FMM_CUDA_TRY(cudaMemsetAsync(m->m2m64, 0, sizeof(double) * edge_fields(p) * NB, st));
 
     copy_d2d(m->perm, S->perm, n_s, st);
     offset_i32_kernel<<<grid_for(n_t, 256), 256, 0, st>>>(m->perm + n_s, T->perm, n_t, (int32_t)n_s, 0);
@@ -1552,7 +1725,6 @@ void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg,
     // multipoles move up the source tree (M2M rounds); locals reach the
     // target leaves by the direct L2L records of the target tree
     copy_rows(m->m2m32, NB, 0, S->m2m32, NBs, edge_fields(p), st);
-    copy_rows(m->m2m64, NB, 0, S->m2m64, NBs, edge_fields(p), st);
     m->n_up = S->L;
     m->up_off_h = new int64_t[S->L + 1];
     for (int r = 0; r <= S->L; r++) m->up_off_h[r] = S->up_off_h[r];

@@ -14,8 +14,12 @@ torch = pytest.importorskip("torch")
 
 TOL_FP64 = 1e-12
 TOL_FP64_FIELD = 1e-11
-TOL_FP32 = 3e-6
-TOL_FP32_FIELD = 3e-5
+# FP32C bars as for one tree (the budget of the single-tree parity tests):
+# potentials 1e-6 on these well-spread sets (measured up to 5.0e-7, the
+# few-target and far-target cases, whose potentials are the smallest), fields
+# 1e-5 (measured up to 6.0e-6)
+TOL_FP32 = 1e-6
+TOL_FP32_FIELD = 1e-5
 
 
 @pytest.fixture(scope="module")
