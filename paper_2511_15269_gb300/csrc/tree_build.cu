@@ -361,13 +361,15 @@ __global__ void __launch_bounds__(kThreads) partition_kernel(const double* __res
 // ---- small segments: all remaining rounds and the leaf sort in one CTA ---------
 constexpr int kSmallThreads = 512;
 
-__device__ void bitonic_sort(unsigned long long* kh, unsigned long long* kl, int size) {
-  for (int k = 2; k <= size; k <<= 1) {
+// Bitonic sort of the `total / sub` consecutive blocks of `sub` keys (sub a
+// power of two dividing total), each ascending in (kh, kl).
+__device__ void bitonic_sort_blocks(unsigned long long* kh, unsigned long long* kl, int total, int sub) {
+  for (int k = 2; k <= sub; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < size; i += blockDim.x) {
+      for (int i = threadIdx.x; i < total; i += blockDim.x) {
         const int ixj = i ^ j;
         if (ixj > i) {
-          const bool asc = (i & k) == 0;
+          const bool asc = k == sub || (i & k) == 0;
           const bool gt = (kh[i] > kh[ixj]) || (kh[i] == kh[ixj] && kl[i] > kl[ixj]);
           if (gt == asc) {
             unsigned long long t = kh[i];
@@ -390,8 +392,6 @@ __global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
   extern __shared__ __align__(16) unsigned char sm[];
   const int64_t g0 = starts[blockIdx.x], g1 = starts[blockIdx.x + 1];
   const int cnt = (int)(g1 - g0);
-  int size = 1;
-  while (size < cnt) size <<= 1;
   const int nsub_max = 1 << rounds;
   // 8-byte items first, then 4-byte ones
   unsigned long long* kh = reinterpret_cast<unsigned long long*>(sm);
@@ -443,28 +443,36 @@ __global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
       axis[j] = ax;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < size; i += blockDim.x) {
-      if (i < cnt) {
-        int lo = 0, hi = nsub - 1;
-        while (lo < hi) {
-          int mid = (lo + hi + 1) >> 1;
-          if (st[mid] <= i) lo = mid;
-          else hi = mid - 1;
-        }
-        unsigned long long k = okey(xa[axis[lo] * kSmallCap + i]);
-        kh[i] = ((unsigned long long)lo << 52) | (k >> 12);
-        kl[i] = ((k & 0xfffull) << 44) | ((unsigned long long)(uint32_t)ia[i] << 12) | (unsigned long long)i;
-      } else {
-        kh[i] = ~0ull;
-        kl[i] = ~0ull;
-      }
+    // each sub-segment sorted on its own: (key on its axis, original index,
+    // position), in blocks of `sub` slots (the largest sub-segment, rounded
+    // up to a power of two; nsub * sub <= kSmallCap)
+    int sub = 1;
+    while (sub < (cnt + nsub - 1) / nsub) sub <<= 1;
+    for (int i = threadIdx.x; i < nsub * sub; i += blockDim.x) {
+      kh[i] = ~0ull;
+      kl[i] = ~0ull;
     }
     __syncthreads();
-    bitonic_sort(kh, kl, size);
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const int slot = (int)(kl[i] & 0xfffull);
-      for (int a = 0; a < 3; a++) xb[a * kSmallCap + i] = xa[a * kSmallCap + slot];
-      ib[i] = ia[slot];
+      int lo = 0, hi = nsub - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (st[mid] <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      const int slot = lo * sub + (i - st[lo]);
+      kh[slot] = okey(xa[axis[lo] * kSmallCap + i]);
+      kl[slot] = ((unsigned long long)(uint32_t)ia[i] << 12) | (unsigned long long)i;
+    }
+    __syncthreads();
+    bitonic_sort_blocks(kh, kl, nsub * sub, sub);
+    for (int i = threadIdx.x; i < nsub * sub; i += blockDim.x) {
+      const int j = i / sub, k = i - j * sub;
+      if (k < st[j + 1] - st[j]) {
+        const int from = (int)(kl[i] & 0xfffull), to = st[j] + k;
+        for (int ax = 0; ax < 3; ax++) xb[ax * kSmallCap + to] = xa[ax * kSmallCap + from];
+        ib[to] = ia[from];
+      }
     }
     __syncthreads();
     {
@@ -486,29 +494,36 @@ __global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
     }
     __syncthreads();
   }
-  // leaves in ascending original index (Listing 2, last line)
+  // leaves in ascending original index (Listing 2, last line), each leaf
+  // sorted on its own in a block of `sub` slots
   const int nleaf = 1 << rounds;
-  for (int i = threadIdx.x; i < size; i += blockDim.x) {
-    if (i < cnt) {
-      int lo = 0, hi = nleaf - 1;
-      while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (st[mid] <= i) lo = mid;
-        else hi = mid - 1;
-      }
-      kh[i] = ((unsigned long long)lo << 32) | (unsigned long long)(uint32_t)ia[i];
-      kl[i] = (unsigned long long)i;
-    } else {
-      kh[i] = ~0ull;
-      kl[i] = ~0ull;
-    }
+  int sub = 1;
+  while (sub < (cnt + nleaf - 1) / nleaf) sub <<= 1;
+  for (int i = threadIdx.x; i < nleaf * sub; i += blockDim.x) {
+    kh[i] = ~0ull;
+    kl[i] = ~0ull;
   }
   __syncthreads();
-  bitonic_sort(kh, kl, size);
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    const int slot = (int)kl[i];
-    for (int a = 0; a < 3; a++) Xo[a * n + g0 + i] = xa[a * kSmallCap + slot];
-    perm[g0 + i] = ia[slot];
+    int lo = 0, hi = nleaf - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (st[mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const int slot = lo * sub + (i - st[lo]);
+    kh[slot] = (unsigned long long)(uint32_t)ia[i];
+    kl[slot] = (unsigned long long)i;
+  }
+  __syncthreads();
+  bitonic_sort_blocks(kh, kl, nleaf * sub, sub);
+  for (int i = threadIdx.x; i < nleaf * sub; i += blockDim.x) {
+    const int j = i / sub, k = i - j * sub;
+    if (k < st[j + 1] - st[j]) {
+      const int from = (int)kl[i], to = st[j] + k;
+      for (int ax = 0; ax < 3; ax++) Xo[ax * n + g0 + to] = xa[ax * kSmallCap + from];
+      perm[g0 + to] = ia[from];
+    }
   }
 }
 
@@ -667,14 +682,51 @@ __device__ __forceinline__ bool well_separated(const double* __restrict__ c, con
   return d > 0.0 && lhs <= rhs;
 }
 
+// Box centres as double-float pairs (hi, lo per coordinate) and radii in
+// FP32, for the FP32 pre-test of Eq. 4 below.
+__global__ void centre_pairs_kernel(int64_t nb, const double* __restrict__ center, const double* __restrict__ radius,
+                                    float* __restrict__ cf, float* __restrict__ rf) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nb; g += (int64_t)gridDim.x * blockDim.x) {
+    for (int a = 0; a < 3; a++) {
+      const double c = center[3 * g + a];
+      const float h = (float)c;
+      cf[6 * g + a] = h;
+      cf[6 * g + 3 + a] = (float)(c - (double)h);
+    }
+    rf[g] = (float)radius[g];
+  }
+}
+
 // Eq. 4 on every candidate pair; the two flags (well separated, kept) are
 // packed as ws + (keep << 32) so that one scan yields both prefix counts
-// (each stays below 2^32).
+// (each stays below 2^32).  The test is decided in FP32 when its two sides
+// differ by far more than the FP32 evaluation can be off (relative 1e-5
+// against a bound of about 1e-6, plus the double-float centres' absolute
+// error); the remaining near-ties, zero distances and huge coordinate
+// ranges take the FP64 sequence that the oracle uses, so every decision is
+// the FP64 one.
 __global__ void ws_kernel(const int32_t* __restrict__ ct, const int32_t* __restrict__ cs, int64_t nc,
                           int64_t offt, int64_t offs, const double* __restrict__ center,
-                          const double* __restrict__ radius, double theta, int64_t* __restrict__ flags) {
+                          const double* __restrict__ radius, const float* __restrict__ cf,
+                          const float* __restrict__ rf, double theta, int64_t* __restrict__ flags) {
+  const float thf = (float)theta;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
-    const bool w = well_separated(center, radius, offs + cs[e], offt + ct[e], theta);
+    const int64_t gs = offs + cs[e], gt = offt + ct[e];
+    const float* a = cf + 6 * gs;
+    const float* b = cf + 6 * gt;
+    const float dx = (a[0] - b[0]) + (a[3] - b[3]);
+    const float dy = (a[1] - b[1]) + (a[4] - b[4]);
+    const float dz = (a[2] - b[2]) + (a[5] - b[5]);
+    const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    const float ra = rf[gs], rb = rf[gt];
+    const float R = fmaxf(ra, rb), r = fminf(ra, rb);
+    const float lhs = fmaf(thf, r, R), rhs = thf * d;
+    const float mag = fabsf(a[0]) + fabsf(a[1]) + fabsf(a[2]) + fabsf(b[0]) + fabsf(b[1]) + fabsf(b[2]);
+    const float guard = 1e-5f * (lhs + rhs) + 1e-12f * mag;
+    bool w;
+    if (d > 0.f && lhs + guard < rhs) w = true;
+    else if (d > 0.f && lhs > rhs + guard) w = false;
+    else w = well_separated(center, radius, gs, gt, theta);
     flags[e] = w ? 1 : ((int64_t)1 << 32);
   }
 }
@@ -820,6 +872,19 @@ __global__ void m2l_geo_kernel(const int32_t* __restrict__ mt, const int32_t* __
     const int64_t gt = mt[e], gs = ms[e];
     const double t[3] = {center[3 * gs] - center[3 * gt], center[3 * gs + 1] - center[3 * gt + 1],
                          center[3 * gs + 2] - center[3 * gt + 2]};
+    if (!g64) {
+      // FP32 records only: t in FP64 (a difference of nearby centres), the
+      // rest in FP32 (a few roundings, like the records' own rounding)
+      const float tx = (float)t[0], ty = (float)t[1], tz = (float)t[2];
+      const float rxy = sqrtf(fmaf(tx, tx, ty * ty));
+      const float r = sqrtf(fmaf(rxy, rxy, tz * tz));
+      const float ri = 1.0f / r;
+      const float rxyi = rxy > 0.f ? 1.0f / rxy : 0.f;
+      const float vals[7] = {ri, (float)radius[gs] * ri, (float)radius[gt] * ri, rxy > 0.f ? tx * rxyi : 1.f,
+                             rxy > 0.f ? ty * rxyi : 0.f, r > 0.f ? tz * ri : 1.f, r > 0.f ? rxy * ri : 0.f};
+      for (int k = 0; k < 7; k++) g32[k * nm + e] = vals[k];
+      continue;
+    }
     const double rxy = sqrt(t[0] * t[0] + t[1] * t[1]);
     const double r = sqrt(rxy * rxy + t[2] * t[2]);
     double ct = 1.0, st = 0.0, cp = 1.0, sp = 0.0;
@@ -1261,12 +1326,17 @@ void march(const fmm_tree* t, Side S, Side T, cudaStream_t st, std::vector<Step>
   int64_t np = 0;
   const bool tie_target = (t->prm.flags & FMM_TIE_TARGET) != 0;
   const bool same_level = (t->prm.flags & FMM_SAME_LEVEL) != 0;
+  float* cf = scratch_alloc<float>(6 * (size_t)t->n_boxes);
+  float* rf = scratch_alloc<float>(t->n_boxes);
+  centre_pairs_kernel<<<grid_for(t->n_boxes, 256), 256, 0, st>>>(t->n_boxes, t->center, t->radius, cf, rf);
+  FMM_LAUNCH_CHECK();
   for (;;) {
     require(nc < ((int64_t)1 << 32), "too many candidate pairs in one level-march step");
     int64_t* flags = scratch_alloc<int64_t>(nc);
     int64_t* pref = scratch_alloc<int64_t>(nc);
     const int64_t offt = T.base + level_offset(lt, s), offs = S.base + level_offset(ls, s);
-    ws_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, t->center, t->radius, t->prm.theta, flags);
+    ws_kernel<<<grid_for(nc, 256), 256, 0, st>>>(ct, cs, nc, offt, offs, t->center, t->radius, cf, rf,
+                                                 t->prm.theta, flags);
     FMM_LAUNCH_CHECK();
     const int64_t both = exclusive_scan(flags, pref, nc, st);
     const int64_t nws = both & 0xffffffffll, nkeep = both >> 32;
@@ -1309,6 +1379,7 @@ void march(const fmm_tree* t, Side S, Side T, cudaStream_t st, std::vector<Step>
     if (adv != 0) ls++;
     if (adv != 1) lt++;
   }
+  dev_free(cf), dev_free(rf);
   *p2p_t_out = p2p_t;
   *p2p_s_out = p2p_s;
   *np_out = np;
