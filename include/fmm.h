@@ -73,12 +73,15 @@ enum {
   FMM_TIE_TARGET = 1, /* equal average radii advance the target level (the
                          same-vs-cross table of Sec. II.B) instead of the source
                          level (the text of Sec. II.B, the default)            */
-  FMM_SAME_LEVEL = 2  /* same-level lists (Sec. II.B, steps 1-3): source and
+  FMM_SAME_LEVEL = 2, /* same-level lists (Sec. II.B, steps 1-3): source and
                          target descend together and only boxes of one level
                          are compared; no cross-level M2L pairs.  Overrides
                          FMM_TIE_TARGET.  More M2L work than the default
                          level march (the same-vs-cross table of Sec. II.B);
                          kept for comparison                                   */
+  FMM_POS_SOA = 4     /* positions passed to the build calls are three arrays
+                         of n doubles (all x, then all y, then all z) instead
+                         of n rows of (x, y, z); the hierarchy is the same    */
 };
 
 #define FMM_MAX_P 10 /* largest supported expansion order */
@@ -91,7 +94,8 @@ typedef struct {
   int splits;     /* s: bisections per level, 2^s children per box, 1..3        */
   double theta;   /* well-separation parameter of Eq. 4, 0 < theta < 1          */
   int precision;  /* FMM_FP64, FMM_FP32C or FMM_FP64DF, used by evaluations     */
-  int flags;      /* 0 or a combination of FMM_TIE_TARGET, FMM_SAME_LEVEL      */
+  int flags;      /* 0 or a combination of FMM_TIE_TARGET, FMM_SAME_LEVEL,
+                     FMM_POS_SOA                                                 */
 } fmm_params;
 
 typedef struct fmm_tree fmm_tree;
@@ -168,7 +172,9 @@ int fmm_num_levels(int64_t n, int leaf_size, int splits);
  * L2L translations from each leaf's ancestors with M2L sums straight to the
  * leaf (the level-by-level L2L chain applied in one step; FP64, also stored
  * rounded to FP32).  -0.0 coordinates are treated as +0.0.
- *   pos     device, n x 3 doubles, read only during the call
+ *   pos     device, n x 3 doubles (x, y, z per point; with FMM_POS_SOA in
+ *           params->flags: x[0..n), y[0..n), z[0..n)), read only during the
+ *           call
  *   n       >= 1 points (< 2^31)
  *   params  host pointer, copied
  *   stream  work is enqueued on it; the call synchronises it before returning
@@ -282,6 +288,38 @@ int fmm_eval_potential(const fmm_tree* tree, const double* q, double* u, void* s
  * L2P uses the gradient of the regular basis (App. A.3). */
 int fmm_eval_field(const fmm_tree* tree, const double* q, double* u, double* field,
                    void* stream);
+
+/* Batched charge sets (the batch form of the evaluation; the paper
+ * evaluates one charge set per call, Sec. III.A): the potentials of n_sets
+ * independent charge sets in one evaluation of a batch tree made by
+ * fmm_tree_merge from n_sets trees.  q_sets and u_sets are HOST arrays of
+ * n_sets DEVICE pointers; set k has offsets[k + 1] - offsets[k] points
+ * (fmm_tree_point_offsets), in its own tree's point order.  The charges are
+ * gathered into the batch's order and the potentials scattered back by
+ * kernels that take the pointers as launch arguments (no host-to-device
+ * copy, so the call can be captured in a CUDA graph).  n_sets must equal
+ * the batch's tree count (1 for a plain tree).  Errors:
+ * FMM_ERR_INVALID_ARG, FMM_ERR_CUDA. */
+int fmm_eval_batched(const fmm_tree* batch, int n_sets, const double* const* q_sets, double* const* u_sets,
+                     void* stream);
+
+/* Evaluation workspace (Sec. III.A evaluations reuse one hierarchy; the
+ * per-call scratch is separate from it): the buffers every evaluation of the
+ * tree overwrites (tree-ordered point records, near-field sums and slots,
+ * expansions, staging buffers, work counters) for the precisions selected so
+ * far.  fmm_tree_workspace_bytes gives their size (host *bytes); a caller
+ * that keeps device memory in its own allocator passes a buffer of at least
+ * that size (device, 256-byte aligned) to fmm_tree_set_workspace, and the
+ * tree releases its own buffers and uses the caller's for every later
+ * evaluation; the caller keeps it valid until the tree is freed or another
+ * workspace (or NULL: the tree's own again) is set.  Selecting a precision
+ * that needs more workspace (FMM_FP64 or FMM_FP64DF for the first time)
+ * requires the caller's workspace to be detached first.  The call
+ * synchronises the device.  Errors: FMM_ERR_INVALID_ARG (NULL tree,
+ * misaligned buffer), FMM_ERR_CAPACITY (buffer too small), FMM_ERR_OOM,
+ * FMM_ERR_CUDA. */
+int fmm_tree_workspace_bytes(const fmm_tree* tree, size_t* bytes);
+int fmm_tree_set_workspace(fmm_tree* tree, void* workspace, size_t ws_bytes);
 
 /* Same as fmm_eval_potential with HOST buffers: copies q to the device,
  * evaluates, copies u back and synchronises `stream`.  Pinned host memory

@@ -33,6 +33,83 @@ __global__ void backward_combine_kernel(int64_t n, const double* __restrict__ q,
     for (int a = 0; a < 3; a++) out[3 * i + a] = -(g[i] * eq[3 * i + a] + q[i] * eg[3 * i + a]);
 }
 
+// Evaluation workspace of a tree: the buffers every evaluation overwrites
+// (point records, near-field sums and slots, expansions, staging buffers,
+// work counters), for the precisions prepared so far.
+struct WsItem {
+  void** ptr;
+  size_t bytes;
+};
+std::vector<WsItem> ws_items(fmm_tree* t) {
+  const int64_t n = t->n, NB = t->n_boxes;
+  const size_t NCP = (size_t)ncoef_pad(t->prm.p);
+  std::vector<WsItem> v;
+  auto add = [&](void* field_addr, size_t bytes) {
+    void** f = reinterpret_cast<void**>(field_addr);
+    if (*f) v.push_back(WsItem{f, bytes});
+  };
+  add(&t->src32, sizeof(float4) * n);
+  add(&t->src_dup, sizeof(DupRec) * n);
+  add(&t->src64, sizeof(dvec4) * n);
+  add(&t->near_u, sizeof(double) * n);
+  add(&t->near_f, sizeof(double) * 3 * n);
+  add(&t->M32, sizeof(float) * NB * NCP);
+  add(&t->Lam32, sizeof(float) * NB * NCP);
+  add(&t->M64, sizeof(double) * NB * NCP);
+  add(&t->Lam64, sizeof(double) * NB * NCP);
+  add(&t->m_df, sizeof(float2) * NB * NCP);
+  add(&t->sym_partial, (t->sym_partial_f64 ? sizeof(double) : sizeof(float)) *
+                           (size_t)std::max<int64_t>(t->n_slots, 1) * std::max(t->sym_stride, 1));
+  add(&t->src_dup2, sizeof(DupRec) * n);
+  add(&t->near_u2, sizeof(float) * 2 * n);
+  add(&t->near_f2, sizeof(float) * 3 * n);
+  add(&t->q_stage, sizeof(double) * n);
+  add(&t->u_stage, sizeof(double) * n);
+  add(&t->f_stage, sizeof(double) * 3 * n);
+  add(&t->g_stage, sizeof(double) * 3 * n);
+  add(&t->counters, sizeof(int) * 8);
+  return v;
+}
+size_t ws_bytes(const std::vector<WsItem>& v) {
+  size_t b = 0;
+  for (auto& w : v) b += (w.bytes + 255) & ~(size_t)255;
+  return b;
+}
+
+// Batched charge sets: per-set pointers passed by value (up to kBatchPtrs
+// sets per launch).
+constexpr int kBatchPtrs = 256;
+struct SetPtrs {
+  const double* p[kBatchPtrs];
+  int64_t off[kBatchPtrs + 1];  // set k: points off[k] .. off[k + 1] - 1 of the batch
+};
+__global__ void batch_gather_kernel(SetPtrs sp, int nsets, double* __restrict__ dst) {
+  const int64_t base = sp.off[0];
+  const int64_t total = sp.off[nsets] - base;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sp.off[mid] - base <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    dst[base + i] = sp.p[lo][base + i - sp.off[lo]];
+  }
+}
+__global__ void batch_scatter_kernel(SetPtrs sp, int nsets, const double* __restrict__ src) {
+  const int64_t base = sp.off[0];
+  const int64_t total = sp.off[nsets] - base;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sp.off[mid] - base <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const_cast<double*>(sp.p[lo])[base + i - sp.off[lo]] = src[base + i];
+  }
+}
+
 void eval_any(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
   if (t->prm.precision == FMM_FP32C) eval_fp32(t, q, u, field, st);
   else eval_fp64(t, q, u, field, st);
@@ -172,16 +249,18 @@ void* tracked_malloc(size_t bytes) {
 
 void dev_free(void* p) {
   if (!p) return;
-  bool pooled = false;
+  bool pooled = false, tracked = false;
   {
     std::lock_guard<std::mutex> lk(g_mem_mu);
     auto it = g_live.find(p);
     if (it != g_live.end()) {
       g_live_bytes -= it->second.bytes;
       pooled = it->second.pooled;
+      tracked = true;
       g_live.erase(it);
     }
   }
+  if (!tracked) return;  // not the library's (a caller's workspace)
   // stream-ordered inside a build (the memory is reused once the work queued
   // before the free has run); otherwise after the device is idle
   if (pooled) cudaFreeAsync(p, tl_alloc_pool ? tl_alloc_stream : nullptr);
@@ -254,7 +333,7 @@ int fmm_build_tree(const double* pos, int64_t n, const fmm_params* params, void*
     require(p.theta > 0.0 && p.theta < 1.0, "theta must be in (0, 1)");
     require(p.precision == FMM_FP64 || p.precision == FMM_FP32C || p.precision == FMM_FP64DF,
             "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
-    require((p.flags & ~(FMM_TIE_TARGET | FMM_SAME_LEVEL)) == 0, "unknown flags");
+    require((p.flags & ~(FMM_TIE_TARGET | FMM_SAME_LEVEL | FMM_POS_SOA)) == 0, "unknown flags");
     auto t0 = std::chrono::steady_clock::now();
     TraceScope trace((cudaStream_t)stream);
     AllocScope scratch((cudaStream_t)stream);
@@ -293,7 +372,8 @@ int fmm_build_tree2(const double* src_pos, int64_t n_src, const double* trg_pos,
     require(p.theta > 0.0 && p.theta < 1.0, "theta must be in (0, 1)");
     require(p.precision == FMM_FP64 || p.precision == FMM_FP32C || p.precision == FMM_FP64DF,
             "precision must be FMM_FP64, FMM_FP32C or FMM_FP64DF");
-    require((p.flags & ~FMM_TIE_TARGET) == 0, "flags must be 0 or FMM_TIE_TARGET for two hierarchies");
+    require((p.flags & ~(FMM_TIE_TARGET | FMM_POS_SOA)) == 0,
+            "flags must be 0 or FMM_TIE_TARGET (with or without FMM_POS_SOA) for two hierarchies");
     auto t0 = std::chrono::steady_clock::now();
     TraceScope trace((cudaStream_t)stream);
     AllocScope scratch((cudaStream_t)stream);
@@ -482,6 +562,86 @@ int fmm_eval_field(const fmm_tree* t, const double* q, double* u, double* field,
   return guarded([&] {
     require(t != nullptr && q != nullptr && field != nullptr, "NULL argument");
     eval_any(t, q, u, field, (cudaStream_t)stream);
+  });
+}
+
+int fmm_tree_workspace_bytes(const fmm_tree* t, size_t* bytes) {
+  return guarded([&] {
+    require(t != nullptr && bytes != nullptr, "NULL argument");
+    *bytes = ws_bytes(ws_items(const_cast<fmm_tree*>(t)));
+  });
+}
+
+int fmm_tree_set_workspace(fmm_tree* t, void* workspace, size_t ws_bytes_given) {
+  return guarded([&] {
+    require(t != nullptr, "tree is NULL");
+    FMM_CUDA_TRY(cudaDeviceSynchronize());  // no evaluation may still use the old buffers
+    std::vector<WsItem> items = ws_items(t);
+    if (workspace == nullptr) {
+      if (!t->ws_external) return;
+      // the tree's own buffers again
+      for (auto& w : items) {
+        *w.ptr = tracked_malloc(w.bytes);
+        t->device_bytes += w.bytes;
+      }
+      t->ws_external = 0;
+      FMM_CUDA_TRY(cudaMemsetAsync(t->counters, 0, sizeof(int) * 8, 0));
+      FMM_CUDA_TRY(cudaStreamSynchronize(0));
+      return;
+    }
+    const size_t need = ws_bytes(items);
+    if (ws_bytes_given < need) {
+      set_error("workspace of %zu bytes is too small: this tree needs %zu (fmm_tree_workspace_bytes)",
+                ws_bytes_given, need);
+      throw Fail{FMM_ERR_CAPACITY};
+    }
+    require(((uintptr_t)workspace & 255) == 0, "workspace must be 256-byte aligned");
+    unsigned char* base = static_cast<unsigned char*>(workspace);
+    size_t off = 0;
+    for (auto& w : items) {
+      if (!t->ws_external) {
+        dev_free(*w.ptr);
+        t->device_bytes -= w.bytes;
+      }
+      *w.ptr = base + off;
+      off += (w.bytes + 255) & ~(size_t)255;
+    }
+    t->ws_external = 1;
+    FMM_CUDA_TRY(cudaMemsetAsync(t->counters, 0, sizeof(int) * 8, 0));
+    FMM_CUDA_TRY(cudaStreamSynchronize(0));
+  });
+}
+
+int fmm_eval_batched(const fmm_tree* t, int n_sets, const double* const* q_sets, double* const* u_sets,
+                     void* stream) {
+  return guarded([&] {
+    require(t != nullptr && q_sets != nullptr && u_sets != nullptr, "NULL argument");
+    require(!t->two_trees, "fmm_eval_batched takes batches of one-point-set trees");
+    const int nt = t->n_trees;
+    require(n_sets == nt, "n_sets must equal the number of trees of the batch");
+    for (int k = 0; k < nt; k++) require(q_sets[k] != nullptr && u_sets[k] != nullptr, "NULL set pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto off = [&](int k) -> int64_t {
+      return t->tree_point_off_h ? t->tree_point_off_h[k] : (k == 0 ? 0 : t->n);
+    };
+    for (int k0 = 0; k0 < nt; k0 += kBatchPtrs) {
+      const int m = std::min(kBatchPtrs, nt - k0);
+      SetPtrs sp;
+      for (int k = 0; k < m; k++) sp.p[k] = q_sets[k0 + k];
+      for (int k = 0; k <= m; k++) sp.off[k] = off(k0 + k);
+      batch_gather_kernel<<<grid_for(sp.off[m] - sp.off[0], 256), 256, 0, st>>>(sp, m, t->q_stage);
+      FMM_LAUNCH_CHECK();
+    }
+    eval_any(t, t->q_stage, t->u_stage, nullptr, st);
+    for (int k0 = 0; k0 < nt; k0 += kBatchPtrs) {
+      const int m = std::min(kBatchPtrs, nt - k0);
+      SetPtrs sp;
+      for (int k = 0; k < m; k++) sp.p[k] = u_sets[k0 + k];
+      for (int k = 0; k <= m; k++) sp.off[k] = off(k0 + k);
+      batch_scatter_kernel<<<grid_for(sp.off[m] - sp.off[0], 256), 256, 0, st>>>(sp, m, t->u_stage);
+      FMM_LAUNCH_CHECK();
+    }
+    t->launches += 2 * ((nt + kBatchPtrs - 1) / kBatchPtrs);
   });
 }
 

@@ -227,6 +227,7 @@ struct fmm_tree {
   double* g_stage = nullptr;     // 3 n (backward)
   int* counters = nullptr;       // work counters, reset before each launch
   int* status = nullptr;         // latched kernel status bits
+  int ws_external = 0;           // the evaluation workspace is the caller's (fmm_tree_set_workspace)
   long long wait_cycles = fmm::kDefaultWaitCycles;  // near-field tile wait limit
 
   // far-field stages run on a second, higher-priority stream forked from

@@ -68,12 +68,14 @@ __device__ __forceinline__ int seg_of(const int64_t* starts, int nseg, int64_t i
 }
 
 // ---- input: SoA copy with -0.0 -> +0.0, finiteness check ----------------------
-__global__ void canon_kernel(const double* __restrict__ pos, int64_t n, double* __restrict__ X,
+// soa: positions given as three arrays of n (x, then y, then z) instead of
+// n rows of (x, y, z)
+__global__ void canon_kernel(const double* __restrict__ pos, int64_t n, int soa, double* __restrict__ X,
                              int32_t* __restrict__ idx, int* __restrict__ bad) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     for (int a = 0; a < 3; a++) {
-      double v = __dadd_rn(pos[3 * i + a], 0.0);
+      double v = __dadd_rn(soa ? pos[a * n + i] : pos[3 * i + a], 0.0);
       if (!isfinite(v)) atomicOr(bad, 1);
       X[a * n + i] = v;
     }
@@ -1108,7 +1110,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   int32_t* Ib = scratch_alloc<int32_t>(n);
   int* flag = scratch_alloc<int>(4);
   FMM_CUDA_TRY(cudaMemsetAsync(flag, 0, 4 * sizeof(int), st));
-  canon_kernel<<<grid_for(n, 256), 256, 0, st>>>(pos, n, Xa, Ia, flag);
+  canon_kernel<<<grid_for(n, 256), 256, 0, st>>>(pos, n, (t->prm.flags & FMM_POS_SOA) ? 1 : 0, Xa, Ia, flag);
   FMM_LAUNCH_CHECK();
   int hflag = 0;
   FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1598,6 +1600,10 @@ void ensure_fp64(fmm_tree* t, cudaStream_t st) {
       FMM_LAUNCH_CHECK();
     }
   }
+  const bool more_ws = !t->M64 || !t->src64 || (t->sym && !t->sym_partial_f64);
+  require(!(more_ws && t->ws_external),
+          "this precision needs a larger evaluation workspace: detach the caller's workspace "
+          "(fmm_tree_set_workspace with NULL) before selecting it, then attach a new one");
   if (!t->M64) {
     t->M64 = dev_alloc<double>(t, (size_t)NB * NCP);
     t->Lam64 = dev_alloc<double>(t, (size_t)NB * NCP);
@@ -1616,6 +1622,9 @@ void ensure_fp64(fmm_tree* t, cudaStream_t st) {
 
 void prepare_df_far(fmm_tree* t, cudaStream_t st) {
   if (t->geo_lo || t->two_trees) return;
+  require(!t->ws_external,
+          "FMM_FP64DF needs a larger evaluation workspace: detach the caller's workspace "
+          "(fmm_tree_set_workspace with NULL) before selecting it, then attach a new one");
   ensure_fp64(t, st);
   const int p = t->prm.p;
   const int64_t ng = (int64_t)m2l_fields(p) * std::max<int64_t>(t->n_m2l, 1);

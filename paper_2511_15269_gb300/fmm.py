@@ -18,6 +18,7 @@ FMM_OK, FMM_ERR_INVALID_ARG, FMM_ERR_CUDA, FMM_ERR_OOM, FMM_ERR_CAPACITY, FMM_ER
 FMM_FP64, FMM_FP32C, FMM_FP64DF = 0, 1, 2
 FMM_TIE_TARGET = 1
 FMM_SAME_LEVEL = 2
+FMM_POS_SOA = 4
 FMM_MAX_P = 10
 
 # exported entry points, in include/fmm.h order
@@ -28,6 +29,7 @@ ENTRY_POINTS = ["fmm_device_peaks", "fmm_last_error", "fmm_set_device_memory_lim
                 "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_set_wait_limit",
                 "fmm_tree_export",
                 "fmm_tree_profile", "fmm_tree_stage_times", "fmm_eval_potential", "fmm_eval_field",
+                "fmm_eval_batched", "fmm_tree_workspace_bytes", "fmm_tree_set_workspace",
                 "fmm_eval_potential_host", "fmm_eval_potential_static", "fmm_backward"]
 STAGES = ["sort", "p2p", "p2m", "m2m", "m2l", "l2l", "l2p"]
 
@@ -87,6 +89,9 @@ def lib():
         L.fmm_tree_stage_times.argtypes = [vp, vp, vp]
         L.fmm_eval_potential.argtypes = [vp, vp, vp, vp]
         L.fmm_eval_field.argtypes = [vp, vp, vp, vp, vp]
+        L.fmm_eval_batched.argtypes = [vp, i, vp, vp, vp]
+        L.fmm_tree_workspace_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.fmm_tree_set_workspace.argtypes = [vp, vp, C.c_size_t]
         L.fmm_eval_potential_host.argtypes = [vp, vp, vp, vp]
         L.fmm_eval_potential_static.argtypes = [vp, vp, vp, vp]
         L.fmm_backward.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -159,6 +164,7 @@ class Tree:
         self.n_charges = n if n_charges is None else n_charges
         self.n_out = n if n_out is None else n_out
         self.two_trees = n_charges is not None
+        self._workspace = None  # a caller workspace attached with fmm_tree_set_workspace
 
     @property
     def handle(self):
@@ -183,9 +189,10 @@ class Tree:
 
 
 def fmm_build_tree(pos, p, leaf_size, splits=2, theta=0.5, precision=FMM_FP32C, flags=0):
-    """Builds the hierarchy of `pos` (N x 3 float64 CUDA tensor) on the device."""
+    """Builds the hierarchy of `pos` on the device: an N x 3 float64 CUDA
+    tensor, or 3 x N with FMM_POS_SOA in flags."""
     pos = pos.contiguous()
-    n = pos.shape[0]
+    n = pos.shape[1] if flags & FMM_POS_SOA else pos.shape[0]
     prm = fmm_params(int(p), int(leaf_size), int(splits), float(theta), int(precision), int(flags))
     h = C.c_void_p()
     _check(lib().fmm_build_tree(_dev(pos, 3 * n, "pos"), n, C.byref(prm), _stream(), C.byref(h)))
@@ -196,7 +203,7 @@ def fmm_build_tree2(src_pos, trg_pos, p, leaf_size, splits=2, theta=0.5, precisi
     """Separate source and target hierarchies: evaluations take charges at
     src_pos (N_s x 3) and return potentials / fields at trg_pos (N_t x 3)."""
     src_pos, trg_pos = src_pos.contiguous(), trg_pos.contiguous()
-    ns, nt = src_pos.shape[0], trg_pos.shape[0]
+    ns, nt = (src_pos.shape[1], trg_pos.shape[1]) if flags & FMM_POS_SOA else (src_pos.shape[0], trg_pos.shape[0])
     prm = fmm_params(int(p), int(leaf_size), int(splits), float(theta), int(precision), int(flags))
     h = C.c_void_p()
     _check(lib().fmm_build_tree2(_dev(src_pos, 3 * ns, "src_pos"), ns, _dev(trg_pos, 3 * nt, "trg_pos"), nt,
@@ -289,6 +296,43 @@ def fmm_eval_field(tree, q, potential=True):
                                 _dev(u, tree.n_out, "u") if u is not None else None,
                                 _dev(f, 3 * tree.n_out, "field"), _stream()))
     return (u, f) if potential else f
+
+
+def fmm_eval_batched(batch, q_sets, u_sets=None):
+    """Potentials of the batch's charge sets (one float64 CUDA tensor per
+    set, in the order the trees were merged) in one evaluation."""
+    offs = fmm_tree_point_offsets(batch)
+    n = len(offs) - 1
+    if len(q_sets) != n:
+        raise FmmError(FMM_ERR_INVALID_ARG, "expected %d charge sets, got %d" % (n, len(q_sets)))
+    if u_sets is None:
+        u_sets = [torch.empty(int(offs[k + 1] - offs[k]), dtype=torch.float64, device=q_sets[k].device)
+                  for k in range(n)]
+    qp = (C.c_void_p * n)(*[_dev(q, int(offs[k + 1] - offs[k]), "q_sets[%d]" % k).value for k, q in enumerate(q_sets)])
+    up = (C.c_void_p * n)(*[_dev(u, int(offs[k + 1] - offs[k]), "u_sets[%d]" % k).value for k, u in enumerate(u_sets)])
+    _check(lib().fmm_eval_batched(batch.handle, n, qp, up, _stream()))
+    return u_sets
+
+
+def fmm_tree_workspace_bytes(tree):
+    v = C.c_size_t()
+    _check(lib().fmm_tree_workspace_bytes(tree.handle, C.byref(v)))
+    return v.value
+
+
+def fmm_tree_set_workspace(tree, workspace):
+    """Evaluations of `tree` use `workspace` (a CUDA tensor of at least
+    fmm_tree_workspace_bytes bytes, kept alive by the caller; the tree holds a
+    reference) for their scratch; None gives the tree its own again."""
+    if workspace is None:
+        _check(lib().fmm_tree_set_workspace(tree.handle, None, 0))
+        tree._workspace = None
+        return
+    if not (isinstance(workspace, torch.Tensor) and workspace.is_cuda and workspace.is_contiguous()):
+        raise TypeError("workspace: expected a contiguous CUDA tensor")
+    _check(lib().fmm_tree_set_workspace(tree.handle, C.c_void_p(workspace.data_ptr()),
+                                        workspace.numel() * workspace.element_size()))
+    tree._workspace = workspace
 
 
 def fmm_eval_potential_host(tree, q_host, u_host=None):
