@@ -297,12 +297,15 @@ def bench_batched(fmm, workloads, oracle, dev):
     sets = workloads.batched_sets(64, seed=0)
     pos_list = [pos for pos, q in sets]
     q_all = np.concatenate([q for pos, q in sets])
-    best, tried = autotune.tune_leaf_size(pos_list, q_all, c["p"], c["s"], c["theta"], fmm.FMM_FP32C)
+    t0 = time.perf_counter()
+    best, opts, tried = autotune.tune(pos_list, q_all, c["p"], c["s"], c["theta"], fmm.FMM_FP32C)
+    tune_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     B = autotune.build_batch(pos_list, c["p"], best, c["s"], c["theta"], fmm.FMM_FP32C)
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
+    autotune.apply_options(B, opts)
     q_d = torch.from_numpy(q_all).to(dev)
     u = torch.empty_like(q_d)
     side = torch.cuda.Stream()
@@ -315,7 +318,9 @@ def bench_batched(fmm, workloads, oracle, dev):
     with torch.cuda.graph(graph):
         fmm.fmm_eval_potential(B, q_d, u)
     ms = event_ms(graph.replay, 10)
+    l0 = fmm.fmm_tree_stats(B)["kernel_launches"]
     ms_eager = event_ms(lambda: fmm.fmm_eval_potential(B, q_d, u), 5)
+    launches_per_eval = (fmm.fmm_tree_stats(B)["kernel_launches"] - l0) / 6
     graph.replay()
     torch.cuda.synchronize()
     uu = u.cpu().numpy()
@@ -332,9 +337,14 @@ def bench_batched(fmm, workloads, oracle, dev):
     n = int(off[-1])
     return {"workload": "64 sets, N log-uniform in [1e4, 5e5] (total %d), cube / 8 Gaussian clusters sigma 0.02, "
                         "p=%d, theta %g, FP32C" % (n, c["p"], c["theta"]),
-            "leaf_size": best, "autotune_ms": tried, "batch_build_ms": build_ms,
+            "leaf_size": best, "launch_options": {str(k): v for k, v in opts.items()},
+            "autotune": {"candidates": len(tried), "seconds": tune_s,
+                         "best_ms": min(tried.values()), "worst_ms": max(tried.values()),
+                         "per_leaf_best_ms": {str(lf): min(v for k, v in tried.items() if k.startswith("%d/" % lf))
+                                              for lf in sorted({int(k.split("/")[0]) for k in tried})}},
+            "batch_build_ms": build_ms,
             "graph_ms": ms, "eager_ms": ms_eager, "Mpoints/s": n / ms / 1e3,
-            "kernel_launches_per_eval": None, "trees": st["n_trees"],
+            "kernel_launches_per_eval": launches_per_eval, "trees": st["n_trees"],
             "rel_l2_vs_direct_64_targets_per_set": float(np.sqrt(errs_num / errs_den))}
 
 

@@ -248,9 +248,36 @@ int fmm_tree_stats(const fmm_tree* tree, fmm_stats* stats);
  * kernels of earlier evaluations of this tree (FMM_OK or FMM_ERR_TIMEOUT). */
 int fmm_tree_status(fmm_tree* tree, void* stream);
 
-/* Limit, in GPU clock cycles, of each near-field warp's wait for a staged
- * source tile (a bulk copy completing on a shared-memory barrier; Sec. II.B
- * near field).  A warp whose wait runs out latches FMM_ERR_TIMEOUT in the
+/* Launch options of later evaluations of a tree: the launch shapes the
+ * autotuner searches (the paper tunes N_max by hand, Sec. III.A; these do
+ * not change results beyond rounding, except FMM_OPT_NEAR_SYMMETRIC which
+ * changes the summation order of the near field).
+ *   FMM_OPT_SCHEDULE        0: every stage on the caller's stream in order;
+ *                           1 (default): P2M and M2M on the tree's second
+ *                           stream beside the near field, the near-field slot
+ *                           gather beside M2L and L2L; 2: M2L and L2L beside
+ *                           the near field; 3: the near field in two launches,
+ *                           P2M and M2M beside the first, L2L beside the second
+ *   FMM_OPT_M2M_ONE_LAUNCH  1 (default): every M2M round in one launch whose
+ *                           warps wait (bounded) for their children's sums;
+ *                           0: one launch per round
+ *   FMM_OPT_NEAR_SYMMETRIC  1 (default): pairs listed both ways evaluated once
+ *                           (potentials of one point set); 0: one-sided
+ *   FMM_OPT_M2L_BLOCKS_PER_SM  cap on resident M2L blocks per SM (0: none)
+ * Errors: FMM_ERR_INVALID_ARG (NULL tree, unknown option, value out of
+ * range). */
+enum {
+  FMM_OPT_SCHEDULE = 1,
+  FMM_OPT_M2M_ONE_LAUNCH = 2,
+  FMM_OPT_NEAR_SYMMETRIC = 3,
+  FMM_OPT_M2L_BLOCKS_PER_SM = 4
+};
+int fmm_tree_set_option(fmm_tree* tree, int option, int value);
+
+/* Limit, in GPU clock cycles, of each bounded device-side wait: a near-field
+ * warp's wait for a staged source tile (a bulk copy completing on a
+ * shared-memory barrier; Sec. II.B near field) and the one-launch M2M's wait
+ * for a child's sum.  A warp whose wait runs out latches FMM_ERR_TIMEOUT in the
  * tree (read by fmm_tree_status), lets its copies in flight land and stops;
  * that evaluation's results are then incomplete.  Default about 2e9 cycles
  * (about a second); 0 gives up before the first poll, which exercises the

@@ -68,6 +68,9 @@ std::vector<WsItem> ws_items(fmm_tree* t) {
   add(&t->f_stage, sizeof(double) * 3 * n);
   add(&t->g_stage, sizeof(double) * 3 * n);
   add(&t->counters, sizeof(int) * 8);
+  add(&t->m2m_ready, sizeof(int) * NB);
+  add(&t->m2l_partial, sizeof(double) * NCP * (size_t)std::max<int64_t>(t->m2l_partial_rows, 1));
+  add(&t->gpart, sizeof(double) * (size_t)std::max<int64_t>(t->n_gchunks, 1) * std::max(t->sym_stride, 1));
   return v;
 }
 size_t ws_bytes(const std::vector<WsItem>& v) {
@@ -134,13 +137,15 @@ void free_tree(fmm_tree* t) {
   if (!t) return;
   cudaDeviceSynchronize();
   void* ptrs[] = {t->perm,     t->box_start, t->box_count, t->center,   t->radius,   t->m2l_off,  t->m2l_src,
-                  t->m2l_trg,  t->m2l_order, t->p2p_off,   t->p2p_src,  t->p2p32,    t->leaf_order, t->pos_local,
+                  t->m2l_trg,  t->m2l_items, t->m2l_split_g, t->m2l_split_row, t->m2l_partial,
+                  t->gch_leaf, t->gch_r0, t->gch_first, t->gmulti_leaf, t->gpart, t->p2p_off,   t->p2p_src,  t->p2p32,    t->leaf_order, t->pos_local,
                   t->pos64,    t->inv_rho32, t->inv_rho64, t->geo32,    t->geo64,    t->m2m32,    t->m2m64,
                   t->l2d32,    t->l2d64,     t->geo_lo,    t->m_df,     t->src32,     t->src64,    t->M32,      t->Lam32,    t->M64,
                   t->Lam64,    t->src_dup,   t->near_u,    t->near_f,    t->q_stage,  t->u_stage,  t->f_stage,  t->g_stage,
                   t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->l2d_off, t->l2d_anc,
                   t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr, t->sym_slot, t->sym_work_off,
-                  t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec, t->src_df, t->sym_frame, t->src_dup2, t->near_u2, t->near_f2};
+                  t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec, t->src_df, t->sym_frame, t->src_dup2, t->near_u2, t->near_f2,
+                  t->m2m_ready};
   for (void* p : ptrs)
     if (p) dev_free(p);
   if (t->prof_ev) {
@@ -192,6 +197,10 @@ cudaMemPool_t pool_for_device() {
 }
 }  // namespace
 
+namespace {
+thread_local cudaStream_t tl_build_stream_end = nullptr;  // the outermost scope's stream
+}  // namespace
+
 void trim_pool() {
   if (tl_alloc_pool) return;  // inside a build: its scope trims at the end
   int dev = 0;
@@ -211,13 +220,15 @@ AllocScope::AllocScope(cudaStream_t s)
     : prev(tl_alloc_stream), prev_pool(tl_alloc_pool), pool(pool_for_device()) {
   tl_alloc_stream = s;
   tl_alloc_pool = pool;
+  if (!prev_pool) tl_build_stream_end = s;
 }
 AllocScope::~AllocScope() {
   tl_alloc_stream = prev;
   tl_alloc_pool = prev_pool;
   if (!prev_pool) {
     // the outermost scope gives the memory freed during the build back
-    cudaDeviceSynchronize();
+    // (builds on other threads and streams keep theirs)
+    cudaStreamSynchronize(tl_build_stream_end);
     cudaMemPoolTrimTo(pool, 0);
   }
 }
@@ -297,6 +308,32 @@ int fmm_device_memory_in_use(size_t* bytes) {
   std::lock_guard<std::mutex> lk(g_mem_mu);
   *bytes = g_live_bytes;
   return FMM_OK;
+}
+
+int fmm_tree_set_option(fmm_tree* tree, int option, int value) {
+  return guarded([&] {
+    require(tree != nullptr, "tree is NULL");
+    switch (option) {
+      case FMM_OPT_SCHEDULE:
+        require(value >= 0 && value <= 3, "FMM_OPT_SCHEDULE takes 0 .. 3");
+        tree->opt_schedule = value;
+        break;
+      case FMM_OPT_M2M_ONE_LAUNCH:
+        require(value == 0 || value == 1, "FMM_OPT_M2M_ONE_LAUNCH takes 0 or 1");
+        tree->opt_m2m_one_launch = value;
+        break;
+      case FMM_OPT_NEAR_SYMMETRIC:
+        require(value == 0 || value == 1, "FMM_OPT_NEAR_SYMMETRIC takes 0 or 1");
+        tree->opt_near_sym = value;
+        break;
+      case FMM_OPT_M2L_BLOCKS_PER_SM:
+        require(value >= 0 && value <= 32, "FMM_OPT_M2L_BLOCKS_PER_SM takes 0 .. 32");
+        tree->opt_m2l_blocks_per_sm = value;
+        break;
+      default:
+        require(false, "unknown option");
+    }
+  });
 }
 
 int fmm_tree_set_wait_limit(fmm_tree* tree, int64_t cycles) {

@@ -104,6 +104,19 @@ struct __align__(32) SymFrame {
   float g, pad;
 };
 
+// One M2L work item: interactions b .. e - 1 of the list of target box g.
+// Lists longer than kM2LItem are split into items of at most kM2LItem
+// interactions whose sums go to rows prow, prow + 1, ... of a partial buffer
+// and are added in item order afterwards (prow < 0: the item is the whole
+// list and writes the target's local expansion itself).
+struct __align__(8) M2LItem {
+  int64_t b, e;
+  int32_t g, prow;
+};
+constexpr int64_t kM2LItem = 8192;
+// slots the symmetric near field's gather adds per chunk (one warp each)
+constexpr int64_t kGatherChunk = 512;
+
 // One work entry of the symmetric near field, read with one coalesced load:
 // the source leaf's point range, the pair's slot (-1: one-sided), the FP32
 // centre offset c_T - c_S and the coincidence threshold (< 0: no masking).
@@ -138,7 +151,24 @@ struct fmm_tree {
   int64_t* m2l_off = nullptr;    // n_boxes + 1, CSR by target global box
   int32_t* m2l_src = nullptr;    // n_m2l
   int32_t* m2l_trg = nullptr;    // n_m2l
-  int32_t* m2l_order = nullptr;  // n_boxes: target boxes, longest list first
+  int64_t n_m2l_items = 0;       // M2L work items (>= n_boxes)
+  fmm::M2LItem* m2l_items = nullptr;  // longest first
+  int64_t n_m2l_split = 0;       // targets whose list is split into several items
+  int32_t* m2l_split_g = nullptr;     // those targets
+  int64_t* m2l_split_row = nullptr;   // n_m2l_split + 1: their first partial row (CSR)
+  double* m2l_partial = nullptr;      // partial rows (ncoef_pad doubles each; FP32 rows use the first half)
+  int64_t m2l_partial_rows = 0;
+  // symmetric near-field slot gather in chunks of at most kGatherChunk slots:
+  // chunk c covers slots gch_r0[c] .. of leaf gch_leaf[c]; leaves with
+  // several chunks (gmulti_leaf, their first chunk gch_off) add the chunks'
+  // sums (gpart, stride rows of 8 bytes per point) in chunk order
+  int64_t n_gchunks = 0;
+  int32_t* gch_leaf = nullptr;
+  int64_t* gch_r0 = nullptr;
+  int64_t* gch_first = nullptr;       // n_leaves + 1: first chunk of each leaf
+  int64_t n_gmulti = 0;
+  int32_t* gmulti_leaf = nullptr;
+  double* gpart = nullptr;            // n_gchunks x sym_stride
   int64_t* p2p_off = nullptr;    // n_leaves + 1, CSR by target leaf
   int32_t* p2p_src = nullptr;    // n_p2p
   fmm::P2PEntry* p2p32 = nullptr;  // n_p2p
@@ -228,6 +258,13 @@ struct fmm_tree {
   int* counters = nullptr;       // work counters, reset before each launch
   int* status = nullptr;         // latched kernel status bits
   int ws_external = 0;           // the evaluation workspace is the caller's (fmm_tree_set_workspace)
+  int* m2m_ready = nullptr;      // n_boxes readiness flags of the one-launch M2M (NULL: one launch per round)
+  // launch options (fmm_tree_set_option): stage order, M2M in one launch,
+  // symmetric near field, cap on M2L blocks per SM (0: full occupancy)
+  int opt_schedule = 1;
+  int opt_m2m_one_launch = 1;
+  int opt_near_sym = 1;
+  int opt_m2l_blocks_per_sm = 0;
   long long wait_cycles = fmm::kDefaultWaitCycles;  // near-field tile wait limit
 
   // far-field stages run on a second, higher-priority stream forked from
@@ -305,8 +342,8 @@ __host__ __device__ constexpr int b_off(int n) {
 // sort.cu: perm = 0 .. n - 1 ordered by descending key (keys clamped to
 // [0, 2^32)), equal keys in ascending index order; asynchronous on st.
 void order_desc(const int64_t* key, int64_t n, int32_t* perm, cudaStream_t st);
-// tree_build.cu: work orders of a tree whose lists are set (m2l_order,
-// leaf_order), on the device.
+// tree_build.cu: work orders of a tree whose lists are set (the M2L work
+// items and leaf_order), on the device.
 void build_work_orders(fmm_tree* t, cudaStream_t st);
 
 // scan.cu: exclusive prefix sum of n int64 values (in place allowed);

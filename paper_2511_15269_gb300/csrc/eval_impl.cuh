@@ -75,9 +75,17 @@ __device__ __forceinline__ void load_coef(const real* src, real (&v)[ncoef(P)]) 
 // Points at or after n_charges (targets of a separate target tree) get q = 0.
 // dup: FP32 near-field records (FP32C); df: charges of the double-float
 // records (FP64DF), whose coordinates are set at build.
+// It also clears the evaluation's work counters (8) and the n_ready
+// readiness flags of the one-launch M2M (the kernels that use them run after
+// it on the same stream).
 __global__ void gather_kernel(int64_t n, int64_t n_charges, const int32_t* __restrict__ perm,
                               const double* __restrict__ q, const vec4* __restrict__ pos,
-                              vec4* __restrict__ src, DupRec* __restrict__ dup, DFRec* __restrict__ df) {
+                              vec4* __restrict__ src, DupRec* __restrict__ dup, DFRec* __restrict__ df,
+                              int* __restrict__ counters, int* __restrict__ ready, int64_t n_ready) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (counters && tid < 8) counters[tid] = 0;
+  if (ready)
+    for (int64_t b = tid; b < n_ready; b += (int64_t)gridDim.x * blockDim.x) ready[b] = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     vec4 p = pos[i];
@@ -191,6 +199,87 @@ __global__ void __launch_bounds__(128) m2m_kernel(int64_t n_child, const int32_t
   }
 }
 
+// ---- E2 in one launch: the M2M rounds of every tree of a batch ---------------
+// The work list is the rounds' child boxes concatenated (round r: the boxes r
+// levels above each tree's leaves; the 2^s children of a parent consecutive,
+// rounds and parent groups aligned to multiples of 2^s).  Warps take chunks
+// of 32 items in list order; a child that is not a leaf (round >= 1) is
+// used once its own M2M sum is written: the warp that wrote it set
+// ready[child] after a memory fence, and the reader waits for the flag (a
+// bounded wait: on timeout ST_TIMEOUT is latched and the evaluation is
+// incomplete).  Chunks are taken in order and only wait for earlier items,
+// which running warps hold, so the waits always end.  Each child's
+// translation and the sum over the 2^s children are the round kernel's, so
+// the result is the same bit for bit.
+constexpr int kMaxRounds = 40;
+struct RoundTab {
+  int64_t pad[kMaxRounds + 1];  // round r occupies chunk slots pad[r] .. pad[r + 1] - 1 (multiples of 32)
+  int64_t off[kMaxRounds + 1];  // and items off[r] .. off[r + 1] - 1 of the work list
+  int n;
+};
+template <int P>
+__global__ void __launch_bounds__(128) m2m_persistent_kernel(RoundTab rt, const int32_t* __restrict__ child,
+                                                             const int32_t* __restrict__ parent, int nch,
+                                                             const real* __restrict__ edge, int64_t edge_stride,
+                                                             real* M, int* ready, int* __restrict__ counter,
+                                                             int* __restrict__ status, long long wait_cycles) {
+  constexpr int NC = ncoef(P);
+  const int lane = lane_id();
+  for (;;) {
+    int64_t base = 0;
+    if (lane == 0) base = atomicAdd(counter, 32);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= rt.pad[rt.n]) break;
+    // each round starts on a chunk boundary, so a chunk holds one round
+    int r = 0;
+    while (rt.pad[r + 1] <= base) r++;
+    const int64_t k = base - rt.pad[r] + lane;
+    const bool active = k < rt.off[r + 1] - rt.off[r];
+    const int64_t t = rt.off[r] + k;
+    real v[NC];
+    int64_t g = 0;
+    if (active) {
+      g = child[t];
+      if (r > 0) {
+        // the child's own sum (written in the previous round) must be complete
+        const long long t0 = clock64();
+        while (atomicAdd(&ready[g], 0) == 0) {
+          if (clock64() - t0 >= wait_cycles) {
+            atomicOr(status, ST_TIMEOUT);
+            break;
+          }
+          __nanosleep(100);  // leave the issue slots to the stages running beside
+        }
+        __threadfence();
+      }
+      const real* row = M + g * ncoef_pad(P);
+#pragma unroll
+      for (int c = 0; c < NC; c++) v[c] = __ldcg(row + c);
+      const real a = edge[0 * edge_stride + g], b = edge[1 * edge_stride + g];
+      real cp[P], sp[P], ct[P], st[P];
+      load_trig<P>(edge, edge_stride, g, 2, cp, sp, ct, st);
+      translate_rotated<P>(v, cp, sp, ct, st, [&](real (&w)[ncoef(P)]) { axial_m2m<P>(w, a, b); });
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; c++) v[c] = real(0);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      real x = v[c];
+      for (int o = 1; o < nch; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[c] = x;
+    }
+    if (active && (k % nch) == 0) {
+      const int64_t pg = parent[g];
+      real* out = M + pg * ncoef_pad(P);
+#pragma unroll
+      for (int c = 0; c < NC; c++) __stcg(out + c, v[c]);
+      __threadfence();
+      atomicExch(&ready[pg], 1);
+    }
+  }
+}
+
 // ---- E3: M2L, persistent; one warp per target box, lanes over its list ------
 // Each lane accumulates its interactions in a shared-memory row of m2l_chunks
 // 16-byte chunks (4 FP32 or 2 FP64 values; an odd count, so the 8 lanes of a
@@ -233,13 +322,11 @@ __device__ __forceinline__ void m2l_acc_add(real* row, const real (&v)[ncoef(P)]
 }
 
 template <int P>
-__global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
-                                                  const int32_t* __restrict__ order,
-                                                  const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(128) m2l_kernel(int64_t n_items, const M2LItem* __restrict__ items,
                                                   const int32_t* __restrict__ src,
                                                   const real* __restrict__ geo, int64_t n_m2l,
                                                   const real* __restrict__ M,
-                                                  real* __restrict__ Lam,
+                                                  real* __restrict__ Lam, real* __restrict__ partial,
                                                   int* __restrict__ counter) {
   constexpr int NC = ncoef(P);
   constexpr int NCP = ncoef_pad(P);
@@ -253,9 +340,10 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
     int t = 0;
     if (lane == 0) t = atomicAdd(counter, 1);
     t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= n_targets) break;
-    const int64_t g = order[t];
-    const int64_t b = off[g], e = off[g + 1];
+    if (t >= n_items) break;
+    const M2LItem it = items[t];
+    const int64_t g = it.g;
+    const int64_t b = it.b, e = it.e;
 #pragma unroll
     for (int c = 0; c < ROW; c++) mine[c] = real(0);
     for (int64_t i = b + lane; i < e; i += 32) {
@@ -270,7 +358,7 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
       m2l_acc_add<P>(mine, v);
     }
     __syncwarp();
-    real* out = Lam + g * NCP;
+    real* out = it.prow < 0 ? Lam + g * NCP : partial + (int64_t)it.prow * NCP;
     for (int c = lane; c < NCP; c += 32) {
       real s = real(0), err = real(0);
       if (c < NC) {
@@ -294,13 +382,12 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_targets,
 // odd row length: conflict-free 8-byte accesses); the warp adds the 32 rows
 // per coefficient in lane order and writes the FP64 locals.
 template <int P>
-__global__ void __launch_bounds__(128) m2l_kernel_df(int64_t n_targets, const int32_t* __restrict__ order,
-                                                     const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(128) m2l_kernel_df(int64_t n_items, const M2LItem* __restrict__ items,
                                                      const int32_t* __restrict__ src,
                                                      const float* __restrict__ geo_h,
                                                      const float* __restrict__ geo_l, int64_t n_m2l,
                                                      const float2* __restrict__ Mdf, double* __restrict__ Lam,
-                                                     int* __restrict__ counter) {
+                                                     double* __restrict__ partial, int* __restrict__ counter) {
   constexpr int NC = ncoef(P);
   constexpr int NCP = ncoef_pad(P);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -313,9 +400,10 @@ __global__ void __launch_bounds__(128) m2l_kernel_df(int64_t n_targets, const in
     int t = 0;
     if (lane == 0) t = atomicAdd(counter, 1);
     t = __shfl_sync(0xffffffffu, t, 0);
-    if (t >= n_targets) break;
-    const int64_t g = order[t];
-    const int64_t b = off[g], e = off[g + 1];
+    if (t >= n_items) break;
+    const M2LItem it = items[t];
+    const int64_t g = it.g;
+    const int64_t b = it.b, e = it.e;
     for (int c = 0; c < NC; c++) mine[c] = make_float2(0.f, 0.f);
     for (int64_t i = b + lane; i < e; i += 32) {
       const float2* ms = Mdf + (int64_t)src[i] * NCP;
@@ -338,7 +426,7 @@ __global__ void __launch_bounds__(128) m2l_kernel_df(int64_t n_targets, const in
       }
     }
     __syncwarp();
-    double* out = Lam + g * NCP;
+    double* out = it.prow < 0 ? Lam + g * NCP : partial + (int64_t)it.prow * NCP;
     for (int c = lane; c < NCP; c += 32) {
       dff s(0.f, 0.f);
       if (c < NC) {
@@ -350,6 +438,27 @@ __global__ void __launch_bounds__(128) m2l_kernel_df(int64_t n_targets, const in
       out[c] = to_double(s);
     }
     __syncwarp();
+  }
+}
+
+// Locals of the targets whose M2L list was split into several work items:
+// the items' partial rows added in item order (compensated in FP32).  One
+// warp per target, lanes over coefficients.
+template <class T>
+__global__ void m2l_combine_kernel(int64_t n_split, const int32_t* __restrict__ split_g,
+                                   const int64_t* __restrict__ split_row, int ncp, const T* __restrict__ partial,
+                                   T* __restrict__ Lam) {
+  const int64_t warps = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; k < n_split; k += warps) {
+    const int64_t g = split_g[k];
+    for (int c = threadIdx.x & 31; c < ncp; c += 32) {
+      T s = T(0), err = T(0);
+      for (int64_t r = split_row[k]; r < split_row[k + 1]; r++) {
+        if (std::is_same<T, float>::value) two_sum(s, err, partial[r * ncp + c]);
+        else s += partial[r * ncp + c];
+      }
+      Lam[g * ncp + c] = s + err;
+    }
   }
 }
 
@@ -1390,25 +1499,38 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
 // (sums computed by the warps of its partners; contiguous, in list order) to
 // its near-field sums.  Warp per leaf, each lane two points, eight slots'
 // loads in flight per point.
-__global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
+// Chunks of at most kGatherChunk slots, one warp each: a leaf with one
+// chunk adds it to its sums directly; a leaf with several writes each
+// chunk's sums (hi, lo per point) to a partial row, and sym_combine_kernel
+// adds the rows in chunk order.
+__global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_chunks, const int32_t* __restrict__ gch_leaf,
+                                                         const int64_t* __restrict__ gch_r0,
+                                                         const int64_t* __restrict__ gch_first,
+                                                         const int32_t* __restrict__ leaf_box,
                                                          const int64_t* __restrict__ box_start,
                                                          const int32_t* __restrict__ box_count,
                                                          const int64_t* __restrict__ recv_off,
                                                          const float* __restrict__ partial, int64_t stride,
-                                                         float* __restrict__ near_u) {
+                                                         float* __restrict__ near_u, float* __restrict__ gpart) {
   const int lane = lane_id();
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-  for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves; leaf += warps) {
-    const int64_t r0 = recv_off[leaf], r1 = recv_off[leaf + 1];
-    if (r0 == r1) continue;
+  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; ch < n_chunks; ch += warps) {
+    const int64_t leaf = gch_leaf[ch];
+    const int64_t r0 = gch_r0[ch], r1 = min(r0 + kGatherChunk, recv_off[leaf + 1]);
+    const bool single = gch_first[leaf + 1] - gch_first[leaf] == 1;
     const int64_t g = leaf_box[leaf];
     const int64_t start = box_start[g];
     const int cnt = box_count[g];
     for (int base = 0; base < cnt; base += 64) {
       const int i0 = base + lane, i1 = base + 32 + lane;
       const bool ok0 = i0 < cnt, ok1 = i1 < cnt;
-      float h0 = ok0 ? near_u[2 * (start + i0)] : 0.f, l0 = ok0 ? near_u[2 * (start + i0) + 1] : 0.f;
-      float h1 = ok1 ? near_u[2 * (start + i1)] : 0.f, l1 = ok1 ? near_u[2 * (start + i1) + 1] : 0.f;
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      if (single) {
+        h0 = ok0 ? near_u[2 * (start + i0)] : 0.f;
+        l0 = ok0 ? near_u[2 * (start + i0) + 1] : 0.f;
+        h1 = ok1 ? near_u[2 * (start + i1)] : 0.f;
+        l1 = ok1 ? near_u[2 * (start + i1) + 1] : 0.f;
+      }
       for (int64_t r = r0; r < r1; r += 8) {
         float v0[8], v1[8];
 #pragma unroll
@@ -1426,24 +1548,43 @@ __global__ void __launch_bounds__(128) sym_gather_kernel(int64_t n_leaves, const
           }
         }
       }
+      float* dst = single ? near_u + 2 * start : gpart + 2 * ch * stride;
       if (ok0) {
-        near_u[2 * (start + i0)] = h0;
-        near_u[2 * (start + i0) + 1] = l0;
+        dst[2 * i0] = h0;
+        dst[2 * i0 + 1] = l0;
       }
       if (ok1) {
-        near_u[2 * (start + i1)] = h1;
-        near_u[2 * (start + i1) + 1] = l1;
+        dst[2 * i1] = h1;
+        dst[2 * i1 + 1] = l1;
       }
     }
   }
 }
 
-// ---- E6 (FP64, potential, one point set): symmetric near field ----------------
-// As p2p_kernel_f32s, in FP64 on absolute positions: a warp per leaf, lane l
-// holds targets l + 32 k; pairs listed both ways are evaluated once and the
-// sources' sums q_i / r are reduced over the warp in chunks of 16 sources
-// (reduce-scatter butterfly on lane bits 4..1, then the lane pair); 1/r from
-// rsqrt_f64.
+// Leaves gathered in several chunks: the chunks' sums added in chunk order.
+__global__ void __launch_bounds__(128) sym_combine_kernel(int64_t n_multi, const int32_t* __restrict__ mleaf,
+                                                          const int64_t* __restrict__ gch_first,
+                                                          const int32_t* __restrict__ leaf_box,
+                                                          const int64_t* __restrict__ box_start,
+                                                          const int32_t* __restrict__ box_count, int64_t stride,
+                                                          const float* __restrict__ gpart, float* __restrict__ near_u) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; k < n_multi; k += warps) {
+    const int64_t leaf = mleaf[k];
+    const int64_t g = leaf_box[leaf];
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    for (int i = threadIdx.x & 31; i < cnt; i += 32) {
+      float h = near_u[2 * (start + i)], l = near_u[2 * (start + i) + 1];
+      for (int64_t ch = gch_first[leaf]; ch < gch_first[leaf + 1]; ch++) {
+        two_sum(h, l, gpart[2 * (ch * stride + i)]);
+        l += gpart[2 * (ch * stride + i) + 1];
+      }
+      near_u[2 * (start + i)] = h;
+      near_u[2 * (start + i) + 1] = l;
+    }
+  }
+}
 
 template <int TPL>
 __global__ void __launch_bounds__(128) p2p_kernel_f64s(P2PArgs a) {
@@ -1592,22 +1733,27 @@ __global__ void __launch_bounds__(128) p2p_kernel_f64s(P2PArgs a) {
 }
 
 // FP64 counterpart of sym_gather_kernel: plain FP64 sums in list order.
-__global__ void __launch_bounds__(128) sym_gather_f64_kernel(int64_t n_leaves, const int32_t* __restrict__ leaf_box,
+// FP64: as sym_gather_kernel / sym_combine_kernel with FP64 sums
+__global__ void __launch_bounds__(128) sym_gather_f64_kernel(int64_t n_chunks, const int32_t* __restrict__ gch_leaf,
+                                                             const int64_t* __restrict__ gch_r0,
+                                                             const int64_t* __restrict__ gch_first,
+                                                             const int32_t* __restrict__ leaf_box,
                                                              const int64_t* __restrict__ box_start,
                                                              const int32_t* __restrict__ box_count,
                                                              const int64_t* __restrict__ recv_off,
                                                              const double* __restrict__ partial, int64_t stride,
-                                                             double* __restrict__ near_u) {
+                                                             double* __restrict__ near_u, double* __restrict__ gpart) {
   const int lane = lane_id();
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
-  for (int64_t leaf = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; leaf < n_leaves; leaf += warps) {
-    const int64_t r0 = recv_off[leaf], r1 = recv_off[leaf + 1];
-    if (r0 == r1) continue;
+  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; ch < n_chunks; ch += warps) {
+    const int64_t leaf = gch_leaf[ch];
+    const int64_t r0 = gch_r0[ch], r1 = min(r0 + kGatherChunk, recv_off[leaf + 1]);
+    const bool single = gch_first[leaf + 1] - gch_first[leaf] == 1;
     const int64_t g = leaf_box[leaf];
     const int64_t start = box_start[g];
     const int cnt = box_count[g];
     for (int i = lane; i < cnt; i += 32) {
-      double acc = near_u[start + i];
+      double acc = single ? near_u[start + i] : 0.0;
       for (int64_t r = r0; r < r1; r += 8) {
         double v[8];
 #pragma unroll
@@ -1616,6 +1762,28 @@ __global__ void __launch_bounds__(128) sym_gather_f64_kernel(int64_t n_leaves, c
         for (int k = 0; k < 8; k++)
           if (r + k < r1) acc += v[k];
       }
+      if (single) near_u[start + i] = acc;
+      else gpart[ch * stride + i] = acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) sym_combine_f64_kernel(int64_t n_multi, const int32_t* __restrict__ mleaf,
+                                                              const int64_t* __restrict__ gch_first,
+                                                              const int32_t* __restrict__ leaf_box,
+                                                              const int64_t* __restrict__ box_start,
+                                                              const int32_t* __restrict__ box_count, int64_t stride,
+                                                              const double* __restrict__ gpart,
+                                                              double* __restrict__ near_u) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; k < n_multi; k += warps) {
+    const int64_t leaf = mleaf[k];
+    const int64_t g = leaf_box[leaf];
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    for (int i = threadIdx.x & 31; i < cnt; i += 32) {
+      double acc = near_u[start + i];
+      for (int64_t ch = gch_first[leaf]; ch < gch_first[leaf + 1]; ch++) acc += gpart[ch * stride + i];
       near_u[start + i] = acc;
     }
   }
@@ -2050,11 +2218,33 @@ void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   t->launches += 1 + t->n_up;
   stage_event(t, FMM_STAGE_P2M, true, st);
   stage_event(t, FMM_STAGE_M2M, false, st);
-  for (int r = 0; r < t->n_up; r++) {
-    const int64_t nchild = t->up_off_h[r + 1] - t->up_off_h[r];
-    m2m_kernel<P><<<grid_for(nchild, 128, 1 << 30), 128, 0, st>>>(nchild, t->up_ids + t->up_off_h[r], t->box_parent,
-                                                                 nch, pp.m2m, t->n_boxes, pp.M);
+  if (t->m2m_ready && t->opt_m2m_one_launch && t->n_up > 1 && t->n_up <= kMaxRounds) {
+    // every round in one launch (readiness flags cleared by the gather)
+    RoundTab rt{};
+    rt.n = t->n_up;
+    rt.pad[0] = 0;
+    for (int r = 0; r < t->n_up; r++) {
+      rt.off[r] = t->up_off_h[r];
+      rt.pad[r + 1] = rt.pad[r] + (t->up_off_h[r + 1] - t->up_off_h[r] + 31) / 32 * 32;
+    }
+    rt.off[t->n_up] = t->up_off_h[t->n_up];
+    int dev = 0, nsm = 0, occ = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // one block per SM: the rounds are short and the near field runs beside
+    int64_t blocks = std::min<int64_t>(nsm, (rt.pad[rt.n] + 127) / 128);
+    m2m_persistent_kernel<P><<<(int)std::max<int64_t>(blocks, 1), 128, 0, st>>>(
+        rt, t->up_ids, t->box_parent, nch, pp.m2m, t->n_boxes, pp.M, t->m2m_ready, t->counters + 2, t->status,
+        t->wait_cycles);
     FMM_LAUNCH_CHECK();
+    t->launches += 1 - t->n_up;
+  } else {
+    for (int r = 0; r < t->n_up; r++) {
+      const int64_t nchild = t->up_off_h[r + 1] - t->up_off_h[r];
+      m2m_kernel<P><<<grid_for(nchild, 128, 1 << 30), 128, 0, st>>>(nchild, t->up_ids + t->up_off_h[r],
+                                                                   t->box_parent, nch, pp.m2m, t->n_boxes, pp.M);
+      FMM_LAUNCH_CHECK();
+    }
   }
   stage_event(t, FMM_STAGE_M2M, true, st);
 }
@@ -2076,8 +2266,8 @@ void run_upward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
 //                and M2M beside the first, M2L alone, L2L beside the second,
 //                then the slot gather and L2P
 enum { kSerial = 0, kUpwardSide = 1, kFarSide = 2, kSplitNear = 3 };
-constexpr int kSchedule = kUpwardSide;
-constexpr bool kOverlapFarField = kSchedule == kFarSide;
+// The order is a tree option (fmm_tree_set_option, FMM_OPT_SCHEDULE; the
+// enumerators match its values), kUpwardSide by default.
 constexpr int kM2LBlocksPerSM = 1;
 
 // Downward pass: M2L over the whole list, then L2L in direct form.
@@ -2094,20 +2284,26 @@ void run_m2l_df(const fmm_tree* t, const Ptrs& pp, cudaStream_t st) {
   const int64_t nm = t->n_boxes * (int64_t)ncoef_pad(P);
   to_dff_kernel<<<grid_for(nm, 256), 256, 0, st>>>(nm, reinterpret_cast<const double*>(pp.M), t->m_df);
   FMM_LAUNCH_CHECK();
-  FMM_CUDA_TRY(cudaMemsetAsync(t->counters, 0, sizeof(int), st));
   int dev = 0, nsm = 0, occ = 0;
   FMM_CUDA_TRY(cudaGetDevice(&dev));
   FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, m2l_kernel_df<P>, 128, smem));
   if (occ < 1) occ = 1;
   int64_t blocks = (int64_t)nsm * occ;
-  const int64_t need = (t->n_boxes + 3) / 4;
+  const int64_t need = (t->n_m2l_items + 3) / 4;
   if (blocks > need) blocks = need;
-  m2l_kernel_df<P><<<(int)blocks, 128, smem, st>>>(t->n_boxes, t->m2l_order, t->m2l_off, t->m2l_src, t->geo32,
+  m2l_kernel_df<P><<<(int)blocks, 128, smem, st>>>(t->n_m2l_items, t->m2l_items, t->m2l_src, t->geo32,
                                                    t->geo_lo, t->n_m2l, t->m_df,
-                                                   reinterpret_cast<double*>(pp.Lam), t->counters);
+                                                   reinterpret_cast<double*>(pp.Lam), t->m2l_partial, t->counters);
   FMM_LAUNCH_CHECK();
   t->launches += 2;
+  if (t->n_m2l_split > 0) {
+    m2l_combine_kernel<double><<<grid_for(t->n_m2l_split * 32, 128), 128, 0, st>>>(
+        t->n_m2l_split, t->m2l_split_g, t->m2l_split_row, ncoef_pad(P), t->m2l_partial,
+        reinterpret_cast<double*>(pp.Lam));
+    FMM_LAUNCH_CHECK();
+    t->launches += 1;
+  }
   stage_event(t, FMM_STAGE_M2L, true, st);
 }
 
@@ -2129,20 +2325,27 @@ void run_m2l(const fmm_tree* t, const Ptrs& pp, cudaStream_t st, bool df_far = f
     attr_set = true;
   }
   stage_event(t, FMM_STAGE_M2L, false, st);
-  FMM_CUDA_TRY(cudaMemsetAsync(t->counters, 0, sizeof(int), st));
   int dev = 0, nsm = 0, occ = 0;
   FMM_CUDA_TRY(cudaGetDevice(&dev));
   FMM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, m2l_kernel<P>, 128, smem));
   if (occ < 1) occ = 1;
-  if (kOverlapFarField && occ > kM2LBlocksPerSM) occ = kM2LBlocksPerSM;
+  if (t->opt_schedule == kFarSide && occ > kM2LBlocksPerSM) occ = kM2LBlocksPerSM;
+  if (t->opt_m2l_blocks_per_sm > 0 && occ > t->opt_m2l_blocks_per_sm) occ = t->opt_m2l_blocks_per_sm;
   int64_t blocks = (int64_t)nsm * occ;
-  const int64_t need = (t->n_boxes + 3) / 4;
+  const int64_t need = (t->n_m2l_items + 3) / 4;
   if (blocks > need) blocks = need;
-  m2l_kernel<P><<<(int)blocks, 128, smem, st>>>(t->n_boxes, t->m2l_order, t->m2l_off, t->m2l_src,
-                                                pp.geo, t->n_m2l, pp.M, pp.Lam, t->counters);
+  real* partial = reinterpret_cast<real*>(t->m2l_partial);
+  m2l_kernel<P><<<(int)blocks, 128, smem, st>>>(t->n_m2l_items, t->m2l_items, t->m2l_src, pp.geo, t->n_m2l, pp.M,
+                                                pp.Lam, partial, t->counters);
   FMM_LAUNCH_CHECK();
   t->launches += 1;
+  if (t->n_m2l_split > 0) {
+    m2l_combine_kernel<real><<<grid_for(t->n_m2l_split * 32, 128), 128, 0, st>>>(
+        t->n_m2l_split, t->m2l_split_g, t->m2l_split_row, ncoef_pad(P), partial, pp.Lam);
+    FMM_LAUNCH_CHECK();
+    t->launches += 1;
+  }
   stage_event(t, FMM_STAGE_M2L, true, st);
 }
 
@@ -2223,7 +2426,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       attr_set = true;
     }
     const int64_t blocks = (a.n_leaves + 3) / 4;
-    if (!field && t->sym) {
+    if (!field && t->sym && t->opt_near_sym) {
       static bool sym_attr = false;
       if (!sym_attr) {
         FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32s<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2245,7 +2448,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
     FMM_LAUNCH_CHECK();
     return;
   } else {
-    if (!field && t->sym && t->prm.precision == FMM_FP64DF) {
+    if (!field && t->sym && t->opt_near_sym && t->prm.precision == FMM_FP64DF) {
       static bool df_attr = false;
       if (!df_attr) {
         FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_dfs<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2262,7 +2465,7 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       FMM_LAUNCH_CHECK();
       return;
     }
-    if (!field && t->sym) {
+    if (!field && t->sym && t->opt_near_sym) {
       static bool sym_attr = false;
       if (!sym_attr) {
         FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f64s<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2277,8 +2480,8 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       FMM_LAUNCH_CHECK();
       return;
     }
-    // FP64 fields and two-tree evaluations: the one-sided kernel
-    FMM_CUDA_TRY(cudaMemsetAsync(t->counters + 1, 0, sizeof(int), st));
+    // FP64 fields and two-tree evaluations: the one-sided kernel (its work
+    // counter was cleared by the gather)
     static bool attr_set = false;
     if (!attr_set) {
       FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel<TPL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2312,21 +2515,35 @@ void run_p2p(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool
 
 // Does this evaluation use the symmetric near field (whose received slots a
 // gather adds before the local evaluation)?
-bool uses_sym(const fmm_tree* t, bool field) { return !field && t->sym; }
+bool uses_sym(const fmm_tree* t, bool field) { return !field && t->sym && t->opt_near_sym; }
 
 // The slot gather of the symmetric near field (after the near-field kernel).
 void run_sym_gather(const fmm_tree* t, real* near_u, cudaStream_t st) {
   if constexpr (kF32) {
-    sym_gather_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off,
-        reinterpret_cast<const float*>(t->sym_partial), (int64_t)t->sym_stride, reinterpret_cast<float*>(near_u));
+    sym_gather_kernel<<<grid_for(t->n_gchunks * 32, 128), 128, 0, st>>>(
+        t->n_gchunks, t->gch_leaf, t->gch_r0, t->gch_first, t->leaf_box, t->box_start, t->box_count,
+        t->sym_recv_off, reinterpret_cast<const float*>(t->sym_partial), (int64_t)t->sym_stride,
+        reinterpret_cast<float*>(near_u), reinterpret_cast<float*>(t->gpart));
+    FMM_LAUNCH_CHECK();
+    if (t->n_gmulti > 0) {
+      sym_combine_kernel<<<grid_for(t->n_gmulti * 32, 128), 128, 0, st>>>(
+          t->n_gmulti, t->gmulti_leaf, t->gch_first, t->leaf_box, t->box_start, t->box_count, (int64_t)t->sym_stride,
+          reinterpret_cast<const float*>(t->gpart), reinterpret_cast<float*>(near_u));
+      FMM_LAUNCH_CHECK();
+    }
   } else {
-    sym_gather_f64_kernel<<<grid_for(t->n_leaves * 32, 128), 128, 0, st>>>(
-        t->n_leaves, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off, t->sym_partial,
-        (int64_t)t->sym_stride, reinterpret_cast<double*>(near_u));
+    sym_gather_f64_kernel<<<grid_for(t->n_gchunks * 32, 128), 128, 0, st>>>(
+        t->n_gchunks, t->gch_leaf, t->gch_r0, t->gch_first, t->leaf_box, t->box_start, t->box_count,
+        t->sym_recv_off, t->sym_partial, (int64_t)t->sym_stride, reinterpret_cast<double*>(near_u), t->gpart);
+    FMM_LAUNCH_CHECK();
+    if (t->n_gmulti > 0) {
+      sym_combine_f64_kernel<<<grid_for(t->n_gmulti * 32, 128), 128, 0, st>>>(
+          t->n_gmulti, t->gmulti_leaf, t->gch_first, t->leaf_box, t->box_start, t->box_count, (int64_t)t->sym_stride,
+          t->gpart, reinterpret_cast<double*>(near_u));
+      FMM_LAUNCH_CHECK();
+    }
   }
-  FMM_LAUNCH_CHECK();
-  t->launches += 1;
+  t->launches += 1 + (t->n_gmulti > 0 ? 1 : 0);
 }
 
 template <class F>
@@ -2349,9 +2566,10 @@ void dispatch_p(int p, F&& f) {
 void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cudaStream_t st) {
   Ptrs pp = ptrs(t);
   stage_event(t, FMM_STAGE_SORT, false, st);
-  const bool df = !kF32 && t->prm.precision == FMM_FP64DF && t->sym && t->src_df && field == nullptr;
+  const bool df = !kF32 && t->prm.precision == FMM_FP64DF && t->sym && t->opt_near_sym && t->src_df && field == nullptr;
   gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, q, pp.pos, pp.src,
-                                                     kF32 ? t->src_dup : nullptr, df ? t->src_df : nullptr);
+                                                     kF32 ? t->src_dup : nullptr, df ? t->src_df : nullptr,
+                                                     t->counters, t->m2m_ready, t->m2m_ready ? t->n_boxes : 0);
   FMM_LAUNCH_CHECK();
   t->launches += 1;
   stage_event(t, FMM_STAGE_SORT, true, st);
@@ -2399,7 +2617,8 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     FMM_CUDA_TRY(cudaEventRecord(t->ev_join, t->far_stream));
     FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
   };
-  if (kSchedule == kSplitNear) {
+  const int schedule = t->opt_schedule;
+  if (schedule == kSplitNear) {
     const int64_t half = t->n_leaves / 2;
     fork();
     upward(t->far_stream);
@@ -2411,7 +2630,7 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     near_range(half, t->n_leaves, fmm_tree::kStageP2P2);
     if (sym) run_sym_gather(t, near_u, st);
     join();
-  } else if (kSchedule == kUpwardSide) {
+  } else if (schedule == kUpwardSide) {
     // P2M, M2M beside the near field; then the slot gather (memory bound)
     // beside M2L and L2L on the higher-priority stream (beside L2L alone:
     // 2.08 / 0.511 / 53.7 ms on the three workloads below, against 2.08 /
@@ -2430,7 +2649,7 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     } else {
       downward(st);
     }
-  } else if (kSchedule == kFarSide) {
+  } else if (schedule == kFarSide) {
     upward(st);
     fork();
     downward(t->far_stream);
@@ -2495,10 +2714,12 @@ void backward_impl(const fmm_tree* t, const double* q, const double* g, double* 
   real* near_f = reinterpret_cast<real*>(t->near_f);
   // near-field records of g, then of q (src32 ends up holding q)
   gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, g, pp.pos, pp.src, t->src_dup2,
-                                                     nullptr);
+                                                     nullptr, t->counters, t->m2m_ready,
+                                                     t->m2m_ready ? t->n_boxes : 0);
   FMM_LAUNCH_CHECK();
   gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, q, pp.pos, pp.src, t->src_dup,
-                                                     nullptr);
+                                                     nullptr, t->counters, t->m2m_ready,
+                                                     t->m2m_ready ? t->n_boxes : 0);
   FMM_LAUNCH_CHECK();
   t->launches += 2;
   require(t->max_leaf <= 128, "fused backward sweep needs leaves of at most 128 points");
@@ -2514,7 +2735,8 @@ void backward_impl(const fmm_tree* t, const double* q, const double* g, double* 
   });
   // far field of g: potential and field
   gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, g, pp.pos, pp.src, nullptr,
-                                                     nullptr);
+                                                     nullptr, t->counters, t->m2m_ready,
+                                                     t->m2m_ready ? t->n_boxes : 0);
   FMM_LAUNCH_CHECK();
   t->launches += 1;
   dispatch_p(t->prm.p, [&](auto pc) {

@@ -202,6 +202,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   m->src_leaf_box = m->leaf_box;
   build_symmetric(m, st);
   m->counters = dev_alloc<int>(m, 8);
+  m->m2m_ready = dev_alloc<int>(m, NB);
   m->status = dev_alloc<int>(m, 1);
   FMM_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));
   FMM_CUDA_TRY(cudaStreamSynchronize(st));

@@ -78,6 +78,7 @@ extern "C" int fmm_eval_potential_static(const fmm_tree* tree, const double* q, 
     view.Lam32 = reinterpret_cast<float*>(base + kOffLam);
     view.Lam64 = reinterpret_cast<double*>(base + kOffLam);
     view.counters = reinterpret_cast<int*>(base + kOffCtr);  // zeroed before every use
+    view.m2m_ready = nullptr;  // M2M one launch per round (no readiness flags in the array)
     view.sym = 0;  // the symmetric near field's slots are tree workspace; the one-sided kernel needs none
     view.prof_on = 0;
     view.prof_ev = nullptr;

@@ -178,6 +178,30 @@ __global__ void frame_rec_kernel(int64_t n_leaves, const int64_t* __restrict__ w
   }
 }
 
+// chunks of the slot gather: leaf l's received slots in pieces of at most
+// kGatherChunk (count, then fill in leaf order)
+__global__ void gch_count_kernel(int64_t n_leaves, const int64_t* __restrict__ recv_off, int64_t* __restrict__ nch,
+                                 int64_t* __restrict__ multi) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n_leaves; l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = recv_off[l + 1] - recv_off[l];
+    const int64_t k = (r + kGatherChunk - 1) / kGatherChunk;
+    nch[l] = k;
+    multi[l] = k > 1 ? 1 : 0;
+  }
+}
+__global__ void gch_fill_kernel(int64_t n_leaves, const int64_t* __restrict__ recv_off,
+                                const int64_t* __restrict__ first, const int64_t* __restrict__ multi_off,
+                                int32_t* __restrict__ gleaf, int64_t* __restrict__ gr0, int32_t* __restrict__ mleaf) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n_leaves; l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = first[l + 1] - first[l];
+    for (int64_t j = 0; j < k; j++) {
+      gleaf[first[l] + j] = (int32_t)l;
+      gr0[first[l] + j] = recv_off[l] + j * kGatherChunk;
+    }
+    if (k > 1) mleaf[multi_off[l]] = (int32_t)l;
+  }
+}
+
 // points of the source leaves a leaf's warp evaluates (its work list)
 __global__ void sym_cost_kernel(int64_t n_leaves, const int64_t* __restrict__ work_off,
                                 const int32_t* __restrict__ work, const int32_t* __restrict__ src,
@@ -238,6 +262,30 @@ void build_symmetric(fmm_tree* t, cudaStream_t st) {
       dev_alloc<float>(t, (size_t)std::max<int64_t>(t->n_slots, 1) * t->sym_stride));
   t->sym_partial_f64 = 0;
   trace_mark("  sym: slots");
+
+  // slot gather in chunks (a leaf that receives tens of thousands of slots,
+  // such as an outlier leaf of a Plummer sphere paired with every other leaf,
+  // is gathered by many warps)
+  {
+    int64_t* nchk = scratch_alloc<int64_t>(NL + 1);
+    int64_t* multi = scratch_alloc<int64_t>(NL + 1);
+    int64_t* multi_off = scratch_alloc<int64_t>(NL + 1);
+    FMM_CUDA_TRY(cudaMemsetAsync(nchk + NL, 0, sizeof(int64_t), st));
+    FMM_CUDA_TRY(cudaMemsetAsync(multi + NL, 0, sizeof(int64_t), st));
+    gch_count_kernel<<<grid_for(NL, 256), 256, 0, st>>>(NL, t->sym_recv_off, nchk, multi);
+    FMM_LAUNCH_CHECK();
+    t->gch_first = dev_alloc<int64_t>(t, NL + 1);
+    t->n_gchunks = exclusive_scan(nchk, t->gch_first, NL + 1, st);
+    t->n_gmulti = exclusive_scan(multi, multi_off, NL + 1, st);
+    t->gch_leaf = dev_alloc<int32_t>(t, std::max<int64_t>(t->n_gchunks, 1));
+    t->gch_r0 = dev_alloc<int64_t>(t, std::max<int64_t>(t->n_gchunks, 1));
+    t->gmulti_leaf = dev_alloc<int32_t>(t, std::max<int64_t>(t->n_gmulti, 1));
+    gch_fill_kernel<<<grid_for(NL, 256), 256, 0, st>>>(NL, t->sym_recv_off, t->gch_first, multi_off, t->gch_leaf,
+                                                       t->gch_r0, t->gmulti_leaf);
+    FMM_LAUNCH_CHECK();
+    t->gpart = dev_alloc<double>(t, (size_t)std::max<int64_t>(t->n_gchunks, 1) * t->sym_stride);
+    dev_free(nchk), dev_free(multi), dev_free(multi_off);
+  }
 
   // work order of the symmetric kernel: heaviest work list first
   int64_t* cost = scratch_alloc<int64_t>(std::max<int64_t>(NL, 1));

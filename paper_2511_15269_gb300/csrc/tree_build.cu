@@ -1516,6 +1516,7 @@ void finish_tree(fmm_tree* t, std::vector<Step>& steps, int32_t* p2p_t, int32_t*
     FMM_CUDA_TRY(cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming));
   }
   t->counters = dev_alloc<int>(t, 8);
+  t->m2m_ready = dev_alloc<int>(t, NB);
   t->status = dev_alloc<int>(t, 1);
   FMM_CUDA_TRY(cudaMemsetAsync(t->status, 0, sizeof(int), st));
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1637,11 +1638,6 @@ void prepare_df_far(fmm_tree* t, cudaStream_t st) {
 }
 
 namespace {
-// M2L list length of every target box
-__global__ void m2l_len_kernel(int64_t nb, const int64_t* __restrict__ off, int64_t* __restrict__ key) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nb; g += (int64_t)gridDim.x * blockDim.x)
-    key[g] = off[g + 1] - off[g];
-}
 // near-field work of every target leaf: its point count times the points of
 // its list's source leaves (one warp per leaf)
 __global__ void leaf_work_kernel(int64_t nl, const int64_t* __restrict__ off, const int32_t* __restrict__ src,
@@ -1658,19 +1654,91 @@ __global__ void leaf_work_kernel(int64_t nl, const int64_t* __restrict__ off, co
 }
 }  // namespace
 
+namespace {
+// items of every target (kM2LItem interactions at most), in target order
+__global__ void m2l_item_count_kernel(int64_t nb, const int64_t* __restrict__ off, int64_t* __restrict__ nit,
+                                      int64_t* __restrict__ nrow, int64_t* __restrict__ split) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nb; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t len = off[g + 1] - off[g];
+    const int64_t k = len > kM2LItem ? (len + kM2LItem - 1) / kM2LItem : 1;
+    nit[g] = k;
+    nrow[g] = k > 1 ? k : 0;
+    split[g] = k > 1 ? 1 : 0;
+  }
+}
+__global__ void m2l_item_fill_kernel(int64_t nb, const int64_t* __restrict__ off, const int64_t* __restrict__ item_off,
+                                     const int64_t* __restrict__ row_off, const int64_t* __restrict__ split_off,
+                                     M2LItem* __restrict__ items, int64_t* __restrict__ len_out,
+                                     int32_t* __restrict__ split_g, int64_t* __restrict__ split_row) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < nb; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = off[g], e = off[g + 1];
+    const int64_t k = item_off[g + 1] - item_off[g];
+    for (int64_t j = 0; j < k; j++) {
+      const int64_t ib = b + j * kM2LItem, ie = ib + kM2LItem < e ? ib + kM2LItem : e;
+      items[item_off[g] + j] = M2LItem{ib, ie, (int32_t)g, k > 1 ? (int32_t)(row_off[g] + j) : -1};
+      len_out[item_off[g] + j] = ie - ib;
+    }
+    if (k > 1) {
+      split_g[split_off[g]] = (int32_t)g;
+      split_row[split_off[g]] = row_off[g];
+    }
+  }
+}
+__global__ void gather_items_kernel(int64_t n, const int32_t* __restrict__ perm, const M2LItem* __restrict__ in,
+                                    M2LItem* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[perm[i]];
+}
+}  // namespace
+
+// M2L work items: every target's list, split into items of at most
+// kM2LItem interactions (a list of tens of thousands of interactions, as
+// outlier boxes of a Plummer sphere have, would otherwise keep one warp busy
+// for milliseconds), ordered longest first; and the near-field work order.
 void build_work_orders(fmm_tree* t, cudaStream_t st) {
   const int64_t NB = t->n_boxes, NL = t->n_leaves;
-  int64_t* key = scratch_alloc<int64_t>(std::max(NB, NL));
-  t->m2l_order = dev_alloc<int32_t>(t, NB);
-  m2l_len_kernel<<<grid_for(NB, 256), 256, 0, st>>>(NB, t->m2l_off, key);
+  int64_t* nit = scratch_alloc<int64_t>(NB + 1);
+  int64_t* nrow = scratch_alloc<int64_t>(NB + 1);
+  int64_t* split = scratch_alloc<int64_t>(NB + 1);
+  int64_t* item_off = scratch_alloc<int64_t>(NB + 1);
+  int64_t* row_off = scratch_alloc<int64_t>(NB + 1);
+  int64_t* split_off = scratch_alloc<int64_t>(NB + 1);
+  FMM_CUDA_TRY(cudaMemsetAsync(nit + NB, 0, sizeof(int64_t), st));
+  FMM_CUDA_TRY(cudaMemsetAsync(nrow + NB, 0, sizeof(int64_t), st));
+  FMM_CUDA_TRY(cudaMemsetAsync(split + NB, 0, sizeof(int64_t), st));
+  m2l_item_count_kernel<<<grid_for(NB, 256), 256, 0, st>>>(NB, t->m2l_off, nit, nrow, split);
   FMM_LAUNCH_CHECK();
-  order_desc(key, NB, t->m2l_order, st);
+  const int64_t NI = exclusive_scan(nit, item_off, NB + 1, st);
+  const int64_t NR = exclusive_scan(nrow, row_off, NB + 1, st);
+  const int64_t NS = exclusive_scan(split, split_off, NB + 1, st);
+  M2LItem* items = scratch_alloc<M2LItem>(NI);
+  int64_t* len = scratch_alloc<int64_t>(NI);
+  int32_t* perm = scratch_alloc<int32_t>(NI);
+  t->n_m2l_items = NI;
+  t->n_m2l_split = NS;
+  t->m2l_items = dev_alloc<M2LItem>(t, NI);
+  t->m2l_split_g = dev_alloc<int32_t>(t, std::max<int64_t>(NS, 1));
+  t->m2l_split_row = dev_alloc<int64_t>(t, NS + 1);
+  t->m2l_partial_rows = NR;
+  t->m2l_partial = dev_alloc<double>(t, (size_t)std::max<int64_t>(NR, 1) * ncoef_pad(t->prm.p));
+  m2l_item_fill_kernel<<<grid_for(NB, 256), 256, 0, st>>>(NB, t->m2l_off, item_off, row_off, split_off, items, len,
+                                                          t->m2l_split_g, t->m2l_split_row);
+  FMM_LAUNCH_CHECK();
+  FMM_CUDA_TRY(cudaMemcpyAsync(t->m2l_split_row + NS, &NR, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  order_desc(len, NI, perm, st);
+  gather_items_kernel<<<grid_for(NI, 256), 256, 0, st>>>(NI, perm, items, t->m2l_items);
+  FMM_LAUNCH_CHECK();
+  dev_free(nit), dev_free(nrow), dev_free(split), dev_free(item_off), dev_free(row_off), dev_free(split_off);
+  dev_free(items), dev_free(len), dev_free(perm);
+
+  int64_t* key = scratch_alloc<int64_t>(std::max<int64_t>(NL, 1));
   t->leaf_order = dev_alloc<int32_t>(t, NL);
   leaf_work_kernel<<<grid_for(NL * 32, 256), 256, 0, st>>>(NL, t->p2p_off, t->p2p_src, t->leaf_box,
                                                           t->src_leaf_box, t->box_count, key);
   FMM_LAUNCH_CHECK();
   order_desc(key, NL, t->leaf_order, st);
   dev_free(key);
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
 // Direct L2L records of a tree whose lists, geometry and parents are set

@@ -19,6 +19,7 @@ FMM_FP64, FMM_FP32C, FMM_FP64DF = 0, 1, 2
 FMM_TIE_TARGET = 1
 FMM_SAME_LEVEL = 2
 FMM_POS_SOA = 4
+FMM_OPT_SCHEDULE, FMM_OPT_M2M_ONE_LAUNCH, FMM_OPT_NEAR_SYMMETRIC, FMM_OPT_M2L_BLOCKS_PER_SM = 1, 2, 3, 4
 FMM_MAX_P = 10
 
 # exported entry points, in include/fmm.h order
@@ -26,7 +27,7 @@ ENTRY_POINTS = ["fmm_device_peaks", "fmm_last_error", "fmm_set_device_memory_lim
                 "fmm_num_levels", "fmm_build_tree", "fmm_build_tree2", "fmm_tree_free",
                 "fmm_tree_merge",
                 "fmm_tree_point_offsets",
-                "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_set_wait_limit",
+                "fmm_tree_set_precision", "fmm_tree_stats", "fmm_tree_status", "fmm_tree_set_option", "fmm_tree_set_wait_limit",
                 "fmm_tree_export",
                 "fmm_tree_profile", "fmm_tree_stage_times", "fmm_eval_potential", "fmm_eval_field",
                 "fmm_eval_batched", "fmm_tree_workspace_bytes", "fmm_tree_set_workspace",
@@ -73,6 +74,7 @@ def lib():
         L.fmm_set_device_memory_limit.argtypes = [C.c_size_t]
         L.fmm_device_memory_in_use.argtypes = [C.POINTER(C.c_size_t)]
         L.fmm_tree_set_wait_limit.argtypes = [vp, i64]
+        L.fmm_tree_set_option.argtypes = [vp, i, i]
         L.fmm_num_levels.argtypes = [i64, i, i]
         L.fmm_num_levels.restype = i
         L.fmm_build_tree.argtypes = [vp, i64, C.POINTER(fmm_params), vp, C.POINTER(vp)]
@@ -245,6 +247,11 @@ def fmm_tree_stats(tree):
 
 def fmm_tree_status(tree):
     _check(lib().fmm_tree_status(tree.handle, _stream()))
+
+
+def fmm_tree_set_option(tree, option, value):
+    """Launch option of later evaluations (FMM_OPT_*)."""
+    _check(lib().fmm_tree_set_option(tree.handle, int(option), int(value)))
 
 
 def fmm_tree_set_wait_limit(tree, cycles):
