@@ -159,6 +159,16 @@ int fmm_set_device_memory_limit(size_t bytes);
 /* Device memory the library holds right now, in bytes (host pointer). */
 int fmm_device_memory_in_use(size_t* bytes);
 
+/* Device memory the library keeps reserved but unused after a build and
+ * after a tree is freed (its stream-ordered pool), so that the next build
+ * reuses it without mapping new memory; the rest goes back to the driver.
+ * Default 2 GiB; 0 returns all of it at those points.  With a cap set
+ * (fmm_set_device_memory_limit) at most the headroom under the cap is kept.
+ * Kept memory is not counted by fmm_device_memory_in_use.  Trims the
+ * current device's pool to the new size (after a device synchronisation).
+ * The paper has no counterpart (an allocator setting).  Always FMM_OK. */
+int fmm_set_pool_retention(size_t bytes);
+
 /* Number of levels L for n points (Sec. II.A step 4): the smallest l with
  * ceil(n / 2^(splits l)) <= leaf_size.  Returns -1 on invalid arguments. */
 int fmm_num_levels(int64_t n, int leaf_size, int splits);

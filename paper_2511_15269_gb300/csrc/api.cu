@@ -71,6 +71,8 @@ std::vector<WsItem> ws_items(fmm_tree* t) {
   add(&t->m2m_ready, sizeof(int) * NB);
   add(&t->m2l_partial, sizeof(double) * NCP * (size_t)std::max<int64_t>(t->m2l_partial_rows, 1));
   add(&t->gpart, sizeof(double) * (size_t)std::max<int64_t>(t->n_gchunks, 1) * std::max(t->sym_stride, 1));
+  add(&t->sym_partial4, 4 * sizeof(float) * (size_t)std::max<int64_t>(t->n_slots, 1) * std::max(t->sym_stride, 1));
+  add(&t->gpart4, 8 * sizeof(float) * (size_t)std::max<int64_t>(t->n_gchunks, 1) * std::max(t->sym_stride, 1));
   return v;
 }
 size_t ws_bytes(const std::vector<WsItem>& v) {
@@ -145,7 +147,7 @@ void free_tree(fmm_tree* t) {
                   t->counters, t->status,   t->leaf_box,  t->box_parent, t->up_ids,  t->l2d_off, t->l2d_anc,
                   t->two_trees ? t->src_leaf_box : nullptr, t->p2p_thr, t->sym_slot, t->sym_work_off,
                   t->sym_work, t->sym_recv_off, t->sym_partial, t->leaf_order_sym, t->sym_rec, t->src_df, t->sym_frame, t->src_dup2, t->near_u2, t->near_f2,
-                  t->m2m_ready};
+                  t->m2m_ready, t->sym_partial4, t->gpart4};
   for (void* p : ptrs)
     if (p) dev_free(p);
   if (t->prof_ev) {
@@ -171,6 +173,7 @@ std::mutex g_mem_mu;
 std::unordered_map<void*, LiveAlloc> g_live;  // library allocation -> size, origin
 size_t g_live_bytes = 0;
 size_t g_mem_limit = 0;  // 0: no cap
+size_t g_pool_keep = (size_t)2 << 30;  // unused pool memory kept for later builds
 cudaMemPool_t g_pool[64] = {};
 
 // The library's memory pool on the current device, created on first use;
@@ -199,6 +202,14 @@ cudaMemPool_t pool_for_device() {
 
 namespace {
 thread_local cudaStream_t tl_build_stream_end = nullptr;  // the outermost scope's stream
+
+// Unused pool memory to keep: the retention, within the headroom under a cap.
+size_t pool_keep_bytes() {
+  std::lock_guard<std::mutex> lk(g_mem_mu);
+  size_t keep = g_pool_keep;
+  if (g_mem_limit) keep = std::min(keep, g_mem_limit > g_live_bytes ? g_mem_limit - g_live_bytes : (size_t)0);
+  return keep;
+}
 }  // namespace
 
 void trim_pool() {
@@ -212,7 +223,7 @@ void trim_pool() {
   }
   if (pool) {
     cudaDeviceSynchronize();
-    cudaMemPoolTrimTo(pool, 0);
+    cudaMemPoolTrimTo(pool, pool_keep_bytes());
   }
 }
 
@@ -229,7 +240,7 @@ AllocScope::~AllocScope() {
     // the outermost scope gives the memory freed during the build back
     // (builds on other threads and streams keep theirs)
     cudaStreamSynchronize(tl_build_stream_end);
-    cudaMemPoolTrimTo(pool, 0);
+    cudaMemPoolTrimTo(pool, pool_keep_bytes());
   }
 }
 
@@ -297,6 +308,15 @@ const char* fmm_last_error(void) { return fmm::last_error(); }
 int fmm_set_device_memory_limit(size_t bytes) {
   std::lock_guard<std::mutex> lk(g_mem_mu);
   g_mem_limit = bytes;
+  return FMM_OK;
+}
+
+int fmm_set_pool_retention(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    g_pool_keep = bytes;
+  }
+  trim_pool();
   return FMM_OK;
 }
 
@@ -598,6 +618,7 @@ int fmm_eval_potential(const fmm_tree* t, const double* q, double* u, void* stre
 int fmm_eval_field(const fmm_tree* t, const double* q, double* u, double* field, void* stream) {
   return guarded([&] {
     require(t != nullptr && q != nullptr && field != nullptr, "NULL argument");
+    if (t->prm.precision == FMM_FP32C && t->opt_near_sym) ensure_sym_vec(const_cast<fmm_tree*>(t), (cudaStream_t)stream);
     eval_any(t, q, u, field, (cudaStream_t)stream);
   });
 }
@@ -702,7 +723,13 @@ int fmm_backward(const fmm_tree* t, const double* q, const double* grad_u, doubl
             "fmm_backward needs one point set; for separate source and target trees evaluate the "
             "transposed problem (sources and targets swapped) instead");
     cudaStream_t st = (cudaStream_t)stream;
-    if (grad_pos && t->prm.precision == FMM_FP32C && t->src_dup2 && t->max_leaf <= 128) {
+    const bool sym_vec = grad_pos && t->prm.precision == FMM_FP32C && t->src_dup2 && t->opt_near_sym &&
+                         ensure_sym_vec(const_cast<fmm_tree*>(t), st);
+    if (sym_vec) {
+      // one symmetric near-field sweep for both charge vectors beside both far
+      // fields, then a combine in tree order
+      backward_sym_fp32(t, q, grad_u, grad_q, grad_pos, st);
+    } else if (grad_pos && t->prm.precision == FMM_FP32C && t->src_dup2 && t->max_leaf <= 128) {
       // one near-field sweep for both charge vectors, then both far fields
       // (leaves of more than 128 points: two field evaluations below)
       backward_fp32(t, q, grad_u, grad_q, t->f_stage, t->g_stage, st);

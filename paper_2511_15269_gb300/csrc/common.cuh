@@ -184,6 +184,11 @@ struct fmm_tree {
   double* sym_partial = nullptr;      // n_slots x sym_stride floats (FP32C), doubles once
                                       // sym_partial_f64 is set (an FP64 precision was selected)
   int sym_partial_f64 = 0;
+  // vector variants of the symmetric near field (FP32C field and backward):
+  // (U, V) slot records, n_slots x sym_stride float4, and gather partials,
+  // n_gchunks x sym_stride x 8 floats; made on the first such evaluation
+  float* sym_partial4 = nullptr;
+  float* gpart4 = nullptr;
   fmm::SymRec* sym_rec = nullptr;     // per work entry, in work-list order
   // FP64DF near field: per-point double-float records (coordinates set at
   // build, charges by every evaluation's gather) and the source frame of
@@ -316,6 +321,11 @@ void ensure_fp64(fmm_tree* t, cudaStream_t st);
 // of its near field (once per tree)
 void prepare_df_far(fmm_tree* t, cudaStream_t st);
 void build_df_near(fmm_tree* t, cudaStream_t st);
+// symmetric.cu: the slot buffers of the symmetric near field's vector
+// variants (field and backward pass, FP32C; leaves of at most 128 points),
+// made on the first evaluation that uses them unless the caller's workspace
+// is attached; returns whether the tree has them.  Synchronous.
+bool ensure_sym_vec(fmm_tree* t, cudaStream_t st);
 // api.cu: releases every device array, stream and event of a tree
 void free_tree(fmm_tree* t);
 // merge.cu: a batch of trees as one tree-shaped object
@@ -329,6 +339,11 @@ void eval_fp64(const fmm_tree* t, const double* q, double* u, double* field, cud
 // g, caller's point order; one near-field sweep for both charge vectors.
 void backward_fp32(const fmm_tree* t, const double* q, const double* g, double* ug, double* fq, double* fg,
                    cudaStream_t st);
+// FP32C backward of one point set with the symmetric near field (vector slot
+// buffers present, leaves of at most 128 points): dL/dq (grad_q) and dL/dx
+// (grad_pos), both nullable, caller's point order.
+void backward_sym_fp32(const fmm_tree* t, const double* q, const double* g, double* grad_q, double* grad_pos,
+                       cudaStream_t st);
 // Per-precision one-time set-up: constant tables for every order.
 void init_tables_fp32();
 void init_tables_fp64();
@@ -346,10 +361,12 @@ void order_desc(const int64_t* key, int64_t n, int32_t* perm, cudaStream_t st);
 // items and leaf_order), on the device.
 void build_work_orders(fmm_tree* t, cudaStream_t st);
 
-// scan.cu: exclusive prefix sum of n int64 values (in place allowed);
-// returns the total (synchronises the stream).
+// scan.cu: exclusive prefix sum of n int64 values (in place allowed), one
+// launch; returns the total (synchronises the stream; FMM_ERR_TIMEOUT if a
+// bounded wait of the look-back gave up).  The asynchronous form leaves the
+// total in *total_dev and sets *err_dev (zeroed by the caller) on a timeout.
 int64_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
-void exclusive_scan_async(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
+void exclusive_scan_async(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev, int* err_dev,
                           cudaStream_t st);
 
 // api.cu: every device allocation of the library goes through these two, so

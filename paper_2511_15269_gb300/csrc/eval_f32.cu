@@ -21,5 +21,9 @@ void backward_fp32(const fmm_tree* t, const double* q, const double* g, double* 
                    cudaStream_t st) {
   backward_impl(t, q, g, ug, fq, fg, st);
 }
+void backward_sym_fp32(const fmm_tree* t, const double* q, const double* g, double* grad_q, double* grad_pos,
+                       cudaStream_t st) {
+  backward_sym_impl(t, q, g, grad_q, grad_pos, st);
+}
 void init_tables_fp32() { upload_tables(); }
 }  // namespace fmm

@@ -1274,8 +1274,7 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 4 : 2) p2p_kernel_bwd(P2PArgs 
 // step jj xor 8 then hold the same source, so the butterfly's first stage
 // needs no selects; at every step a warp reads four records whose
 // 16-byte halves fall in distinct banks.
-template <int NPH>
-__device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* dst, int j, int scount) {
+__device__ __forceinline__ float butterfly_sum(float (&P)[16], int l16) {
 #pragma unroll
   for (int i = 0; i < 8; i++) P[i] += __shfl_xor_sync(0xffffffffu, P[i + 8], 8);
   // after the stages with masks 4, 2, 1 lane l16 holds the half-warp sum of
@@ -1290,7 +1289,12 @@ __device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* 
       P[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
     }
   }
-  if (j < scount) dst[j] = P[0];
+  return P[0];
+}
+template <int NPH>
+__device__ __forceinline__ void butterfly_store(float (&P)[16], int l16, float* dst, int j, int scount) {
+  const float v = butterfly_sum(P, l16);
+  if (j < scount) dst[j] = v;
 }
 
 // One chunk of 32 sources (16 per half-warp): u of the lane's targets in pu,
@@ -1582,6 +1586,445 @@ __global__ void __launch_bounds__(128) sym_combine_kernel(int64_t n_multi, const
       }
       near_u[2 * (start + i)] = h;
       near_u[2 * (start + i) + 1] = l;
+    }
+  }
+}
+
+// ---- E6 (FP32C, one point set): symmetric near field of a vector quantity ------
+// The symmetric scheme of p2p_kernel_f32s for evaluations that need, besides
+// 1/r, the vector d / r^3 (d = x_t - x_s) at both points of a pair.  Each
+// point ends with a potential-like sum U (compensated, as the potential) and a
+// vector sum V:
+//   kSvField (the field of the charges q):
+//     U_t = sum_s q_s / r,  V_t = sum_s q_s d_ts / r^3   (the source side of a
+//     pair gets q_t / r and q_t d_st / r^3 = -q_t d_ts / r^3);
+//   kSvBackward (the near-field part of the backward pass, charges q and
+//   cotangents g = dL/du):
+//     U_t = sum_s g_s / r  (the potential of g, for dL/dq), and
+//     V_t = sum_s (g_t q_s + q_t g_s) d_ts / r^3, whose coefficient is the
+//     same for both points of a pair, so the source side gets -V's term; up to
+//     the factor 1/(4 pi) it is the near part of dL/dx_t (the gradient of
+//     sum_ij g_i K_ij q_j with K = -1/(4 pi r)).
+// The source side of a pair is summed over the lane's targets in registers,
+// then over the half-warp by four reduce-scatter butterflies, and stored as
+// (U, V) float4 records to the pair's slot row; sv_gather_kernel adds the
+// received rows.  Targets and sources are both read from the DupRec tiles
+// (positions relative to their leaf's centre; q from `tile`, g from
+// `tile_g`), so the far field may rewrite the FP32 point records meanwhile.
+constexpr int kSvField = 0;
+constexpr int kSvBackward = 1;
+
+// One ordered pair, one-sided (self pairs and pairs listed one way): the
+// target side only.
+template <int MODE, bool MASK, int NPH>
+__device__ __forceinline__ void sv_pair_one(const ulonglong2 a, const ulonglong2 b, const f2 sg, const f2 (&tx)[NPH],
+                                            const f2 (&ty)[NPH], const f2 (&tz)[NPH], const f2 (&tq)[NPH],
+                                            const f2 (&tg)[NPH], f2 (&pu)[NPH], f2 (&vx)[NPH], f2 (&vy)[NPH],
+                                            f2 (&vz)[NPH], float thr) {
+#pragma unroll
+  for (int k = 0; k < NPH; k++) {
+    const f2 dx = f2sub(tx[k], a.x), dy = f2sub(ty[k], a.y), dz = f2sub(tz[k], b.x);
+    const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+    float r0, r1;
+    f2unpack(r2, r0, r1);
+    float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
+    if (MASK) {
+      i0 = (r0 > thr) ? i0 : 0.f;
+      i1 = (r1 > thr) ? i1 : 0.f;
+    }
+    const f2 ri = f2pack(i0, i1);
+    const f2 ri3 = f2mul(f2mul(ri, ri), ri);
+    f2 w;
+    if (MODE == kSvField) {
+      pu[k] = f2fma(b.y, ri, pu[k]);
+      w = f2mul(b.y, ri3);
+    } else {
+      pu[k] = f2fma(sg, ri, pu[k]);
+      const f2 c = f2fma(tg[k], b.y, f2mul(tq[k], sg));
+      w = f2mul(c, ri3);
+    }
+    vx[k] = f2fma(w, dx, vx[k]);
+    vy[k] = f2fma(w, dy, vy[k]);
+    vz[k] = f2fma(w, dz, vz[k]);
+  }
+}
+
+// One chunk of 32 sources of a pair evaluated for both sides (source order
+// and butterfly as in sym_chunk): the target sums in pu, vx, vy, vz; the
+// lane's share of each source's sums in PU, PX, PY, PZ (V's source-side terms
+// with the sign of d_ts: negated when stored).
+template <int MODE, bool MASK, bool FULL, int NPH>
+__device__ __forceinline__ void sv_chunk(const ulonglong2* s2, const ulonglong2* g2, int c0, int half, int sw,
+                                         int scount, const f2 (&tx)[NPH], const f2 (&ty)[NPH],
+                                         const f2 (&tz)[NPH], const f2 (&tq)[NPH], const f2 (&tg)[NPH],
+                                         f2 (&pu)[NPH], f2 (&vx)[NPH], f2 (&vy)[NPH], f2 (&vz)[NPH],
+                                         float (&PU)[16], float (&PX)[16], float (&PY)[16], float (&PZ)[16],
+                                         float thr) {
+  const int r_lo = c0 + half + 2 * sw, r_hi = c0 + half + 2 - 2 * sw;
+#pragma unroll
+  for (int jj = 0; jj < 16; jj++) {
+    const int k = jj & 7;
+    const int j = (jj < 8 ? r_lo : r_hi) + 4 * k;
+    PU[jj] = PX[jj] = PY[jj] = PZ[jj] = 0.f;
+    if (FULL || j < scount) {
+      const ulonglong2 sa = s2[2 * j], sb = s2[2 * j + 1];
+      const f2 sg = (MODE == kSvBackward) ? g2[2 * j + 1].y : 0ull;
+      f2 au = 0ull, ax = 0ull, ay = 0ull, az = 0ull;
+#pragma unroll
+      for (int kk = 0; kk < NPH; kk++) {
+        const f2 dx = f2sub(tx[kk], sa.x), dy = f2sub(ty[kk], sa.y), dz = f2sub(tz[kk], sb.x);
+        const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+        float r0, r1;
+        f2unpack(r2, r0, r1);
+        float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
+        if (MASK) {
+          i0 = (r0 > thr) ? i0 : 0.f;
+          i1 = (r1 > thr) ? i1 : 0.f;
+        }
+        const f2 ri = f2pack(i0, i1);
+        const f2 ri3 = f2mul(f2mul(ri, ri), ri);
+        if (MODE == kSvField) {
+          pu[kk] = f2fma(sb.y, ri, pu[kk]);
+          const f2 ws = f2mul(sb.y, ri3);  // q_s / r^3
+          vx[kk] = f2fma(ws, dx, vx[kk]);
+          vy[kk] = f2fma(ws, dy, vy[kk]);
+          vz[kk] = f2fma(ws, dz, vz[kk]);
+          au = f2fma(tq[kk], ri, au);
+          const f2 wt = f2mul(tq[kk], ri3);  // q_t / r^3
+          ax = f2fma(wt, dx, ax);
+          ay = f2fma(wt, dy, ay);
+          az = f2fma(wt, dz, az);
+        } else {
+          pu[kk] = f2fma(sg, ri, pu[kk]);
+          au = f2fma(tg[kk], ri, au);
+          const f2 c = f2fma(tg[kk], sb.y, f2mul(tq[kk], sg));
+          const f2 w = f2mul(c, ri3);
+          vx[kk] = f2fma(w, dx, vx[kk]);
+          vy[kk] = f2fma(w, dy, vy[kk]);
+          vz[kk] = f2fma(w, dz, vz[kk]);
+          ax = f2fma(w, dx, ax);
+          ay = f2fma(w, dy, ay);
+          az = f2fma(w, dz, az);
+        }
+      }
+      float a0, a1;
+      f2unpack(au, a0, a1);
+      PU[jj] = a0 + a1;
+      f2unpack(ax, a0, a1);
+      PX[jj] = a0 + a1;
+      f2unpack(ay, a0, a1);
+      PY[jj] = a0 + a1;
+      f2unpack(az, a0, a1);
+      PZ[jj] = a0 + a1;
+    }
+  }
+}
+
+template <int TPL, int MODE>
+__global__ void __launch_bounds__(128, TPL <= 2 ? 3 : 2) p2p_kernel_f32sv(P2PArgs a) {
+  constexpr bool BWD = MODE == kSvBackward;
+  constexpr int CAP = TPL * 32;
+  constexpr int WARPS = 4;
+  constexpr int NT = 2 * TPL;
+  constexpr int NPH = TPL;
+  constexpr int NTILE = BWD ? 2 : 1;  // staged tiles per source leaf: q (and g)
+  extern __shared__ __align__(128) unsigned char p2p_smem[];
+  DupRec (*sbuf)[2][NTILE][CAP] = reinterpret_cast<DupRec (*)[2][NTILE][CAP]>(p2p_smem);
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const DupRec* tile = reinterpret_cast<const DupRec*>(a.tile);
+  const DupRec* tile_g = a.tile_g;
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int half = lane >> 4, l16 = lane & 15;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+  if (t >= a.n_leaves) return;
+  const int64_t leaf = a.order[t];
+  const int64_t g = a.leaf_box[leaf];
+  const int64_t tstart = a.box_start[g];
+  const int tcnt = a.box_count[g];
+  float tx0[NT], ty0[NT], tz0[NT], tq0[NT], tg0[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const int i = l16 + 16 * k;
+    if (i < tcnt) {
+      const DupRec p = tile[tstart + i];
+      tx0[k] = p.x0;
+      ty0[k] = p.y0;
+      tz0[k] = p.z0;
+      tq0[k] = p.q0;
+      tg0[k] = BWD ? tile_g[tstart + i].q0 : 0.f;
+    } else {
+      // absent targets far from every source, with zero charges: finite
+      // terms that add nothing to the sources' sums
+      tx0[k] = 1e18f;
+      ty0[k] = tz0[k] = tq0[k] = tg0[k] = 0.f;
+    }
+  }
+  f2 tq[NPH], tg[NPH], vx[NPH], vy[NPH], vz[NPH];
+#pragma unroll
+  for (int k = 0; k < NPH; k++) {
+    tq[k] = f2pack(tq0[2 * k], tq0[2 * k + 1]);
+    tg[k] = f2pack(tg0[2 * k], tg0[2 * k + 1]);
+    vx[k] = vy[k] = vz[k] = 0ull;
+  }
+  float hi[NT], lo[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) hi[k] = lo[k] = 0.f;
+  const int64_t kb = a.work_off[leaf];
+  const int nwk = (int)(a.work_off[leaf + 1] - kb);
+  SymRec mine{};
+  auto load_batch = [&](int base) {
+    if (base + lane < nwk) mine = a.rec[kb + base + lane];
+  };
+  auto bcast = [&](int src_lane) {
+    SymRec r;
+    r.start = __shfl_sync(0xffffffffu, mine.start, src_lane);
+    r.count = __shfl_sync(0xffffffffu, mine.count, src_lane);
+    r.slot = __shfl_sync(0xffffffffu, mine.slot, src_lane);
+    r.dx = __shfl_sync(0xffffffffu, mine.dx, src_lane);
+    r.dy = __shfl_sync(0xffffffffu, mine.dy, src_lane);
+    r.dz = __shfl_sync(0xffffffffu, mine.dz, src_lane);
+    r.thr = __shfl_sync(0xffffffffu, mine.thr, src_lane);
+    return r;
+  };
+  auto issue = [&](const SymRec& r, int buf) {
+    if (lane == 0) {
+      const uint32_t bytes = (uint32_t)(r.count * sizeof(DupRec));
+      fence_proxy_async();
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[buf])),
+                   "r"(NTILE * bytes)
+                   : "memory");
+      bulk_copy(sbuf[warp][buf][0], tile + r.start, bytes, &bar[buf]);
+      if (BWD) bulk_copy(sbuf[warp][buf][NTILE - 1], tile_g + r.start, bytes, &bar[buf]);
+    }
+  };
+  uint32_t phase = 0;
+  if (nwk > 0) {
+    load_batch(0);
+    issue(bcast(0), 0);
+  }
+  for (int w = 0; w < nwk; w++) {
+    const int buf = w & 1;
+    if (w > 0 && (w & 31) == 0) load_batch(w);  // warp-uniform
+    const SymRec en = bcast(w & 31);
+    if (w + 1 < nwk) {
+      const SymRec nx = ((w + 1) & 31) ? bcast((w + 1) & 31) : a.rec[kb + w + 1];
+      issue(nx, buf ^ 1);
+    }
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      // copies still in flight into this warp's buffers must land first
+      mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
+      return;
+    }
+    phase ^= 1u << buf;
+    const int scount = en.count;
+    const bool mask = en.thr >= 0.f;
+    const float thr = en.thr;
+    const int slot = en.slot;
+    const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
+    f2 tx[NPH], ty[NPH], tz[NPH], pu[NPH];
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      tx[k] = f2add(f2pack(tx0[2 * k], tx0[2 * k + 1]), ddx);
+      ty[k] = f2add(f2pack(ty0[2 * k], ty0[2 * k + 1]), ddy);
+      tz[k] = f2add(f2pack(tz0[2 * k], tz0[2 * k + 1]), ddz);
+      pu[k] = 0ull;
+    }
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sbuf[warp][buf][0]);
+    const ulonglong2* g2 = reinterpret_cast<const ulonglong2*>(sbuf[warp][buf][NTILE - 1]);
+    if (slot < 0) {
+      // one-sided: the self pair and pairs listed in one direction only
+      if (mask) {
+#pragma unroll 2
+        for (int j = half; j < scount; j += 2)
+          sv_pair_one<MODE, true, NPH>(s2[2 * j], s2[2 * j + 1], BWD ? g2[2 * j + 1].y : 0ull, tx, ty, tz, tq, tg,
+                                       pu, vx, vy, vz, thr);
+      } else {
+#pragma unroll 2
+        for (int j = half; j < scount; j += 2)
+          sv_pair_one<MODE, false, NPH>(s2[2 * j], s2[2 * j + 1], BWD ? g2[2 * j + 1].y : 0ull, tx, ty, tz, tq, tg,
+                                        pu, vx, vy, vz, thr);
+      }
+    } else {
+      float4* dst = reinterpret_cast<float4*>(a.partial) + (int64_t)slot * a.stride;
+      float PU[16], PX[16], PY[16], PZ[16];
+      const int sw = (l16 >> 3) & 1;
+      const int jmine = half + 4 * (l16 & 7) + 2 * sw;  // source of this lane after the butterflies
+      auto finish = [&](int c0) {
+        const float su = butterfly_sum(PU, l16);
+        const float sx = butterfly_sum(PX, l16);
+        const float sy = butterfly_sum(PY, l16);
+        const float sz = butterfly_sum(PZ, l16);
+        if (c0 + jmine < scount) dst[c0 + jmine] = make_float4(su, -sx, -sy, -sz);
+      };
+      int c0 = 0;
+      for (; c0 + 32 <= scount; c0 += 32) {
+        if (mask)
+          sv_chunk<MODE, true, true, NPH>(s2, g2, c0, half, sw, scount, tx, ty, tz, tq, tg, pu, vx, vy, vz, PU, PX,
+                                          PY, PZ, thr);
+        else
+          sv_chunk<MODE, false, true, NPH>(s2, g2, c0, half, sw, scount, tx, ty, tz, tq, tg, pu, vx, vy, vz, PU, PX,
+                                           PY, PZ, thr);
+        finish(c0);
+      }
+      if (c0 < scount) {
+        if (mask)
+          sv_chunk<MODE, true, false, NPH>(s2, g2, c0, half, sw, scount, tx, ty, tz, tq, tg, pu, vx, vy, vz, PU, PX,
+                                           PY, PZ, thr);
+        else
+          sv_chunk<MODE, false, false, NPH>(s2, g2, c0, half, sw, scount, tx, ty, tz, tq, tg, pu, vx, vy, vz, PU,
+                                            PX, PY, PZ, thr);
+        finish(c0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      float u0, u1;
+      f2unpack(pu[k], u0, u1);
+      two_sum(hi[2 * k], lo[2 * k], u0);
+      two_sum(hi[2 * k + 1], lo[2 * k + 1], u1);
+    }
+    __syncwarp();
+  }
+  // combine the two halves
+  float fx[NT], fy[NT], fz[NT];
+#pragma unroll
+  for (int k = 0; k < NPH; k++) {
+    f2unpack(vx[k], fx[2 * k], fx[2 * k + 1]);
+    f2unpack(vy[k], fy[2 * k], fy[2 * k + 1]);
+    f2unpack(vz[k], fz[2 * k], fz[2 * k + 1]);
+  }
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi[k], 16);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo[k], 16);
+    two_sum(hi[k], lo[k], oh);
+    lo[k] += ol;
+    fx[k] += __shfl_xor_sync(0xffffffffu, fx[k], 16);
+    fy[k] += __shfl_xor_sync(0xffffffffu, fy[k], 16);
+    fz[k] += __shfl_xor_sync(0xffffffffu, fz[k], 16);
+  }
+  if (half == 0) {
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+      const int i = l16 + 16 * k;
+      if (i < tcnt) {
+        const int64_t pidx = tstart + i;
+        a.near_u[2 * pidx] = hi[k];
+        a.near_u[2 * pidx + 1] = lo[k];
+        a.near_f[3 * pidx] = fx[k];
+        a.near_f[3 * pidx + 1] = fy[k];
+        a.near_f[3 * pidx + 2] = fz[k];
+      }
+    }
+  }
+}
+
+// Gather of the vector variants: every leaf adds the (U, V) rows it received
+// (list order) to its sums; chunking as in sym_gather_kernel, partial sums of
+// a leaf with several chunks in gpart rows of 8 floats per point
+// (U hi, U lo, Vx, Vy, Vz, unused).
+__global__ void __launch_bounds__(128) sv_gather_kernel(int64_t n_chunks, const int32_t* __restrict__ gch_leaf,
+                                                        const int64_t* __restrict__ gch_r0,
+                                                        const int64_t* __restrict__ gch_first,
+                                                        const int32_t* __restrict__ leaf_box,
+                                                        const int64_t* __restrict__ box_start,
+                                                        const int32_t* __restrict__ box_count,
+                                                        const int64_t* __restrict__ recv_off,
+                                                        const float4* __restrict__ partial, int64_t stride,
+                                                        float* __restrict__ near_u, float* __restrict__ near_v,
+                                                        float* __restrict__ gpart) {
+  const int lane = lane_id();
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; ch < n_chunks; ch += warps) {
+    const int64_t leaf = gch_leaf[ch];
+    const int64_t r0 = gch_r0[ch], r1 = min(r0 + kGatherChunk, recv_off[leaf + 1]);
+    const bool single = gch_first[leaf + 1] - gch_first[leaf] == 1;
+    const int64_t g = leaf_box[leaf];
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    for (int i = lane; i < cnt; i += 32) {
+      float h = 0.f, l = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+      if (single) {
+        const int64_t p = start + i;
+        h = near_u[2 * p];
+        l = near_u[2 * p + 1];
+        vx = near_v[3 * p];
+        vy = near_v[3 * p + 1];
+        vz = near_v[3 * p + 2];
+      }
+      for (int64_t r = r0; r < r1; r += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = (r + k < r1) ? partial[(r + k) * stride + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          if (r + k < r1) {
+            two_sum(h, l, v[k].x);
+            vx += v[k].y;
+            vy += v[k].z;
+            vz += v[k].w;
+          }
+        }
+      }
+      if (single) {
+        const int64_t p = start + i;
+        near_u[2 * p] = h;
+        near_u[2 * p + 1] = l;
+        near_v[3 * p] = vx;
+        near_v[3 * p + 1] = vy;
+        near_v[3 * p + 2] = vz;
+      } else {
+        float4* row = reinterpret_cast<float4*>(gpart) + 2 * (ch * stride + i);
+        row[0] = make_float4(h, l, vx, vy);
+        row[1] = make_float4(vz, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+}
+
+// Leaves gathered in several chunks: the chunks' (U, V) sums added in chunk
+// order.
+__global__ void __launch_bounds__(128) sv_combine_kernel(int64_t n_multi, const int32_t* __restrict__ mleaf,
+                                                         const int64_t* __restrict__ gch_first,
+                                                         const int32_t* __restrict__ leaf_box,
+                                                         const int64_t* __restrict__ box_start,
+                                                         const int32_t* __restrict__ box_count, int64_t stride,
+                                                         const float* __restrict__ gpart, float* __restrict__ near_u,
+                                                         float* __restrict__ near_v) {
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; k < n_multi; k += warps) {
+    const int64_t leaf = mleaf[k];
+    const int64_t g = leaf_box[leaf];
+    const int64_t start = box_start[g];
+    const int cnt = box_count[g];
+    for (int i = threadIdx.x & 31; i < cnt; i += 32) {
+      const int64_t p = start + i;
+      float h = near_u[2 * p], l = near_u[2 * p + 1];
+      float vx = near_v[3 * p], vy = near_v[3 * p + 1], vz = near_v[3 * p + 2];
+      for (int64_t ch = gch_first[leaf]; ch < gch_first[leaf + 1]; ch++) {
+        const float4* row = reinterpret_cast<const float4*>(gpart) + 2 * (ch * stride + i);
+        const float4 a0 = row[0], a1 = row[1];
+        two_sum(h, l, a0.x);
+        l += a0.y;
+        vx += a0.z;
+        vy += a0.w;
+        vz += a1.x;
+      }
+      near_u[2 * p] = h;
+      near_u[2 * p + 1] = l;
+      near_v[3 * p] = vx;
+      near_v[3 * p + 1] = vy;
+      near_v[3 * p + 2] = vz;
     }
   }
 }
@@ -2066,9 +2509,10 @@ __device__ __forceinline__ PointIn l2p_point_in(const vec4* __restrict__ src, co
   if (i < cnt) {
     const int64_t pidx = start + i;
     r.s = src[pidx];
-    r.nearv = kF32 ? (double)near_u[2 * pidx] + (double)near_u[2 * pidx + 1] : (double)near_u[pidx];
+    // no near sums (NULL): the far field alone
+    if (near_u) r.nearv = kF32 ? (double)near_u[2 * pidx] + (double)near_u[2 * pidx + 1] : (double)near_u[pidx];
     r.o = perm[pidx];
-    if (FIELD) {
+    if (FIELD && near_f) {
       r.nf[0] = near_f[3 * pidx];
       r.nf[1] = near_f[3 * pidx + 1];
       r.nf[2] = near_f[3 * pidx + 2];
@@ -2375,6 +2819,15 @@ void run_downward(const fmm_tree* t, const Ptrs& pp, cudaStream_t st, bool df_fa
   run_l2l<P>(t, pp, st);
 }
 
+// Does this evaluation use the symmetric near field (whose received slots a
+// gather adds before the local evaluation)?  Fields: the FP32C vector variant,
+// once its slot buffers exist (leaves of at most 128 points).
+bool uses_sym(const fmm_tree* t, bool field) {
+  if (!t->sym || !t->opt_near_sym) return false;
+  if (!field) return true;
+  return kF32 && t->sym_partial4 != nullptr && t->max_leaf <= 128;
+}
+
 template <int P>
 void run_l2p(const fmm_tree* t, const Ptrs& pp, const real* near_u, const real* near_f, double* u,
              double* field, cudaStream_t st) {
@@ -2442,6 +2895,27 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       p2p_kernel_f32s<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
       return;
+    }
+    if constexpr (TPL <= 4) {
+      if (field && uses_sym(t, true)) {
+        static bool sv_attr = false;
+        if (!sv_attr) {
+          FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32sv<TPL, kSvField>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32sv<TPL, kSvField>,
+                                            cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            (int)cudaSharedmemCarveoutMaxShared));
+          sv_attr = true;
+        }
+        a.order = t->leaf_order_sym + lb;
+        a.work_off = t->sym_work_off;
+        a.rec = t->sym_rec;
+        a.partial = t->sym_partial4;
+        a.stride = t->sym_stride;
+        p2p_kernel_f32sv<TPL, kSvField><<<(unsigned)blocks, 128, smem, st>>>(a);
+        FMM_LAUNCH_CHECK();
+        return;
+      }
     }
     if (field) p2p_kernel_f32h<TPL, true><<<(unsigned)blocks, 128, smem, st>>>(a);
     else p2p_kernel_f32h<TPL, false><<<(unsigned)blocks, 128, smem, st>>>(a);
@@ -2513,13 +2987,29 @@ void run_p2p(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, bool
   else run_p2p_tpl<8>(t, pp, near_u, near_f, field, lb, le, st);
 }
 
-// Does this evaluation use the symmetric near field (whose received slots a
-// gather adds before the local evaluation)?
-bool uses_sym(const fmm_tree* t, bool field) { return !field && t->sym && t->opt_near_sym; }
+// The slot gather of the symmetric near field's vector variants: (U, V)
+// rows into near_u (hi, lo) and near_v (3 floats per point).
+void run_sv_gather(const fmm_tree* t, float* near_u, float* near_v, cudaStream_t st) {
+  sv_gather_kernel<<<grid_for(t->n_gchunks * 32, 128), 128, 0, st>>>(
+      t->n_gchunks, t->gch_leaf, t->gch_r0, t->gch_first, t->leaf_box, t->box_start, t->box_count, t->sym_recv_off,
+      reinterpret_cast<const float4*>(t->sym_partial4), (int64_t)t->sym_stride, near_u, near_v, t->gpart4);
+  FMM_LAUNCH_CHECK();
+  if (t->n_gmulti > 0) {
+    sv_combine_kernel<<<grid_for(t->n_gmulti * 32, 128), 128, 0, st>>>(
+        t->n_gmulti, t->gmulti_leaf, t->gch_first, t->leaf_box, t->box_start, t->box_count, (int64_t)t->sym_stride,
+        t->gpart4, near_u, near_v);
+    FMM_LAUNCH_CHECK();
+  }
+  t->launches += 1 + (t->n_gmulti > 0 ? 1 : 0);
+}
 
 // The slot gather of the symmetric near field (after the near-field kernel).
-void run_sym_gather(const fmm_tree* t, real* near_u, cudaStream_t st) {
+void run_sym_gather(const fmm_tree* t, real* near_u, real* near_f, bool field, cudaStream_t st) {
   if constexpr (kF32) {
+    if (field) {
+      run_sv_gather(t, reinterpret_cast<float*>(near_u), reinterpret_cast<float*>(near_f), st);
+      return;
+    }
     sym_gather_kernel<<<grid_for(t->n_gchunks * 32, 128), 128, 0, st>>>(
         t->n_gchunks, t->gch_leaf, t->gch_r0, t->gch_first, t->leaf_box, t->box_start, t->box_count,
         t->sym_recv_off, reinterpret_cast<const float*>(t->sym_partial), (int64_t)t->sym_stride,
@@ -2628,7 +3118,7 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     fork();
     l2l(t->far_stream);
     near_range(half, t->n_leaves, fmm_tree::kStageP2P2);
-    if (sym) run_sym_gather(t, near_u, st);
+    if (sym) run_sym_gather(t, near_u, near_f, field != nullptr, st);
     join();
   } else if (schedule == kUpwardSide) {
     // P2M, M2M beside the near field; then the slot gather (memory bound)
@@ -2643,7 +3133,7 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     join();
     if (sym) {
       fork();
-      run_sym_gather(t, near_u, t->far_stream);
+      run_sym_gather(t, near_u, near_f, field != nullptr, t->far_stream);
       downward(st);
       join();
     } else {
@@ -2654,13 +3144,13 @@ void eval_impl(const fmm_tree* t, const double* q, double* u, double* field, cud
     fork();
     downward(t->far_stream);
     near();
-    if (sym) run_sym_gather(t, near_u, st);
+    if (sym) run_sym_gather(t, near_u, near_f, field != nullptr, st);
     join();
   } else {
     upward(st);
     downward(st);
     near();
-    if (sym) run_sym_gather(t, near_u, st);
+    if (sym) run_sym_gather(t, near_u, near_f, field != nullptr, st);
   }
   stage_event(t, FMM_STAGE_L2P, false, st);
   dispatch_p(t->prm.p, [&](auto pc) {
@@ -2745,6 +3235,115 @@ void backward_impl(const fmm_tree* t, const double* q, const double* g, double* 
     run_downward<P>(t, pp, st);
     run_l2p<P>(t, pp, reinterpret_cast<real*>(t->near_u2), reinterpret_cast<real*>(t->near_f2), ug, fg, st);
   });
+}
+
+
+// Backward pass with the symmetric near field (FP32C, one point set, leaves of
+// at most 128 points, vector slot buffers present): one symmetric sweep gives
+// U = the near potential sums of g and the pair-symmetric vector C
+// (p2p_kernel_f32sv, kSvBackward); the far fields of q and then of g run
+// meanwhile on the tree's second stream (far parts only: L2P without near
+// sums), and a combine in tree order adds the near parts:
+//   dL/dq_i = (K g)_i = (far part) - U_i / (4 pi),
+//   dL/dx_i = -(g_i E^far_q,i + q_i E^far_g,i) + C_i / (4 pi).
+__global__ void backward_sym_combine_kernel(int64_t n, const int32_t* __restrict__ perm, int64_t out_base,
+                                            const double* __restrict__ q, const double* __restrict__ g,
+                                            const double* __restrict__ fq, const double* __restrict__ fg,
+                                            const float* __restrict__ near_u, const float* __restrict__ near_v,
+                                            double* __restrict__ grad_q, double* __restrict__ grad_pos) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = perm[i] - out_base;
+    if (grad_q) grad_q[o] -= kInv4Pi * ((double)near_u[2 * i] + (double)near_u[2 * i + 1]);
+    if (grad_pos) {
+      const double qi = q[o], gi = g[o];
+      for (int c = 0; c < 3; c++)
+        grad_pos[3 * o + c] = -(gi * fq[3 * o + c] + qi * fg[3 * o + c]) + kInv4Pi * (double)near_v[3 * i + c];
+    }
+  }
+}
+
+template <int TPL>
+void run_p2p_bwd_sym_tpl(const fmm_tree* t, cudaStream_t st) {
+  P2PArgs a{};
+  a.n_leaves = t->n_leaves;
+  a.leaf_box = t->leaf_box;
+  a.order = t->leaf_order_sym;
+  a.work_off = t->sym_work_off;
+  a.rec = t->sym_rec;
+  a.partial = t->sym_partial4;
+  a.stride = t->sym_stride;
+  a.box_start = t->box_start;
+  a.box_count = t->box_count;
+  a.tile = t->src_dup;
+  a.tile_g = t->src_dup2;
+  a.near_u = reinterpret_cast<real*>(t->near_u2);
+  a.near_f = reinterpret_cast<real*>(t->near_f2);
+  a.status = t->status;
+  a.wait_cycles = t->wait_cycles;
+  const size_t smem = (size_t)4 * 2 * 2 * TPL * 32 * 32;  // [warp][buf][q, g] 32-byte records
+  static bool attr_set = false;
+  if (!attr_set) {
+    FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32sv<TPL, kSvBackward>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32sv<TPL, kSvBackward>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+    attr_set = true;
+  }
+  p2p_kernel_f32sv<TPL, kSvBackward><<<(unsigned)((t->n_leaves + 3) / 4), 128, smem, st>>>(a);
+  FMM_LAUNCH_CHECK();
+  t->launches += 1;
+}
+
+template <int Unused = 0>
+void backward_sym_impl(const fmm_tree* t, const double* q, const double* g, double* grad_q, double* grad_pos,
+                       cudaStream_t st) {
+  Ptrs pp = ptrs(t);
+  // near-field records of g, then of q (the FP32 point records end up
+  // holding q for the far field of q)
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, g, pp.pos, pp.src, t->src_dup2,
+                                                     nullptr, t->counters, t->m2m_ready,
+                                                     t->m2m_ready ? t->n_boxes : 0);
+  FMM_LAUNCH_CHECK();
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->n_charges, t->perm, q, pp.pos, pp.src, t->src_dup,
+                                                     nullptr, t->counters, t->m2m_ready,
+                                                     t->m2m_ready ? t->n_boxes : 0);
+  FMM_LAUNCH_CHECK();
+  t->launches += 2;
+  FMM_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+  FMM_CUDA_TRY(cudaStreamWaitEvent(t->far_stream, t->ev_fork, 0));
+  // far fields on the second stream: q, then g (whose gather rewrites the
+  // FP32 point records only after q's local evaluation has read them)
+  cudaStream_t fs = t->far_stream;
+  dispatch_p(t->prm.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    run_upward<P>(t, pp, fs);
+    run_downward<P>(t, pp, fs);
+    run_l2p<P>(t, pp, nullptr, nullptr, nullptr, t->f_stage, fs);
+  });
+  gather_kernel<<<grid_for(t->n, 256), 256, 0, fs>>>(t->n, t->n_charges, t->perm, g, pp.pos, pp.src, nullptr,
+                                                     nullptr, t->counters, t->m2m_ready,
+                                                     t->m2m_ready ? t->n_boxes : 0);
+  FMM_LAUNCH_CHECK();
+  t->launches += 1;
+  dispatch_p(t->prm.p, [&](auto pc) {
+    constexpr int P = decltype(pc)::value;
+    run_upward<P>(t, pp, fs);
+    run_downward<P>(t, pp, fs);
+    run_l2p<P>(t, pp, nullptr, nullptr, grad_q, t->g_stage, fs);
+  });
+  // the near field on the caller's stream meanwhile
+  if (t->max_leaf <= 32) run_p2p_bwd_sym_tpl<1>(t, st);
+  else if (t->max_leaf <= 64) run_p2p_bwd_sym_tpl<2>(t, st);
+  else run_p2p_bwd_sym_tpl<4>(t, st);
+  run_sv_gather(t, t->near_u2, t->near_f2, st);
+  FMM_CUDA_TRY(cudaEventRecord(t->ev_join, fs));
+  FMM_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+  backward_sym_combine_kernel<<<grid_for(t->n, 256), 256, 0, st>>>(t->n, t->perm, t->out_base, q, g, t->f_stage,
+                                                                   t->g_stage, t->near_u2, t->near_f2, grad_q,
+                                                                   grad_pos);
+  FMM_LAUNCH_CHECK();
+  t->launches += 1;
 }
 
 }  // namespace

@@ -1,13 +1,30 @@
-// Exclusive prefix sums of int64 arrays on the device (reduce-then-scan:
-// per-block scans, a recursive scan of the block totals, then a fix-up).
+// Exclusive prefix sums of int64 arrays on the device: one launch, single
+// pass with decoupled look-back (Merrill & Garland, "Single-pass Parallel
+// Prefix Scan with Decoupled Look-back", 2016).  Blocks take tiles in the
+// order they start (a ticket counter), so a tile only ever waits for tiles
+// whose blocks are already running; every tile publishes its own sum at
+// once and its inclusive prefix as soon as it is known, and a tile's look-back
+// adds its predecessors' sums until it meets a published prefix.  The wait
+// for a predecessor is bounded (a clock limit, then an error word), so a
+// fault elsewhere cannot leave the scan spinning.
 #include "common.cuh"
 
 namespace fmm {
 namespace {
 
-constexpr int kScanThreads = 512;
-constexpr int kScanItems = 8;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr long long kScanWaitCycles = 2000000000ll;  // about a second at 2 GHz
+
+// Per-tile look-back record: the tile's own sum (flag 1) and its inclusive
+// prefix (flag 2), written before the flag that announces them.
+struct __align__(16) TileState {
+  int64_t agg;
+  int64_t incl;
+  int flag;
+  int pad;
+};
 
 __device__ int64_t block_exclusive(int64_t v, int64_t* total) {
   __shared__ int64_t warp_sums[kScanThreads / 32];
@@ -36,9 +53,18 @@ __device__ int64_t block_exclusive(int64_t v, int64_t* total) {
   return before + x - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_tiles(const int64_t* in, int64_t* out, int64_t n,
-                                                           int64_t* tile_sums) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+// ws: tiles TileStates, then the ticket counter (zeroed before the launch).
+// total: the sum of all n inputs; err: set when a look-back wait gave up.
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(const int64_t* in, int64_t* out, int64_t n,
+                                                            TileState* ws, unsigned* ticket, int64_t* total,
+                                                            int* err) {
+  __shared__ unsigned tile_sh;
+  __shared__ int64_t prefix_sh;
+  if (threadIdx.x == 0) tile_sh = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int64_t tile = tile_sh;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int64_t v[kScanItems];
   int64_t s = 0;
 #pragma unroll
@@ -46,71 +72,93 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles(const int64_t* in, in
     v[k] = (base + k < n) ? in[base + k] : 0;
     s += v[k];
   }
-  int64_t total;
-  int64_t run = block_exclusive(s, &total);
+  int64_t agg;
+  int64_t run = block_exclusive(s, &agg);
+  if (threadIdx.x == 0) {
+    volatile TileState* me = ws + tile;
+    int64_t excl = 0;
+    if (tile == 0) {
+      me->incl = agg;
+      __threadfence();
+      me->flag = 2;
+    } else {
+      me->agg = agg;
+      __threadfence();
+      me->flag = 1;
+      int64_t j = tile - 1;
+      const long long t0 = clock64();
+      while (j >= 0) {
+        volatile TileState* pj = ws + j;
+        const int f = pj->flag;
+        if (f == 0) {
+          if (clock64() - t0 > kScanWaitCycles) {
+            atomicExch(err, 1);
+            break;
+          }
+          continue;
+        }
+        __threadfence();
+        if (f == 2) {
+          excl += pj->incl;
+          break;
+        }
+        excl += pj->agg;
+        j--;
+      }
+      me->incl = excl + agg;
+      __threadfence();
+      me->flag = 2;
+    }
+    prefix_sh = excl;
+    if (tile == tiles - 1) *total = excl + agg;
+  }
+  __syncthreads();
+  run += prefix_sh;
 #pragma unroll
   for (int k = 0; k < kScanItems; k++) {
     if (base + k < n) out[base + k] = run;
     run += v[k];
   }
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-__global__ void add_tile_offsets(int64_t* out, int64_t n, const int64_t* tile_off) {
-  const int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
-  const int64_t add = tile_off[blockIdx.x];
-  for (int k = 0; k < kScanItems; k++) {
-    int64_t j = i + (int64_t)k * kScanThreads;
-    if (j < n) out[j] += add;
-  }
-}
-
-__global__ void write_total(const int64_t* in_last, const int64_t* out_last, int64_t* total) {
-  *total = *in_last + *out_last;
-}
-
-void scan_rec(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, int64_t* total_dev) {
+// Launches the scan; total_dev and err_dev receive the sum and the error word.
+void scan_launch(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev, int* err_dev, cudaStream_t st) {
   if (n <= 0) {
     FMM_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(int64_t), st));
     return;
   }
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
-  int64_t* sums = scratch_alloc<int64_t>((size_t)tiles + 1);
-  // keep the last input before an in-place scan overwrites it
-  int64_t* last_in = scratch_alloc<int64_t>(1);
-  FMM_CUDA_TRY(cudaMemcpyAsync(last_in, in + n - 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-  scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, sums);
+  require(tiles < ((int64_t)1 << 31), "scan too long");
+  const size_t ws_bytes = sizeof(TileState) * (size_t)tiles + 16;
+  unsigned char* ws = scratch_alloc<unsigned char>(ws_bytes);
+  FMM_CUDA_TRY(cudaMemsetAsync(ws, 0, ws_bytes, st));
+  scan_kernel<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, n, reinterpret_cast<TileState*>(ws),
+                                                        reinterpret_cast<unsigned*>(ws + sizeof(TileState) * tiles),
+                                                        total_dev, err_dev);
   FMM_LAUNCH_CHECK();
-  if (tiles > 1) {
-    int64_t* dummy = scratch_alloc<int64_t>(1);
-    scan_rec(sums, sums, tiles, st, dummy);
-    add_tile_offsets<<<(unsigned)tiles, kScanThreads, 0, st>>>(out, n, sums);
-    FMM_LAUNCH_CHECK();
-    FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    dev_free(dummy);
-  }
-  write_total<<<1, 1, 0, st>>>(last_in, out + n - 1, total_dev);
-  FMM_LAUNCH_CHECK();
-  FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  dev_free(sums);
-  dev_free(last_in);
+  dev_free(ws);  // stream-ordered: reused only after the scan has run
 }
 
 }  // namespace
 
-void exclusive_scan_async(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
+void exclusive_scan_async(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev, int* err_dev,
                           cudaStream_t st) {
-  scan_rec(in, out, n, st, total_dev);
+  scan_launch(in, out, n, total_dev, err_dev, st);
 }
 
 int64_t exclusive_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st) {
-  int64_t* tot = scratch_alloc<int64_t>(1);
-  scan_rec(in, out, n, st, tot);
-  int64_t h = 0;
-  FMM_CUDA_TRY(cudaMemcpyAsync(&h, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  int64_t* res = scratch_alloc<int64_t>(2);  // total, error word
+  FMM_CUDA_TRY(cudaMemsetAsync(res, 0, 2 * sizeof(int64_t), st));
+  scan_launch(in, out, n, res, reinterpret_cast<int*>(res + 1), st);
+  int64_t h[2] = {0, 0};
+  FMM_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  dev_free(tot);
-  return h;
+  dev_free(res);
+  if (h[1]) {
+    set_error("a bounded device-side wait gave up (prefix sum look-back)");
+    throw Fail{FMM_ERR_TIMEOUT};
+  }
+  return h[0];
 }
 
 }  // namespace fmm

@@ -90,14 +90,15 @@ void order_desc(const int64_t* key, int64_t n, int32_t* perm, cudaStream_t st) {
   int32_t* vb = scratch_alloc<int32_t>(n);
   int64_t* hist = scratch_alloc<int64_t>(256 * nblk);
   int64_t* pref = scratch_alloc<int64_t>(256 * nblk);
-  int64_t* total = scratch_alloc<int64_t>(1);
+  int64_t* total = scratch_alloc<int64_t>(2);  // total, error word of the scans
+  FMM_CUDA_TRY(cudaMemsetAsync(total + 1, 0, sizeof(int64_t), st));
   sort_keys_kernel<<<grid_for(n, 256), 256, 0, st>>>(key, n, ka, va);
   FMM_LAUNCH_CHECK();
   for (int pass = 0; pass < 4; pass++) {
     const int shift = 8 * pass;
     sort_hist_kernel<<<(unsigned)nblk, kSortThreads, 0, st>>>(ka, n, shift, nblk, hist);
     FMM_LAUNCH_CHECK();
-    exclusive_scan_async(hist, pref, 256 * nblk, total, st);
+    exclusive_scan_async(hist, pref, 256 * nblk, total, reinterpret_cast<int*>(total + 1), st);
     const bool last = pass == 3;
     sort_scatter_kernel<<<(unsigned)nblk, kSortThreads, 0, st>>>(ka, va, n, shift, nblk, pref, kb,
                                                                  last ? perm : vb);
@@ -105,7 +106,14 @@ void order_desc(const int64_t* key, int64_t n, int32_t* perm, cudaStream_t st) {
     std::swap(ka, kb);
     std::swap(va, vb);
   }
+  int64_t err = 0;
+  FMM_CUDA_TRY(cudaMemcpyAsync(&err, total + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
   dev_free(ka), dev_free(kb), dev_free(va), dev_free(vb), dev_free(hist), dev_free(pref), dev_free(total);
+  if (err) {
+    set_error("a bounded device-side wait gave up (prefix sum look-back)");
+    throw Fail{FMM_ERR_TIMEOUT};
+  }
 }
 
 }  // namespace fmm

@@ -318,4 +318,15 @@ void build_df_near(fmm_tree* t, cudaStream_t st) {
   FMM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
+bool ensure_sym_vec(fmm_tree* t, cudaStream_t st) {
+  if (!t->sym || t->max_leaf > 128) return false;
+  if (t->sym_partial4) return true;
+  if (t->ws_external) return false;  // evaluations allocate nothing beside a caller's workspace
+  const size_t stride = (size_t)std::max(t->sym_stride, 1);
+  t->sym_partial4 = dev_alloc<float>(t, 4 * (size_t)std::max<int64_t>(t->n_slots, 1) * stride);
+  t->gpart4 = dev_alloc<float>(t, 8 * (size_t)std::max<int64_t>(t->n_gchunks, 1) * stride);
+  FMM_CUDA_TRY(cudaStreamSynchronize(st));
+  return true;
+}
+
 }  // namespace fmm

@@ -199,10 +199,13 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const double* __re
                                                               const int32_t* __restrict__ idx, int64_t n,
                                                               const int64_t* __restrict__ starts, int nseg,
                                                               const Sel* __restrict__ sel, int d,
-                                                              unsigned* __restrict__ hist) {
+                                                              unsigned* __restrict__ hist,
+                                                              const int* __restrict__ prev_unresolved) {
   const int64_t c0 = (int64_t)blockIdx.x * kChunk;
   const int64_t c1 = min(c0 + kChunk, n);
   if (c0 >= n) return;
+  // every segment's pivot was settled by an earlier digit: nothing to count
+  if (prev_unresolved && *prev_unresolved == 0) return;
   const int s0 = seg_of(starts, nseg, c0), s1 = seg_of(starts, nseg, c1 - 1);
   __shared__ unsigned sh[256];
   if (s0 == s1) {
@@ -235,10 +238,11 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const double* __re
 // the pivot (the first bin whose cumulative count exceeds its rank), and the
 // bins are cleared for the next digit.
 __global__ void radix_select_kernel(Sel* __restrict__ sel, int nseg, int d, unsigned* __restrict__ hist,
-                                    int* __restrict__ unresolved) {
+                                    const int* __restrict__ prev_unresolved, int* __restrict__ unresolved) {
   const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (j >= nseg) return;  // whole warps leave together
+  if (prev_unresolved && *prev_unresolved == 0) return;  // all settled; the bins are clear
   unsigned* h = hist + (size_t)j * 256 + 8 * lane;
   Sel s = sel[j];
   if (!s.resolved) {
@@ -361,7 +365,7 @@ __global__ void __launch_bounds__(kThreads) partition_kernel(const double* __res
 }
 
 // ---- small segments: all remaining rounds and the leaf sort in one CTA ---------
-constexpr int kSmallThreads = 512;
+constexpr int kSmallThreads = 256;
 
 // Bitonic sort of the `total / sub` consecutive blocks of `sub` keys (sub a
 // power of two dividing total), each ascending in (kh, kl).
@@ -388,27 +392,30 @@ __device__ void bitonic_sort_blocks(unsigned long long* kh, unsigned long long* 
   }
 }
 
-__global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
+// One CTA per segment of at most kSmallCap points: every remaining round and
+// the leaf sort.  Shared memory holds only the sort keys and the points'
+// current order (local slot numbers); coordinates and original indices are
+// read through that order from global memory (the segment's 48 KB stay in
+// L1/L2), so four CTAs fit on an SM and all segments of a 2^20-point build
+// are resident at once.
+__global__ void __launch_bounds__(kSmallThreads, 4) small_segment_kernel(
     const double* __restrict__ X, const int32_t* __restrict__ idx, int64_t n,
     const int64_t* __restrict__ starts, int rounds, double* __restrict__ Xo, int32_t* __restrict__ perm) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int64_t g0 = starts[blockIdx.x], g1 = starts[blockIdx.x + 1];
   const int cnt = (int)(g1 - g0);
   const int nsub_max = 1 << rounds;
+  const double* Xs = X + g0;      // this segment's coordinates: Xs[a * n + l]
+  const int32_t* Is = idx + g0;   // and original indices
   // 8-byte items first, then 4-byte ones
   unsigned long long* kh = reinterpret_cast<unsigned long long*>(sm);
   unsigned long long* kl = kh + kSmallCap;
-  double* xa = reinterpret_cast<double*>(kl + kSmallCap);  // 3 x kSmallCap
-  double* xb = xa + 3 * kSmallCap;                         // 3 x kSmallCap
-  unsigned long long* bb = reinterpret_cast<unsigned long long*>(xb + 3 * kSmallCap);  // 6 x nsub_max
-  int32_t* ia = reinterpret_cast<int32_t*>(bb + 6 * nsub_max);
+  unsigned long long* bb = kl + kSmallCap;                 // 6 x nsub_max
+  int32_t* ia = reinterpret_cast<int32_t*>(bb + 6 * nsub_max);  // current order: local slots
   int32_t* ib = ia + kSmallCap;
   int* st = ib + kSmallCap;                                // nsub_max + 2
   int* axis = st + nsub_max + 2;                           // nsub_max
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    for (int a = 0; a < 3; a++) xa[a * kSmallCap + i] = X[a * n + g0 + i];
-    ia[i] = idx[g0 + i];
-  }
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) ia[i] = i;
   if (threadIdx.x == 0) {
     st[0] = 0;
     st[1] = cnt;
@@ -429,8 +436,9 @@ __global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
         if (st[mid] <= i) lo = mid;
         else hi = mid - 1;
       }
+      const int l = ia[i];
       for (int a = 0; a < 3; a++) {
-        unsigned long long k = okey(xa[a * kSmallCap + i]);
+        unsigned long long k = okey(Xs[a * n + l]);
         atomicMin(&bb[6 * lo + a], k);
         atomicMax(&bb[6 * lo + 3 + a], k);
       }
@@ -463,24 +471,18 @@ __global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
         else hi = mid - 1;
       }
       const int slot = lo * sub + (i - st[lo]);
-      kh[slot] = okey(xa[axis[lo] * kSmallCap + i]);
-      kl[slot] = ((unsigned long long)(uint32_t)ia[i] << 12) | (unsigned long long)i;
+      const int l = ia[i];
+      kh[slot] = okey(Xs[axis[lo] * n + l]);
+      kl[slot] = ((unsigned long long)(uint32_t)Is[l] << 12) | (unsigned long long)i;
     }
     __syncthreads();
     bitonic_sort_blocks(kh, kl, nsub * sub, sub);
     for (int i = threadIdx.x; i < nsub * sub; i += blockDim.x) {
       const int j = i / sub, k = i - j * sub;
-      if (k < st[j + 1] - st[j]) {
-        const int from = (int)(kl[i] & 0xfffull), to = st[j] + k;
-        for (int ax = 0; ax < 3; ax++) xb[ax * kSmallCap + to] = xa[ax * kSmallCap + from];
-        ib[to] = ia[from];
-      }
+      if (k < st[j + 1] - st[j]) ib[st[j] + k] = ia[(int)(kl[i] & 0xfffull)];
     }
     __syncthreads();
     {
-      double* t = xa;
-      xa = xb;
-      xb = t;
       int32_t* u = ia;
       ia = ib;
       ib = u;
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
       else hi = mid - 1;
     }
     const int slot = lo * sub + (i - st[lo]);
-    kh[slot] = (unsigned long long)(uint32_t)ia[i];
+    kh[slot] = (unsigned long long)(uint32_t)Is[ia[i]];
     kl[slot] = (unsigned long long)i;
   }
   __syncthreads();
@@ -522,16 +524,16 @@ __global__ void __launch_bounds__(kSmallThreads) small_segment_kernel(
   for (int i = threadIdx.x; i < nleaf * sub; i += blockDim.x) {
     const int j = i / sub, k = i - j * sub;
     if (k < st[j + 1] - st[j]) {
-      const int from = (int)kl[i], to = st[j] + k;
-      for (int ax = 0; ax < 3; ax++) Xo[ax * n + g0 + to] = xa[ax * kSmallCap + from];
-      perm[g0 + to] = ia[from];
+      const int l = ia[(int)kl[i]], to = st[j] + k;
+      for (int ax = 0; ax < 3; ax++) Xo[ax * n + g0 + to] = Xs[ax * n + l];
+      perm[g0 + to] = Is[l];
     }
   }
 }
 
 size_t small_smem_bytes(int rounds) {
   const size_t nsub = (size_t)1 << rounds;
-  return (size_t)kSmallCap * (8 + 8 + 24 + 24 + 4 + 4) + nsub * 48 + sizeof(int) * (2 * nsub + 2);
+  return (size_t)kSmallCap * (8 + 8 + 4 + 4) + nsub * 48 + sizeof(int) * (2 * nsub + 2);
 }
 
 // ---- geometry --------------------------------------------------------------------
@@ -1112,26 +1114,26 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   FMM_CUDA_TRY(cudaMemsetAsync(flag, 0, 4 * sizeof(int), st));
   canon_kernel<<<grid_for(n, 256), 256, 0, st>>>(pos, n, (t->prm.flags & FMM_POS_SOA) ? 1 : 0, Xa, Ia, flag);
   FMM_LAUNCH_CHECK();
-  int hflag = 0;
-  FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-  FMM_CUDA_TRY(cudaStreamSynchronize(st));
-  if (hflag) {
-    dev_free(Xa), dev_free(Xb), dev_free(Ia), dev_free(Ib), dev_free(flag);
-    require(false, "positions must be finite");
-  }
-  int has_dup = 0;
+  // the duplicate test runs on whatever was read (a non-finite position
+  // makes its answer meaningless, not unsafe), so that one round trip
+  // returns both flags
+  int hflag[2] = {0, 0};
   {
     int64_t tsize = 1;
     while (tsize < 2 * n) tsize <<= 1;
     int* tab = scratch_alloc<int>(tsize);
     FMM_CUDA_TRY(cudaMemsetAsync(tab, 0xff, sizeof(int) * tsize, st));
-    FMM_CUDA_TRY(cudaMemsetAsync(flag + 1, 0, sizeof(int), st));
     duplicate_kernel<<<grid_for(n, 256), 256, 0, st>>>(Xa, n, tab, tsize - 1, flag + 1);
     FMM_LAUNCH_CHECK();
-    FMM_CUDA_TRY(cudaMemcpyAsync(&has_dup, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FMM_CUDA_TRY(cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
     dev_free(tab);
   }
+  if (hflag[0]) {
+    dev_free(Xa), dev_free(Xb), dev_free(Ia), dev_free(Ib), dev_free(flag);
+    require(false, "positions must be finite");
+  }
+  const int has_dup = hflag[1];
   t->has_duplicates = has_dup;
   trace_mark("canon + duplicates");
 
@@ -1163,8 +1165,10 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
     unsigned long long* ctr = scratch_alloc<unsigned long long>(2 * (size_t)maxseg);
     unsigned* hist = scratch_alloc<unsigned>(256 * (size_t)maxseg);
     Sel* sel = scratch_alloc<Sel>(maxseg);
+    int* uflag = scratch_alloc<int>(12);  // per digit: some segment still unresolved
     FMM_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(unsigned) * 256 * (size_t)maxseg, st));
     const int nblk = (int)((n + kChunk - 1) / kChunk);
+    int guess = 5;  // digits queued before the first look (random keys of ~2^20 points)
     for (int r = 0; r < r0; r++) {
       const int ns = 1 << r;
       const int64_t* stt = starts + round_off[r];
@@ -1174,22 +1178,34 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
       FMM_LAUNCH_CHECK();
       seg_axis_kernel<<<(ns + 255) / 256, 256, 0, st>>>(bmin, bmax, stt, ns, sel);
       FMM_LAUNCH_CHECK();
-      // 8-bit digits of the 96-bit key; a resolved segment skips the later
-      // passes on the device, and the host looks at the flag only from the
-      // third digit on (random 64-bit keys of up to ~2^24 points are
-      // resolved by then), one synchronisation per round in the usual case
-      for (int d = 0; d < 12; d++) {
-        FMM_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
-        radix_hist_kernel<<<nblk, kThreads, 0, st>>>(Xa, Ia, n, stt, ns, sel, d, hist);
-        FMM_LAUNCH_CHECK();
-        radix_select_kernel<<<(ns + 3) / 4, 128, 0, st>>>(sel, ns, d, hist, flag);
-        FMM_LAUNCH_CHECK();
-        if (d >= 2) {
-          FMM_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-          FMM_CUDA_TRY(cudaStreamSynchronize(st));
-          if (!hflag) break;
+      // 8-bit digits of the 96-bit key.  As many digits as the previous
+      // round needed are queued at once (a resolved segment skips the later
+      // passes, and once every segment is resolved the remaining launches
+      // return at once); one host round trip reads the per-digit flags, and
+      // more digits follow only if some segment is still unresolved
+      FMM_CUDA_TRY(cudaMemsetAsync(uflag, 0, sizeof(int) * 12, st));
+      int queued = 0, need = 12;
+      while (queued < 12) {
+        const int upto = std::min(12, queued == 0 ? guess : queued + 1);
+        for (int d = queued; d < upto; d++) {
+          const int* prev = d > 0 ? uflag + d - 1 : nullptr;
+          radix_hist_kernel<<<nblk, kThreads, 0, st>>>(Xa, Ia, n, stt, ns, sel, d, hist, prev);
+          FMM_LAUNCH_CHECK();
+          radix_select_kernel<<<(ns + 3) / 4, 128, 0, st>>>(sel, ns, d, hist, prev, uflag + d);
+          FMM_LAUNCH_CHECK();
+        }
+        queued = upto;
+        int hf[12];
+        FMM_CUDA_TRY(cudaMemcpyAsync(hf, uflag, sizeof(int) * queued, cudaMemcpyDeviceToHost, st));
+        FMM_CUDA_TRY(cudaStreamSynchronize(st));
+        int d = 0;
+        while (d < queued && hf[d]) d++;
+        if (d < queued) {
+          need = d + 1;  // digit d left every segment resolved
+          break;
         }
       }
+      guess = std::max(need, 2);
       FMM_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * 2 * ns, st));
       partition_kernel<<<nblk, kThreads, 0, st>>>(Xa, Ia, n, stt, ns, sel, ctr, Xb, Ib);
       FMM_LAUNCH_CHECK();
@@ -1197,7 +1213,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
       std::swap(Ia, Ib);
     }
     FMM_CUDA_TRY(cudaStreamSynchronize(st));
-    dev_free(bmin), dev_free(bmax), dev_free(ctr), dev_free(hist), dev_free(sel);
+    dev_free(bmin), dev_free(bmax), dev_free(ctr), dev_free(hist), dev_free(sel), dev_free(uflag);
   }
   trace_mark("large bisection rounds");
 
@@ -1207,6 +1223,8 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
     const int rounds = R - r0;
     const size_t smem = small_smem_bytes(rounds);
     FMM_CUDA_TRY(cudaFuncSetAttribute(small_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FMM_CUDA_TRY(cudaFuncSetAttribute(small_segment_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
     small_segment_kernel<<<1 << r0, kSmallThreads, smem, st>>>(Xa, Ia, n, starts + round_off[r0], rounds, Xb,
                                                                t->perm);
     FMM_LAUNCH_CHECK();

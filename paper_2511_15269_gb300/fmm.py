@@ -24,6 +24,7 @@ FMM_MAX_P = 10
 
 # exported entry points, in include/fmm.h order
 ENTRY_POINTS = ["fmm_device_peaks", "fmm_last_error", "fmm_set_device_memory_limit", "fmm_device_memory_in_use",
+                "fmm_set_pool_retention",
                 "fmm_num_levels", "fmm_build_tree", "fmm_build_tree2", "fmm_tree_free",
                 "fmm_tree_merge",
                 "fmm_tree_point_offsets",
@@ -73,6 +74,7 @@ def lib():
         L.fmm_device_peaks.argtypes = [vp, vp]
         L.fmm_set_device_memory_limit.argtypes = [C.c_size_t]
         L.fmm_device_memory_in_use.argtypes = [C.POINTER(C.c_size_t)]
+        L.fmm_set_pool_retention.argtypes = [C.c_size_t]
         L.fmm_tree_set_wait_limit.argtypes = [vp, i64]
         L.fmm_tree_set_option.argtypes = [vp, i, i]
         L.fmm_num_levels.argtypes = [i64, i, i]
@@ -143,6 +145,11 @@ def fmm_last_error():
 def fmm_set_device_memory_limit(nbytes):
     """Caps the device memory the library holds (0: no cap)."""
     _check(lib().fmm_set_device_memory_limit(int(nbytes)))
+
+
+def fmm_set_pool_retention(nbytes):
+    """Unused device memory the library keeps for later builds (default 2 GiB)."""
+    _check(lib().fmm_set_pool_retention(int(nbytes)))
 
 
 def fmm_device_memory_in_use():

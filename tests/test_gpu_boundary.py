@@ -123,3 +123,30 @@ def test_eval_batched_matches_the_concatenated_evaluation(F):
     F.fmm_tree_status(B)
     with pytest.raises(F.FmmError):
         F.fmm_eval_batched(B, q_sets[:2])
+
+
+def test_pool_retention(F):
+    # unused pool memory after a tree is freed: kept up to the retention,
+    # given back with retention 0; a rebuild from kept memory gives the same
+    # tree
+    pos, q = workloads.uniform_cube(300000, seed=41)
+    pd, qd = cuda(pos), cuda(q)
+    torch.cuda.synchronize()
+    F.fmm_set_pool_retention(0)
+    free0 = torch.cuda.mem_get_info()[0]
+    try:
+        F.fmm_set_pool_retention(2 << 30)
+        T = F.fmm_build_tree(pd, 6, 64, 2, 0.5, F.FMM_FP32C)
+        tree_bytes = F.fmm_tree_stats(T)["device_bytes"]
+        u_a = F.fmm_eval_potential(T, qd).cpu().numpy()
+        T.free()
+        kept = free0 - torch.cuda.mem_get_info()[0]
+        assert tree_bytes <= kept <= (2 << 30) + (64 << 20)
+        T = F.fmm_build_tree(pd, 6, 64, 2, 0.5, F.FMM_FP32C)
+        u_b = F.fmm_eval_potential(T, qd).cpu().numpy()
+        np.testing.assert_array_equal(u_a, u_b)
+        T.free()
+        F.fmm_set_pool_retention(0)
+        assert free0 - torch.cuda.mem_get_info()[0] <= (64 << 20)
+    finally:
+        F.fmm_set_pool_retention(2 << 30)
