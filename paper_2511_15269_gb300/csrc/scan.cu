@@ -4,7 +4,8 @@
 // order they start (a ticket counter), so a tile only ever waits for tiles
 // whose blocks are already running; every tile publishes its own sum at
 // once and its inclusive prefix as soon as it is known, and a tile's look-back
-// adds its predecessors' sums until it meets a published prefix.  The wait
+// (one warp, 32 predecessors per step) adds its predecessors' sums until it
+// meets a published prefix.  The wait
 // for a predecessor is bounded (a clock limit, then an error word), so a
 // fault elsewhere cannot leave the scan spinning.
 #include "common.cuh"
@@ -74,43 +75,67 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(const int64_t* in, i
   }
   int64_t agg;
   int64_t run = block_exclusive(s, &agg);
-  if (threadIdx.x == 0) {
+  // warp 0 publishes this tile's sum and looks back over windows of 32
+  // predecessors at once: each lane waits for its predecessor's record, the
+  // nearest one with a published prefix ends the look-back
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
     volatile TileState* me = ws + tile;
+    if (lane == 0) {
+      if (tile == 0) {
+        me->incl = agg;
+      } else {
+        me->agg = agg;
+      }
+      __threadfence();
+      me->flag = tile == 0 ? 2 : 1;
+    }
     int64_t excl = 0;
-    if (tile == 0) {
-      me->incl = agg;
-      __threadfence();
-      me->flag = 2;
-    } else {
-      me->agg = agg;
-      __threadfence();
-      me->flag = 1;
-      int64_t j = tile - 1;
+    if (tile > 0) {
       const long long t0 = clock64();
-      while (j >= 0) {
-        volatile TileState* pj = ws + j;
-        const int f = pj->flag;
-        if (f == 0) {
-          if (clock64() - t0 > kScanWaitCycles) {
-            atomicExch(err, 1);
-            break;
+      int64_t j = tile - 1;  // top of the window
+      for (;;) {
+        const int64_t jj = j - lane;
+        int f = 2;
+        int64_t val = 0;
+        bool late = false;
+        if (jj >= 0) {
+          volatile TileState* pj = ws + jj;
+          f = pj->flag;
+          while (f == 0) {
+            if (clock64() - t0 > kScanWaitCycles) {
+              late = true;
+              break;
+            }
+            f = pj->flag;
           }
-          continue;
+          __threadfence();
+          if (f == 2) val = pj->incl;
+          else if (f == 1) val = pj->agg;
         }
-        __threadfence();
-        if (f == 2) {
-          excl += pj->incl;
+        if (__any_sync(0xffffffffu, late)) {
+          if (lane == 0) atomicExch(err, 1);
           break;
         }
-        excl += pj->agg;
-        j--;
+        const unsigned done = __ballot_sync(0xffffffffu, f == 2);
+        const int k = done ? __ffs(done) - 1 : 32;  // nearest predecessor with a prefix
+        int64_t c = lane <= k ? val : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        excl += c;
+        if (done) break;
+        j -= 32;
       }
-      me->incl = excl + agg;
-      __threadfence();
-      me->flag = 2;
+      if (lane == 0) {
+        me->incl = excl + agg;
+        __threadfence();
+        me->flag = 2;
+      }
     }
-    prefix_sh = excl;
-    if (tile == tiles - 1) *total = excl + agg;
+    if (lane == 0) {
+      prefix_sh = excl;
+      if (tile == tiles - 1) *total = excl + agg;
+    }
   }
   __syncthreads();
   run += prefix_sh;

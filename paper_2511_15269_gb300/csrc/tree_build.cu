@@ -531,6 +531,8 @@ __global__ void __launch_bounds__(kSmallThreads, 4) small_segment_kernel(
   }
 }
 
+// segments of at most kSmallCap = 2048 points split at most 11 more times
+constexpr int kSmallMaxRounds = 11;
 size_t small_smem_bytes(int rounds) {
   const size_t nsub = (size_t)1 << rounds;
   return (size_t)kSmallCap * (8 + 8 + 4 + 4) + nsub * 48 + sizeof(int) * (2 * nsub + 2);
@@ -1221,8 +1223,12 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   t->perm = dev_alloc<int32_t>(t, n);
   {
     const int rounds = R - r0;
+    require(rounds <= kSmallMaxRounds, "segment rounds beyond the small-segment kernel's tables");
     const size_t smem = small_smem_bytes(rounds);
-    FMM_CUDA_TRY(cudaFuncSetAttribute(small_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // one constant limit for every build (builds on other threads launch
+    // this kernel concurrently; a per-launch value could undercut theirs)
+    FMM_CUDA_TRY(cudaFuncSetAttribute(small_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)small_smem_bytes(kSmallMaxRounds)));
     FMM_CUDA_TRY(cudaFuncSetAttribute(small_segment_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
     small_segment_kernel<<<1 << r0, kSmallThreads, smem, st>>>(Xa, Ia, n, starts + round_off[r0], rounds, Xb,
