@@ -81,11 +81,12 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip FP64, backward, errors, CPU baseline")
     ap.add_argument("--n", type=int, default=None,
                     help="points of the uniform cube (default 2^20); smaller values are for profiling captures")
-    ap.add_argument("--only", default=None, choices=["build-cube", "build-plummer", "field", "backward"],
+    ap.add_argument("--only", default=None, choices=["build-cube", "build-plummer", "field", "backward", "batched"],
                     help="time one part alone and print its own JSON line: the tree build (--warmup untimed then "
                          "--steps timed builds) of the uniform cube or of the 4M Plummer workload "
                          "(FMM_BUILD_TRACE=1 in the environment prints every build's phase times), or the "
-                         "field / backward evaluation of the uniform cube (no extras)")
+                         "field / backward evaluation of the uniform cube, or the 64-set batch at leaf 64 with "
+                         "the default launch options (no extras)")
     return ap.parse_args()
 
 
@@ -109,6 +110,43 @@ def bench_only(args, cfg):
         pos, q = workloads.uniform_cube(c["n"], seed=0)
         name = "uniform cube N=%d, p=%d, leaf %d, s=%d, theta %g" % (c["n"], c["p"], c["leaf_size"], c["s"],
                                                                      c["theta"])
+    if args.only == "batched":
+        from paper_2511_15269_gb300 import autotune
+        cb = workloads.CONFIGS["batched64_p6"]
+        sets = workloads.batched_sets(64, seed=0)
+        B = autotune.build_batch([p for p, _ in sets], cb["p"], 64, cb["s"], cb["theta"], fmm.FMM_FP32C)
+        q_d = torch.from_numpy(np.concatenate([q for _, q in sets])).cuda()
+        u = torch.empty_like(q_d)
+        for _ in range(max(args.warmup, 3)):
+            fmm.fmm_eval_potential(B, q_d, u)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for a, b in ev:
+            a.record()
+            fmm.fmm_eval_potential(B, q_d, u)
+            b.record()
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        fmm.fmm_tree_profile(B, True)
+        fmm.fmm_eval_potential(B, q_d, u)
+        torch.cuda.synchronize()
+        fmm.fmm_tree_profile(B, False)
+        stages, calls = fmm.fmm_tree_stage_times(B)
+        n = int(q_d.numel())
+        st = fmm.fmm_tree_stats(B)
+        sm = {k: v / max(calls, 1) for k, v in stages.items()}
+        rates = {"p2p_TFLOP/s": 10.0 * st["n_p2p_pairs"] / (sm["p2p"] * 1e-3) / 1e12,
+                 "m2l_TFLOP/s": 2.0 * M2L_MACS[cb["p"]] * st["n_m2l"] / (sm["m2l"] * 1e-3) / 1e12,
+                 "n_p2p_pairs": st["n_p2p_pairs"], "n_m2l": st["n_m2l"]}
+        print(json.dumps({"metric": "batched evaluation time", "value": float(np.mean(ms)), "unit": "ms",
+                          "stage_rates": rates,
+                          "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+                          "workload": "64 sets, N log-uniform in [1e4, 5e5] (total %d), p=%d, leaf 64, theta %g, "
+                                      "FP32C, default launch options" % (n, cb["p"], cb["theta"]),
+                          "min_ms": float(np.min(ms)), "Mpoints/s": n / np.min(ms) / 1e3,
+                          "stage_ms": sm}))
+        return
     pos_d = torch.from_numpy(pos).cuda()
     if args.only.startswith("build"):
         times, st = [], None

@@ -137,6 +137,7 @@ struct fmm_tree {
   int64_t n_boxes = 0, n_leaves = 0;
   int64_t n_m2l = 0, n_p2p = 0, n_p2p_pairs = 0;
   int max_leaf = 0;          // largest leaf point count
+  int min_leaf = 0;          // smallest target leaf point count
   int has_duplicates = 0;    // two distinct points share a position
   double build_ms = 0;
   size_t device_bytes = 0;

@@ -360,15 +360,20 @@ __global__ void __launch_bounds__(128) m2l_kernel(int64_t n_items, const M2LItem
     __syncwarp();
     real* out = it.prow < 0 ? Lam + g * NCP : partial + (int64_t)it.prow * NCP;
     for (int c = lane; c < NCP; c += 32) {
-      real s = real(0), err = real(0);
+      real s = real(0);
       if (c < NC) {
-#pragma unroll 8
-        for (int j = 0; j < 32; j++) {
-          if (kF32) two_sum(s, err, rows[j * ROW + c]);
-          else s += rows[j * ROW + c];
-        }
+        // the 32 lane rows summed as a balanced tree (rounding error grows
+        // with log2 32 = 5 levels, not with 32 terms), in a fixed order
+        real x[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) x[j] = rows[j * ROW + c];
+#pragma unroll
+        for (int w = 16; w >= 1; w >>= 1)
+#pragma unroll
+          for (int j = 0; j < w; j++) x[j] += x[j + w];
+        s = x[0];
       }
-      out[c] = s + err;
+      out[c] = s;
     }
     __syncwarp();
   }
@@ -1336,6 +1341,183 @@ __device__ __forceinline__ void sym_chunk(const ulonglong2* s2, int c0, int half
       P[jj] = a0 + a1;
     }
   }
+}
+
+// One target leaf of the symmetric near field with NPH packed target pairs
+// per lane (2 NPH targets, 32 NPH per warp); the staging buffers hold
+// CAP-record source tiles.
+template <int NPH, int CAP>
+__device__ __forceinline__ void sym_leaf_f32(const P2PArgs& a, DupRec (&sb)[2][CAP], uint64_t* bar, int64_t leaf,
+                                             int64_t tstart, int tcnt) {
+  constexpr int NT = 2 * NPH;
+  const DupRec* tile = reinterpret_cast<const DupRec*>(a.tile);
+  const int lane = lane_id();
+  const int half = lane >> 4, l16 = lane & 15;
+  float tx0[NT], ty0[NT], tz0[NT], tq0[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const int i = l16 + 16 * k;
+    if (i < tcnt) {
+      const float4 p = reinterpret_cast<const float4*>(a.src)[tstart + i];
+      tx0[k] = p.x;
+      ty0[k] = p.y;
+      tz0[k] = p.z;
+      tq0[k] = p.w;
+    } else {
+      // absent targets far from every source (finite 1/r, zero charge): they
+      // must not add 0 * inf to the sources' sums
+      tx0[k] = 1e18f;
+      ty0[k] = tz0[k] = tq0[k] = 0.f;
+    }
+  }
+  f2 tq[NPH];
+#pragma unroll
+  for (int k = 0; k < NPH; k++) tq[k] = f2pack(tq0[2 * k], tq0[2 * k + 1]);
+  float hi[NT], lo[NT];
+#pragma unroll
+  for (int k = 0; k < NT; k++) hi[k] = lo[k] = 0.f;
+  const int64_t kb = a.work_off[leaf];
+  const int nwk = (int)(a.work_off[leaf + 1] - kb);
+  // work records: lane l holds the record of entry base + l of the current
+  // batch of 32; fields are broadcast per entry
+  SymRec mine{};
+  auto load_batch = [&](int base) {
+    if (base + lane < nwk) mine = a.rec[kb + base + lane];
+  };
+  auto bcast = [&](int src_lane) {
+    SymRec r;
+    r.start = __shfl_sync(0xffffffffu, mine.start, src_lane);
+    r.count = __shfl_sync(0xffffffffu, mine.count, src_lane);
+    r.slot = __shfl_sync(0xffffffffu, mine.slot, src_lane);
+    r.dx = __shfl_sync(0xffffffffu, mine.dx, src_lane);
+    r.dy = __shfl_sync(0xffffffffu, mine.dy, src_lane);
+    r.dz = __shfl_sync(0xffffffffu, mine.dz, src_lane);
+    r.thr = __shfl_sync(0xffffffffu, mine.thr, src_lane);
+    return r;
+  };
+  auto issue = [&](const SymRec& r, int buf) {
+    if (lane == 0) {
+      fence_proxy_async();
+      tma_load_1d(sb[buf], tile + r.start, (uint32_t)(r.count * sizeof(DupRec)), &bar[buf]);
+    }
+  };
+  uint32_t phase = 0;
+  if (nwk > 0) {
+    load_batch(0);
+    issue(bcast(0), 0);
+  }
+  for (int w = 0; w < nwk; w++) {
+    const int buf = w & 1;
+    if (w > 0 && (w & 31) == 0) load_batch(w);  // warp-uniform
+    const SymRec en = bcast(w & 31);
+    if (w + 1 < nwk) {
+      const SymRec nx = ((w + 1) & 31) ? bcast((w + 1) & 31) : a.rec[kb + w + 1];
+      issue(nx, buf ^ 1);
+    }
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      // copies still in flight into this warp's buffers must land first
+      mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
+      return;
+    }
+    phase ^= 1u << buf;
+    const int scount = en.count;
+    const bool mask = en.thr >= 0.f;
+    const float thr = en.thr;
+    const int slot = en.slot;
+    const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
+    f2 tx[NPH], ty[NPH], tz[NPH], pu[NPH];
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      tx[k] = f2add(f2pack(tx0[2 * k], tx0[2 * k + 1]), ddx);
+      ty[k] = f2add(f2pack(ty0[2 * k], ty0[2 * k + 1]), ddy);
+      tz[k] = f2add(f2pack(tz0[2 * k], tz0[2 * k + 1]), ddz);
+      pu[k] = 0ull;
+    }
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb[buf]);
+    if (slot < 0) {
+      // one-sided: the self pair and pairs listed in one direction only
+      f2 px[NPH], py[NPH], pz[NPH];
+      if (mask) p2p_tile_f32h<true, false, NPH>(sb[buf], scount, half, tx, ty, tz, pu, px, py, pz, thr);
+      else p2p_tile_f32h<false, false, NPH>(sb[buf], scount, half, tx, ty, tz, pu, px, py, pz, thr);
+    } else {
+      float* dst = reinterpret_cast<float*>(a.partial) + (int64_t)slot * a.stride;
+      float P[16];
+      int c0 = 0;
+      const int sw = (l16 >> 3) & 1;
+      const int jmine = half + 4 * (l16 & 7) + 2 * sw;  // source of this lane after the butterfly
+      for (; c0 + 32 <= scount; c0 += 32) {
+        if (mask) sym_chunk<true, true, NPH>(s2, c0, half, sw, scount, tx, ty, tz, tq, pu, P, thr);
+        else sym_chunk<false, true, NPH>(s2, c0, half, sw, scount, tx, ty, tz, tq, pu, P, thr);
+        butterfly_store<NPH>(P, l16, dst, c0 + jmine, scount);
+      }
+      if (c0 < scount) {
+        if (mask) sym_chunk<true, false, NPH>(s2, c0, half, sw, scount, tx, ty, tz, tq, pu, P, thr);
+        else sym_chunk<false, false, NPH>(s2, c0, half, sw, scount, tx, ty, tz, tq, pu, P, thr);
+        butterfly_store<NPH>(P, l16, dst, c0 + jmine, scount);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NPH; k++) {
+      float u0, u1;
+      f2unpack(pu[k], u0, u1);
+      two_sum(hi[2 * k], lo[2 * k], u0);
+      two_sum(hi[2 * k + 1], lo[2 * k + 1], u1);
+    }
+    __syncwarp();
+  }
+  // combine the two halves
+#pragma unroll
+  for (int k = 0; k < NT; k++) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi[k], 16);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo[k], 16);
+    two_sum(hi[k], lo[k], oh);
+    lo[k] += ol;
+  }
+  if (half == 0) {
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+      const int i = l16 + 16 * k;
+      if (i < tcnt) {
+        const int64_t pidx = tstart + i;
+        a.near_u[2 * pidx] = hi[k];
+        a.near_u[2 * pidx + 1] = lo[k];
+      }
+    }
+  }
+}
+
+// Symmetric near field kernel for trees whose smallest leaf fills at most
+// half of the warp's target slots (such as a batch of sets of different
+// sizes): such leaves take the half-width layout, so no lane computes for
+// absent targets in the second packed pair.  Trees of full leaves launch
+// p2p_kernel_f32s (the same per-leaf code written out in the kernel, which
+// keeps its register allocation).
+template <int TPL>
+__global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_kernel_f32s_half(P2PArgs a) {
+  constexpr int CAP = TPL * 32;
+  constexpr int WARPS = 4;
+  extern __shared__ __align__(128) unsigned char p2p_smem[];
+  DupRec (*sbuf)[2][CAP] = reinterpret_cast<DupRec (*)[2][CAP]>(p2p_smem);
+  __shared__ __align__(8) uint64_t bars[WARPS][2];
+  const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const int64_t t = (int64_t)blockIdx.x * WARPS + warp;
+  if (t >= a.n_leaves) return;
+  const int64_t leaf = a.order[t];
+  const int64_t g = a.leaf_box[leaf];
+  const int64_t tstart = a.box_start[g];
+  const int tcnt = a.box_count[g];
+  if (tcnt <= 16 * TPL) sym_leaf_f32<TPL / 2, CAP>(a, sbuf[warp], bar, leaf, tstart, tcnt);
+  else sym_leaf_f32<TPL, CAP>(a, sbuf[warp], bar, leaf, tstart, tcnt);
 }
 
 template <int TPL>
@@ -2882,9 +3064,17 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
     if (!field && t->sym && t->opt_near_sym) {
       static bool sym_attr = false;
       if (!sym_attr) {
-        FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32s<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32s<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
         FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32s<TPL>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                           (int)cudaSharedmemCarveoutMaxShared));
+        if constexpr (TPL >= 2) {
+          FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32s_half<TPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+          FMM_CUDA_TRY(cudaFuncSetAttribute(p2p_kernel_f32s_half<TPL>,
+                                            cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            (int)cudaSharedmemCarveoutMaxShared));
+        }
         sym_attr = true;
       }
       a.order = t->leaf_order_sym + lb;
@@ -2892,7 +3082,15 @@ void run_p2p_tpl(const fmm_tree* t, const Ptrs& pp, real* near_u, real* near_f, 
       a.rec = t->sym_rec;
       a.partial = t->sym_partial;
       a.stride = t->sym_stride;
-      p2p_kernel_f32s<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);
+      // leaves that fill at most half of the target slots exist
+      bool half_launched = false;
+      if constexpr (TPL >= 2) {
+        if (t->min_leaf <= 16 * TPL) {
+          p2p_kernel_f32s_half<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);
+          half_launched = true;
+        }
+      }
+      if (!half_launched) p2p_kernel_f32s<TPL><<<(unsigned)blocks, 128, smem, st>>>(a);
       FMM_LAUNCH_CHECK();
       return;
     }

@@ -8,6 +8,8 @@
 #include <chrono>
 #include <vector>
 
+#include <climits>
+
 #include "common.cuh"
 
 namespace fmm {
@@ -64,7 +66,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   m->s = s;
   m->n_trees = nt;
   std::vector<int64_t> po(nt + 1, 0), bo(nt + 1, 0), lo(nt + 1, 0), mo(nt + 1, 0), eo(nt + 1, 0);
-  int Lmax = 0, max_leaf = 0;
+  int Lmax = 0, max_leaf = 0, min_leaf = INT_MAX;
   int64_t pairs = 0;
   for (int k = 0; k < nt; k++) {
     const fmm_tree& t = *in[k];
@@ -75,6 +77,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
     eo[k + 1] = eo[k] + t.n_p2p;
     Lmax = std::max(Lmax, t.L);
     max_leaf = std::max(max_leaf, t.max_leaf);
+    min_leaf = std::min(min_leaf, t.min_leaf);
     pairs += t.n_p2p_pairs;
     m->prm.leaf_size = std::max(m->prm.leaf_size, t.prm.leaf_size);
     m->has_duplicates |= t.has_duplicates;
@@ -89,6 +92,7 @@ void merge_trees(fmm_tree* const* in, int nt, cudaStream_t st, fmm_tree* m) {
   m->n_p2p = NP;
   m->n_p2p_pairs = pairs;
   m->max_leaf = max_leaf;
+  m->min_leaf = nt > 0 ? min_leaf : 0;
   m->tree_point_off_h = new int64_t[nt + 1];
   for (int k = 0; k <= nt; k++) m->tree_point_off_h[k] = po[k];
   m->level_avg_host = new double[Lmax + 1]();

@@ -1106,6 +1106,7 @@ void build_hierarchy(fmm_tree* t, const double* pos, cudaStream_t st, double** b
   const int64_t NB = t->n_boxes, NL = t->n_leaves;
   const int64_t leaf_off = level_offset(L, s);
   t->max_leaf = (int)((n + NL - 1) / NL);
+  t->min_leaf = (int)(n / NL);  // median splits: every leaf holds floor or ceil of n / NL
 
   // ---- canonical SoA copy, validation ----
   double* Xa = scratch_alloc<double>(3 * (size_t)n);
@@ -1851,6 +1852,7 @@ void build_tree2(fmm_tree* m, const double* src, int64_t n_s, const double* trg,
     m->n_leaves = T->n_leaves;
     m->n_src_leaves = S->n_leaves;
     m->max_leaf = std::max(S->max_leaf, T->max_leaf);
+    m->min_leaf = T->min_leaf;
     m->level_avg_host = new double[S->L + T->L + 2];
     for (int l = 0; l <= S->L; l++) m->level_avg_host[l] = S->level_avg_host[l];
     for (int l = 0; l <= T->L; l++) m->level_avg_host[S->L + 1 + l] = T->level_avg_host[l];
