@@ -750,6 +750,19 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         ms_field = e0.elapsed_time(e1) / 3
+        # the field's near-field stage, for its roofline (18 flops per ordered pair)
+        fmm.fmm_tree_profile(T, True)
+        fmm.fmm_eval_field(T, q_d)
+        torch.cuda.synchronize()
+        fmm.fmm_tree_profile(T, False)
+        fst, fcalls = fmm.fmm_tree_stage_times(T)
+        f_p2p_ms = fst["p2p"] / max(fcalls, 1)
+        f_ach = 18.0 * st["n_p2p_pairs"] / (f_p2p_ms * 1e-3) / 1e12
+        rooflines["p2p_field"] = {
+            "bound": "alu", "kernel": "p2p_kernel_f32sv (symmetric near field with field, FP32 + MUFU rsqrt)",
+            "achieved": f_ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": f_ach / peak_tflops,
+            "traffic": recorded_traffic("p2p_kernel_f32sv_field", "cube%d_p%d" % (n, cfg["p"])),
+            "flops_per_pair": 18, "p2p_ms": f_p2p_ms}
         # the same with the one-sided near field (FMM_OPT_NEAR_SYMMETRIC = 0)
         fmm.fmm_tree_set_option(T, fmm.FMM_OPT_NEAR_SYMMETRIC, 0)
         ms_field1 = event_ms(lambda: fmm.fmm_eval_field(T, q_d), 3)
