@@ -155,3 +155,21 @@ def test_field_slot_buffers_and_caller_workspace(F, orc):
     # cotangent g = q: dL/dq = K q = u, dL/dx = -(q E_q + q E_q) = -2 q E
     assert rel_l2(gq2, u_o) <= TOL_FP32
     assert rel_l2(gp2, -2 * q[:, None] * f_o) <= TOL_FP32_GRAD
+
+
+@pytest.mark.parametrize("n,leaf", [(8348, 64), (16484, 128)])
+def test_half_width_layout_mixed_leaves(F, orc, n, leaf):
+    # leaves of floor / ceil(n / 4^L) points straddling half of the warp's
+    # target slots (32 | 33 points with 64 slots, 64 | 65 with 128): the
+    # potential kernel runs both layouts in one launch
+    pos, q = workloads.uniform_cube(n, 38)
+    T = F.fmm_build_tree(cuda(pos), 6, leaf, 2, 0.5, F.FMM_FP32C)
+    O = orc.Tree(pos, leaf, 2, 0.5)
+    u_o = O.eval(q, 6)
+    u = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    F.fmm_tree_status(T)
+    F.fmm_tree_set_option(T, F.FMM_OPT_NEAR_SYMMETRIC, 0)
+    u1 = F.fmm_eval_potential(T, cuda(q)).cpu().numpy()
+    print("n %d leaf %d: sym %.2e one-sided %.2e" % (n, leaf, rel_l2(u, u_o), rel_l2(u1, u_o)))
+    assert rel_l2(u, u_o) <= TOL_FP32
+    assert rel_l2(u, u1) <= TOL_FP32
