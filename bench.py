@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip FP64, backward, errors, CPU baseline")
     ap.add_argument("--n", type=int, default=None,
                     help="points of the uniform cube (default 2^20); smaller values are for profiling captures")
+    ap.add_argument("--sets", type=int, default=64,
+                    help="charge sets of --only batched (default 64; fewer for profiling captures)")
     ap.add_argument("--only", default=None, choices=["build-cube", "build-plummer", "field", "backward", "batched"],
                     help="time one part alone and print its own JSON line: the tree build (--warmup untimed then "
                          "--steps timed builds) of the uniform cube or of the 4M Plummer workload "
@@ -113,7 +115,7 @@ def bench_only(args, cfg):
     if args.only == "batched":
         from paper_2511_15269_gb300 import autotune
         cb = workloads.CONFIGS["batched64_p6"]
-        sets = workloads.batched_sets(64, seed=0)
+        sets = workloads.batched_sets(args.sets, seed=0)
         B = autotune.build_batch([p for p, _ in sets], cb["p"], 64, cb["s"], cb["theta"], fmm.FMM_FP32C)
         q_d = torch.from_numpy(np.concatenate([q for _, q in sets])).cuda()
         u = torch.empty_like(q_d)
@@ -142,8 +144,8 @@ def bench_only(args, cfg):
         print(json.dumps({"metric": "batched evaluation time", "value": float(np.mean(ms)), "unit": "ms",
                           "stage_rates": rates,
                           "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
-                          "workload": "64 sets, N log-uniform in [1e4, 5e5] (total %d), p=%d, leaf 64, theta %g, "
-                                      "FP32C, default launch options" % (n, cb["p"], cb["theta"]),
+                          "workload": "%d sets, N log-uniform in [1e4, 5e5] (total %d), p=%d, leaf 64, theta %g, "
+                                      "FP32C, default launch options" % (args.sets, n, cb["p"], cb["theta"]),
                           "min_ms": float(np.min(ms)), "Mpoints/s": n / np.min(ms) / 1e3,
                           "stage_ms": sm}))
         return

@@ -1488,6 +1488,205 @@ __device__ __forceinline__ void sym_leaf_f32(const P2PArgs& a, DupRec (&sb)[2][C
   }
 }
 
+// Quarter-warp layout for target leaves of at most 32 points: four groups
+// of 8 lanes take every fourth source record of a chunk of 32, and each lane
+// holds 4 targets i = l8 + 8 k as two packed pairs, so every record loaded
+// serves 4 targets (the half-warp layout serves 2 with such leaves).  The
+// sources' sums of a group's 8 records are reduced by a 3-stage
+// reduce-scatter over the group (lane l8 ends with its step l8's record).
+// Every leaf of at most 32 points takes this layout in every kernel, so a
+// batch evaluates its small leaves as the single trees do, bit for bit.
+template <bool MASK, bool FULL>
+__device__ __forceinline__ void symq_chunk(const ulonglong2* s2, int c0, int grp, int scount, const f2 (&tx)[2],
+                                           const f2 (&ty)[2], const f2 (&tz)[2], const f2 (&tq)[2], f2 (&pu)[2],
+                                           float (&P)[8], float thr) {
+#pragma unroll
+  for (int jj = 0; jj < 8; jj++) {
+    const int j = c0 + 4 * jj + grp;
+    P[jj] = 0.f;
+    if (FULL || j < scount) {
+      const ulonglong2 sa = s2[2 * j], sb = s2[2 * j + 1];
+      f2 acc = 0ull;
+#pragma unroll
+      for (int kk = 0; kk < 2; kk++) {
+        const f2 dx = f2sub(tx[kk], sa.x), dy = f2sub(ty[kk], sa.y), dz = f2sub(tz[kk], sb.x);
+        const f2 r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));
+        float r0, r1;
+        f2unpack(r2, r0, r1);
+        float i0 = rsqrt_mufu(r0), i1 = rsqrt_mufu(r1);
+        if (MASK) {
+          i0 = (r0 > thr) ? i0 : 0.f;
+          i1 = (r1 > thr) ? i1 : 0.f;
+        }
+        const f2 ri = f2pack(i0, i1);
+        pu[kk] = f2fma(sb.y, ri, pu[kk]);
+        acc = f2fma(tq[kk], ri, acc);
+      }
+      float a0, a1;
+      f2unpack(acc, a0, a1);
+      P[jj] = a0 + a1;
+    }
+  }
+}
+
+__device__ __forceinline__ float butterfly8_sum(float (&P)[8], int l8) {
+#pragma unroll
+  for (int m = 4; m >= 1; m >>= 1) {
+    const bool up = (l8 & m) != 0;
+#pragma unroll
+    for (int i = 0; i < m; i++) {
+      const float keep = up ? P[i + m] : P[i];
+      const float send = up ? P[i] : P[i + m];
+      P[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  return P[0];
+}
+
+template <int CAP>
+__device__ __forceinline__ void symq_leaf_f32(const P2PArgs& a, DupRec (&sb)[2][CAP], uint64_t* bar, int64_t leaf,
+                                              int64_t tstart, int tcnt) {
+  const DupRec* tile = reinterpret_cast<const DupRec*>(a.tile);
+  const int lane = lane_id();
+  const int grp = lane >> 3, l8 = lane & 7;
+  float tx0[4], ty0[4], tz0[4], tq0[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int i = l8 + 8 * k;
+    if (i < tcnt) {
+      const float4 p = reinterpret_cast<const float4*>(a.src)[tstart + i];
+      tx0[k] = p.x;
+      ty0[k] = p.y;
+      tz0[k] = p.z;
+      tq0[k] = p.w;
+    } else {
+      // absent targets far from every source, with zero charge
+      tx0[k] = 1e18f;
+      ty0[k] = tz0[k] = tq0[k] = 0.f;
+    }
+  }
+  f2 tq[2];
+#pragma unroll
+  for (int k = 0; k < 2; k++) tq[k] = f2pack(tq0[2 * k], tq0[2 * k + 1]);
+  float hi[4], lo[4];
+#pragma unroll
+  for (int k = 0; k < 4; k++) hi[k] = lo[k] = 0.f;
+  const int64_t kb = a.work_off[leaf];
+  const int nwk = (int)(a.work_off[leaf + 1] - kb);
+  SymRec mine{};
+  auto load_batch = [&](int base) {
+    if (base + lane < nwk) mine = a.rec[kb + base + lane];
+  };
+  auto bcast = [&](int src_lane) {
+    SymRec r;
+    r.start = __shfl_sync(0xffffffffu, mine.start, src_lane);
+    r.count = __shfl_sync(0xffffffffu, mine.count, src_lane);
+    r.slot = __shfl_sync(0xffffffffu, mine.slot, src_lane);
+    r.dx = __shfl_sync(0xffffffffu, mine.dx, src_lane);
+    r.dy = __shfl_sync(0xffffffffu, mine.dy, src_lane);
+    r.dz = __shfl_sync(0xffffffffu, mine.dz, src_lane);
+    r.thr = __shfl_sync(0xffffffffu, mine.thr, src_lane);
+    return r;
+  };
+  auto issue = [&](const SymRec& r, int buf) {
+    if (lane == 0) {
+      fence_proxy_async();
+      tma_load_1d(sb[buf], tile + r.start, (uint32_t)(r.count * sizeof(DupRec)), &bar[buf]);
+    }
+  };
+  uint32_t phase = 0;
+  if (nwk > 0) {
+    load_batch(0);
+    issue(bcast(0), 0);
+  }
+  for (int w = 0; w < nwk; w++) {
+    const int buf = w & 1;
+    if (w > 0 && (w & 31) == 0) load_batch(w);  // warp-uniform
+    const SymRec en = bcast(w & 31);
+    if (w + 1 < nwk) {
+      const SymRec nx = ((w + 1) & 31) ? bcast((w + 1) & 31) : a.rec[kb + w + 1];
+      issue(nx, buf ^ 1);
+    }
+    if (!mbar_wait(&bar[buf], (phase >> buf) & 1u, a.wait_cycles)) {
+      if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+      // copies still in flight into this warp's buffers must land first
+      mbar_wait(&bar[buf], (phase >> buf) & 1u, kDrainWaitCycles);
+      if (w + 1 < nwk) mbar_wait(&bar[buf ^ 1], (phase >> (buf ^ 1)) & 1u, kDrainWaitCycles);
+      return;
+    }
+    phase ^= 1u << buf;
+    const int scount = en.count;
+    const bool mask = en.thr >= 0.f;
+    const float thr = en.thr;
+    const int slot = en.slot;
+    const f2 ddx = f2pack(en.dx, en.dx), ddy = f2pack(en.dy, en.dy), ddz = f2pack(en.dz, en.dz);
+    f2 tx[2], ty[2], tz[2], pu[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      tx[k] = f2add(f2pack(tx0[2 * k], tx0[2 * k + 1]), ddx);
+      ty[k] = f2add(f2pack(ty0[2 * k], ty0[2 * k + 1]), ddy);
+      tz[k] = f2add(f2pack(tz0[2 * k], tz0[2 * k + 1]), ddz);
+      pu[k] = 0ull;
+    }
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb[buf]);
+    if (slot < 0) {
+      // one-sided: the self pair and pairs listed in one direction only
+      f2 px[2], py[2], pz[2];
+      for (int j = grp; j < scount; j += 4) {
+        if (mask) p2p_pair_f32<true, false, 2>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, px, py, pz, thr);
+        else p2p_pair_f32<false, false, 2>(s2[2 * j], s2[2 * j + 1], tx, ty, tz, pu, px, py, pz, thr);
+      }
+    } else {
+      float* dst = reinterpret_cast<float*>(a.partial) + (int64_t)slot * a.stride;
+      float P[8];
+      int c0 = 0;
+      for (; c0 + 32 <= scount; c0 += 32) {
+        if (mask) symq_chunk<true, true>(s2, c0, grp, scount, tx, ty, tz, tq, pu, P, thr);
+        else symq_chunk<false, true>(s2, c0, grp, scount, tx, ty, tz, tq, pu, P, thr);
+        const float v = butterfly8_sum(P, l8);
+        dst[c0 + 4 * l8 + grp] = v;
+      }
+      if (c0 < scount) {
+        if (mask) symq_chunk<true, false>(s2, c0, grp, scount, tx, ty, tz, tq, pu, P, thr);
+        else symq_chunk<false, false>(s2, c0, grp, scount, tx, ty, tz, tq, pu, P, thr);
+        const float v = butterfly8_sum(P, l8);
+        const int j = c0 + 4 * l8 + grp;
+        if (j < scount) dst[j] = v;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      float u0, u1;
+      f2unpack(pu[k], u0, u1);
+      two_sum(hi[2 * k], lo[2 * k], u0);
+      two_sum(hi[2 * k + 1], lo[2 * k + 1], u1);
+    }
+    __syncwarp();
+  }
+  // combine the four groups (lanes l8, l8 + 8, l8 + 16, l8 + 24)
+#pragma unroll
+  for (int m = 8; m <= 16; m <<= 1) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const float oh = __shfl_xor_sync(0xffffffffu, hi[k], m);
+      const float ol = __shfl_xor_sync(0xffffffffu, lo[k], m);
+      two_sum(hi[k], lo[k], oh);
+      lo[k] += ol;
+    }
+  }
+  if (grp == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int i = l8 + 8 * k;
+      if (i < tcnt) {
+        const int64_t pidx = tstart + i;
+        a.near_u[2 * pidx] = hi[k];
+        a.near_u[2 * pidx + 1] = lo[k];
+      }
+    }
+  }
+}
+
 // Symmetric near field kernel for trees whose smallest leaf fills at most
 // half of the warp's target slots (such as a batch of sets of different
 // sizes): such leaves take the half-width layout, so no lane computes for
@@ -1516,7 +1715,8 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
   const int64_t g = a.leaf_box[leaf];
   const int64_t tstart = a.box_start[g];
   const int tcnt = a.box_count[g];
-  if (tcnt <= 16 * TPL) sym_leaf_f32<TPL / 2, CAP>(a, sbuf[warp], bar, leaf, tstart, tcnt);
+  if (tcnt <= 32) symq_leaf_f32<CAP>(a, sbuf[warp], bar, leaf, tstart, tcnt);
+  else if (tcnt <= 16 * TPL) sym_leaf_f32<TPL / 2, CAP>(a, sbuf[warp], bar, leaf, tstart, tcnt);
   else sym_leaf_f32<TPL, CAP>(a, sbuf[warp], bar, leaf, tstart, tcnt);
 }
 
@@ -1546,6 +1746,11 @@ __global__ void __launch_bounds__(128, TPL <= 2 ? 5 : (TPL == 4 ? 3 : 2)) p2p_ke
   const int64_t g = a.leaf_box[leaf];
   const int64_t tstart = a.box_start[g];
   const int tcnt = a.box_count[g];
+  if constexpr (TPL == 1) {
+    // leaves of at most 32 points: the quarter-warp layout
+    symq_leaf_f32<CAP>(a, sbuf[warp], bar, leaf, tstart, tcnt);
+    return;
+  }
   float tx0[NT], ty0[NT], tz0[NT], tq0[NT];
 #pragma unroll
   for (int k = 0; k < NT; k++) {
