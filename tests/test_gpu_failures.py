@@ -54,6 +54,28 @@ def test_wait_timeout_is_reported_and_recovered(F, orc, precision, field):
     assert rel_l2(u, uo) <= (1e-6 if precision == 1 else 1e-12)
 
 
+def test_wait_timeout_in_the_backward_sweep(F, orc):
+    # the symmetric backward sweep's tile waits: timeout reported, the tree
+    # stays usable and the next backward pass is correct
+    pos, q = workloads.uniform_cube(20000, seed=24)
+    g = np.random.default_rng(5).normal(size=len(q))
+    T = F.fmm_build_tree(torch.from_numpy(pos).cuda(), 6, 64, 2, 0.5, 1)
+    qd, gd = torch.from_numpy(q).cuda(), torch.from_numpy(g).cuda()
+    F.fmm_tree_set_wait_limit(T, 0)
+    F.fmm_backward(T, qd, gd)
+    with pytest.raises(F.FmmError) as ei:
+        F.fmm_tree_status(T)
+    assert ei.value.code == F.FMM_ERR_TIMEOUT
+    F.fmm_tree_set_wait_limit(T, 2000000000)
+    gq, gp = (x.cpu().numpy() for x in F.fmm_backward(T, qd, gd))
+    F.fmm_tree_status(T)
+    O = orc.Tree(pos, 64, 2, 0.5)
+    _, fq = O.eval(q, 6, field=True)
+    v, fg = O.eval(g, 6, field=True)
+    assert rel_l2(gq, v) <= 1e-6
+    assert rel_l2(gp, -(g[:, None] * fq + q[:, None] * fg)) <= 3e-5
+
+
 def test_wait_limit_rejects_negative(F):
     pos, _ = workloads.uniform_cube(1000, seed=22)
     T = F.fmm_build_tree(torch.from_numpy(pos).cuda(), 4, 32, 2, 0.5, 1)
